@@ -1,0 +1,371 @@
+"""Benchmark of the collision-integral hot path on GB300.
+
+Workload (default): the 2->2 Bose-Einstein problem with massless and
+m = 0.5 scalars, 128 log-spaced grid points on [1e-3, 30], sigma_E = 0.005,
+1e6 samples per task per iteration x 8 iterations (512 tasks: 2 species x
+128 points x gain/loss), f = BE(T=1) + a Gaussian bump, stepped with Heun.
+One bench step = one Heun step = two full collision sweeps (spline build,
+8 VEGAS iterations of the persistent sample kernel + refinement, assembly)
+plus the predictor and corrector updates.
+
+Metric: C[f] grid sweeps/s (FP32 integrand path) at the configured budget;
+also integrand evals/s, the FP64 path, and both normalised to a 1e-4 median
+relative MC error of the gain / loss estimates.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "C[f] grid sweeps/s and integrand evals/s, FP32 vs FP64 path, at 1e-4 rel MC err"
+UNIT = "sweeps/s"
+WORKLOAD = "c2_bose_2to2"
+FP32_PEAK_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+
+
+def flops_per_sample(n_legs):
+    """FP32 operations per sample of the sample kernel, counted from its
+    source (FMA = 2): 5 per VEGAS dimension (3 per integrated leg), 33 per
+    integrated leg (sincos argument scaling, momentum components, energy,
+    energy balance, measure, spline lookup, statistical factor), 23 for the
+    conserved leg, 2 for the Gaussian argument, 4 + 1 for the weight and its
+    square and 8 for the two compensated sums:  48 (n - 2) + 40."""
+    return 48 * (n_legs - 2) + 40
+
+
+def mufu_per_sample(n_legs):
+    """Special-function-unit operations per sample: 2 sincos + 1 rsqrt +
+    1 log2 per integrated leg, 2 rsqrt + 1 log2 for the conserved leg and the
+    Gaussian's exp2."""
+    return 6 * (n_legs - 2) + 4
+
+
+def workload():
+    import workloads as W
+    return W.c2_bose_2to2()
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def rel_err_stats(col):
+    mean, err = col.task_results()
+    ok = np.abs(mean) > 0
+    r = err[ok] / np.abs(mean[ok])
+    return float(np.median(r)), float(np.max(r))
+
+
+def run_native(args, rank, world):
+    import torch
+
+    import workloads as W
+    from paper_2603_28848_gb300 import Collision, build
+
+    build()
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    prob, f0 = workload()
+    n_legs = 4
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MiB > L2
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---------------- FP32 path: the headline ----------------------------------------
+    col = Collision(prob, W.PREC_FP32)
+    evals = col.sweep_samples()
+    samples_per_launch = col.sweep_samples(0)
+    logf = torch.tensor(np.log(f0), dtype=torch.float64, device="cuda").contiguous()
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    dt = torch.full((1,), 0.5, dtype=torch.float64, device="cuda")
+    C = torch.empty_like(logf)
+    for _ in range(args.warmup):
+        dt.fill_(0.5)
+        col.step_heun(logf, t, dt, C)
+    col.check()
+    stream = torch.cuda.current_stream()
+    clocks = Clocks(dev)
+    col.profile(True)
+    torch.cuda.synchronize()
+    barrier()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        dt.fill_(0.5)
+        col.step_heun(logf, t, dt, C)
+        launches += col.last_launch_count()
+        flush.zero_()                                  # evict L2 between steps
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    kern_ms, kern_n = col.profile_read()
+    col.profile(False)
+    col.check()
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = tt.item()
+    sweeps = 2 * args.steps * world
+    sweeps_per_s = sweeps / (ms / 1e3)
+    med32, max32 = rel_err_stats(col)
+
+    # ---------------- e2e: host buffers through the public API --------------------------
+    h_logf = torch.tensor(np.log(f0), dtype=torch.float64).pin_memory()
+    h_t = torch.zeros(1, dtype=torch.float64).pin_memory()
+    h_dt = torch.full((1,), 0.5, dtype=torch.float64).pin_memory()
+    h_out = torch.empty_like(h_logf).pin_memory()
+    h_C = torch.empty_like(h_logf).pin_memory()
+    torch.cuda.synchronize()
+    barrier()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        logf.copy_(h_logf, non_blocking=True)
+        t.copy_(h_t, non_blocking=True)
+        dt.copy_(h_dt, non_blocking=True)
+        col.step_heun(logf, t, dt, C)
+        h_out.copy_(logf, non_blocking=True)
+        h_C.copy_(C, non_blocking=True)
+        flush.zero_()
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e2.elapsed_time(e3)
+    if world > 1:
+        tt = torch.tensor([ms_e2e], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms_e2e = tt.item()
+    col.close()
+
+    # ---------------- FP64 path (same workload, fewer steps) ---------------------------------
+    fp64 = None
+    if not args.skip_fp64:
+        col64 = Collision(prob, W.PREC_FP64)
+        logf64 = torch.tensor(np.log(f0), dtype=torch.float64, device="cuda").contiguous()
+        t64 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dt64 = torch.full((1,), 0.5, dtype=torch.float64, device="cuda")
+        f64 = torch.exp(logf64)
+        col64.eval(f64, 0.0)                          # warm-up sweep (maps adapt)
+        torch.cuda.synchronize()
+        col64.profile(True)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.fp64_steps):
+            dt64.fill_(0.5)
+            col64.step_heun(logf64, t64, dt64)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a0.elapsed_time(a1)
+        k64_ms, k64_n = col64.profile_read()
+        col64.check()
+        med64, max64 = rel_err_stats(col64)
+        s64 = 2 * args.fp64_steps / (ms64 / 1e3)
+        fp64 = {"sweeps_per_s": s64, "evals_per_s": s64 * evals,
+                "sweeps_per_s_at_1e-4": s64 / (med64 / 1e-4) ** 2,
+                "rel_err_median": med64, "rel_err_max": max64, "steps": args.fp64_steps, "warmup_sweeps": 1,
+                "sample_kernel_ms_per_launch": k64_ms / max(k64_n, 1)}
+        col64.close()
+
+    # ---------------- roofline of the dominant kernel ----------------------------------------
+    per_launch_ms = kern_ms / max(kern_n, 1)
+    flops = flops_per_sample(n_legs) * samples_per_launch
+    achieved = flops / (per_launch_ms / 1e3) / 1e12
+    peaks = measured_peaks()
+    peak = FP32_PEAK_TFLOPS_NOMINAL
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "best::eval_kernel<float,4> (persistent sample kernel)",
+            "flops_per_sample": flops_per_sample(n_legs), "mufu_per_sample": mufu_per_sample(n_legs),
+            "samples_per_launch": samples_per_launch, "launch_ms": per_launch_ms,
+            "share_of_step": kern_ms / ms if ms > 0 else None,
+            "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz max SM clock (nominal unit "
+                          "counts; MEASURED_PEAKS.json has no FP32 figure)"}
+
+    out = {
+        "metric": METRIC, "value": sweeps_per_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded; BE(T=1) + Gaussian bump, no dataset)",
+        "config": {"workload": f"{WORKLOAD}: 2 species (m=0, m=0.5) BE 2->2, 128 log points [1e-3,30], "
+                               "sigma_E=0.005, 1e6 samples x 8 iterations per task, 512 tasks, Heun steps",
+                   "grid_points": prob.grid.n, "tasks": 512, "neval": 1_000_000, "nitn": 8,
+                   "step": "one Heun step = 2 sweeps", "l2": "flushed between steps (512 MiB write, in the "
+                   "timed region)", "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "evals_per_s": sweeps_per_s * evals,
+        "evals_per_sweep": evals,
+        "sweeps_per_s_at_1e-4": sweeps_per_s / (med32 / 1e-4) ** 2,
+        "rel_err_median": med32, "rel_err_max": max32,
+        "fp64": fp64,
+        "fp32_over_fp64_at_1e-4": (sweeps_per_s / world / (med32 / 1e-4) ** 2) / fp64["sweeps_per_s_at_1e-4"]
+        if fp64 else None,
+        "roofline": roof,
+        "e2e": {"value": sweeps / (ms_e2e / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": logf.numel() * 8 + 16, "d2h_bytes_per_step": 2 * logf.numel() * 8},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.skip_cpu:
+        out["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds, evals)
+    return out
+
+
+def cpu_baseline(prob, seconds, evals):
+    """The oracle, as it stands, on a bounded sample of the same workload:
+    whole tasks (all iterations) at a reduced budget, scaled by evals."""
+    from dataclasses import replace
+
+    from oracle import collision as ocol
+    from oracle import vegas
+    from oracle.tasks import side_integrals
+
+    neval = 20_000
+    small = replace(prob, processes=tuple(replace(p, neval=neval) for p in prob.processes))
+    sis = side_integrals(small)
+    q, f0 = None, workload()[1]
+    dists = ocol.distributions(small, f0, 0.0)
+    t0 = time.perf_counter()
+    done = 0
+    k = 0
+    pts = [5, 40, 70, 100, 120, 20, 60, 90]
+    while time.perf_counter() - t0 < seconds:
+        si_idx = k % len(sis)
+        i = pts[(k // len(sis)) % len(pts)]
+        term = k % 2
+        si = sis[si_idx]
+        p = small.processes[si.process]
+        ocol.evaluate_task(small, si_idx, si, i, term, f0, 0.0, vegas.uniform_edges(si.dim, p.nbins), 0,
+                           "f32", dists)
+        done += neval * p.nitn
+        k += 1
+    el = time.perf_counter() - t0
+    evs = done / el
+    return {"value": evs / evals, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "evals_per_s": evs,
+            "sample": f"{k} whole tasks (8 iterations, {neval} samples each) of the same workload, "
+                      f"{el:.1f} s; sweeps/s = oracle evals/s / evals per sweep ({evals:.3g})"}
+
+
+def run_reference(args, rank, world):
+    """The oracle timed on the host cores (the reference arm of this build)."""
+    prob, _ = workload()
+    # evaluations per sweep: 2 species x 128 points x (gain, loss) x nitn x neval
+    evals = sum(2 * prob.grid.n * p.nitn * p.neval for p in prob.processes)
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(prob, 1.0, evals)
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(prob, args.ref_seconds, evals))
+    v = statistics.mean(b["value"] for b in vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v if v > 0 else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)", "config": {"workload": WORKLOAD, "arm": "CPU oracle, 1 core"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=8.0)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    out = run_native(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * best.h -- C ABI of the GB300 collision-integral library (libbest.so).
+ *
+ * The library evaluates the momentum-resolved collision integral C_a[f](p_i)
+ * of the Boltzmann equation (Eq. (1)-(3) of the paper) for n_in -> n_out
+ * processes by VEGAS adaptive Monte Carlo in 3(n_total - 2) dimensions
+ * (Sec. 2D, App. A), at every grid point of a comoving momentum grid, and
+ * steps log f in time with Euler or Heun (Sec. 3C).
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named *_dev are device pointers owned by the caller (for
+ *     example torch tensors' data_ptr()); they must stay valid until the
+ *     work queued on `stream` has finished.  Host pointers are read during
+ *     the call only.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Every call that takes a stream only enqueues work on
+ *     it and returns without synchronising (except where stated), so its
+ *     results are valid once the stream reaches that point.
+ *   - Distributions are laid out species-major: f[s * n_grid + i] is f of
+ *     species s at grid point i, FP64.
+ *   - No call throws across the ABI.  Each returns a best_status;
+ *     best_last_error() gives a one-line description of the last failure
+ *     on that context.  A context must not be used from two host threads
+ *     at once.
+ */
+#ifndef BEST_H
+#define BEST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BEST_OK = 0,
+    BEST_ERR_INVALID = 1,   /* bad argument or configuration */
+    BEST_ERR_CUDA = 2,      /* a CUDA runtime call failed */
+    BEST_ERR_OOM = 3,       /* device allocation failed */
+    BEST_ERR_NUMERIC = 4,   /* non-positive or non-finite f, or a NaN result */
+    BEST_ERR_TIMEOUT = 5    /* reserved: no device wait in this library spins */
+} best_status;
+
+/* Quantum statistics of a species (Sec. 3A): eta = 0 (MB), +1 (BE), -1 (FD). */
+typedef enum { BEST_MB = 0, BEST_BE = 1, BEST_FD = 2 } best_stat;
+
+/* Arithmetic of the per-sample integrand.  Accumulators, VEGAS refinement,
+ * spline construction and time stepping are FP64 in both. */
+typedef enum { BEST_FP64 = 0, BEST_FP32 = 1 } best_precision;
+
+#define BEST_MAX_LEGS 6        /* n_total <= 6: up to 12 VEGAS dimensions */
+#define BEST_MAX_SPECIES 8
+#define BEST_MAX_PROCESSES 16
+
+/* Comoving momentum grid shared by all species (Sec. 3A): n points over
+ * [q_min, q_max], logarithmic (log_spaced != 0) or linear; 4 <= n <= 4096. */
+typedef struct {
+    int32_t n;
+    int32_t log_spaced;
+    double q_min, q_max;
+} best_grid;
+
+/* A species: statistics and mass m(t) = mass0 + mass1 * t (Sec. 3A). */
+typedef struct {
+    int32_t stat;          /* best_stat */
+    int32_t pad_;
+    double mass0, mass1;
+} best_species;
+
+/* A process n_in -> n_out (Sec. 3A, App. D) with constant |M|^2 = coupling^2.
+ * species[0 .. n_in-1] are the initial legs, species[n_in .. n_in+n_out-1]
+ * the final legs.  neval is the number of samples per VEGAS iteration per
+ * task (one task = one grid point, one pinned side, gain or loss); a
+ * non-NULL neval_per_point (host array of grid.n entries, copied during
+ * best_collision_init) overrides it per grid point.  nitn VEGAS iterations
+ * per evaluation, damping alpha, nbins increments per dimension (2..256).
+ * sigma_E is the width of the Gaussian of Eq. (11). */
+typedef struct {
+    int32_t n_in, n_out;
+    int32_t species[BEST_MAX_LEGS];
+    double coupling;
+    double sigma_E;
+    int64_t neval;
+    const int64_t* neval_per_point;
+    int32_t nitn;
+    int32_t nbins;
+    double alpha;
+} best_process;
+
+typedef struct {
+    best_grid grid;
+    int32_t n_species;
+    int32_t n_processes;
+    const best_species* species;     /* host array [n_species] */
+    const best_process* processes;   /* host array [n_processes] */
+    int32_t precision;               /* best_precision */
+    int32_t tail_points;             /* grid points in each end fit of Eq. (13), >= 2 */
+    uint64_t seed;                   /* Philox key */
+    double e_cut;                    /* samples with any E_k < e_cut weigh 0 (App. A) */
+    int32_t expansion;               /* 0: a = 1; 1: a(t) = a0 (t / t0)^(1/2) (Sec. 3E) */
+    int32_t pad_;
+    double a0, t0;
+    double eps_dt;                   /* bound on max |dt C/f| of Eq. (16) */
+} best_config;
+
+typedef struct best_ctx best_ctx;
+
+/*
+ * Builds a context: validates the configuration, enumerates the side
+ * integrals and tasks of the identical-particle decomposition (Eq. (7),
+ * Eq. (8); roles of App. A), allocates and owns all device state (VEGAS
+ * maps, one per task, kept across calls as in Sec. 3D; spline tables;
+ * accumulators; the work partition), and picks the launch shape for the
+ * current device.  Synchronous.  On failure *out is NULL and the status says
+ * why (best_last_error(NULL) describes it).
+ */
+best_status best_collision_init(const best_config* cfg, best_ctx** out);
+
+/*
+ * One collision-integral sweep at time t (host value): C_dev[s*n+i] =
+ * C_a(p_i) of Eq. (7) for every species and grid point, err_dev the Monte
+ * Carlo standard error (sqrt of sum mult^2 (sigma_gain^2 + sigma_loss^2)).
+ * f_dev: [n_species * n_grid] FP64, f > 0.  Runs nitn VEGAS iterations per
+ * task, refines every map after every iteration and advances the context's
+ * evaluation counter (part of the Philox counter).  err_dev may be NULL.
+ */
+best_status best_collision_eval(best_ctx* ctx, const double* f_dev, double t,
+                                double* C_dev, double* err_dev, void* stream);
+
+/*
+ * One log-space Euler step (Eq. (14)) with the step bound of Eq. (16):
+ * logf_dev [n_species * n_grid] is updated in place; *t_dev (device FP64)
+ * is the current time and advances by the step used; *dt_dev (device FP64)
+ * holds the requested step on entry and the step used on return,
+ * dt = min(dt_requested, eps_dt / max |C/f|).  C_dev, if not NULL, receives
+ * C[f(t)].  No host synchronisation: the call can be captured in a CUDA
+ * graph.
+ */
+best_status best_step_euler(best_ctx* ctx, double* logf_dev, double* t_dev,
+                            double* dt_dev, double* C_dev, void* stream);
+
+/*
+ * One Heun step (Eq. (15)): k1 = C[f] at t, f* = exp(log f + dt k1/f),
+ * k2 = C[f*] at t + dt, log f += dt/2 (k1/f + k2/f*), dt bounded by
+ * Eq. (16) from k1.  Arguments as for best_step_euler.
+ */
+best_status best_step_heun(best_ctx* ctx, double* logf_dev, double* t_dev,
+                           double* dt_dev, double* C_dev, void* stream);
+
+/* Context geometry. */
+int32_t best_num_tasks(const best_ctx* ctx);
+int32_t best_num_side_integrals(const best_ctx* ctx);
+
+/* Integrand evaluations of one sweep: in VEGAS iteration `iteration` (one
+ * launch of the sample kernel), or in all iterations when iteration < 0. */
+int64_t best_sweep_samples(const best_ctx* ctx, int32_t iteration);
+
+/*
+ * Copies per-task results of the last completed sweep to host memory
+ * (synchronises the stream): mean[t] and err[t] are the combined VEGAS
+ * estimate of task t and its standard error.  Task numbering:
+ * t = (side_integral * n_grid + grid_point) * 2 + term, term 0 = gain,
+ * 1 = loss; side integrals ordered by process, side (initial first), then
+ * observed species.  Either pointer may be NULL.
+ */
+best_status best_get_task_results(best_ctx* ctx, double* mean, double* err, void* stream);
+
+/*
+ * Copies (to) / from host memory the VEGAS map edges of every task:
+ * task t, dimension d, edge b at edges[t * 3*(BEST_MAX_LEGS-2) * (nbins_max+1)
+ * + d * (nbins_max+1) + b], nbins_max the largest nbins of any process.
+ * Synchronous.  best_map_stride() returns 3*(BEST_MAX_LEGS-2)*(nbins_max+1).
+ */
+int64_t best_map_stride(const best_ctx* ctx);
+best_status best_get_maps(best_ctx* ctx, double* edges_host);
+best_status best_set_maps(best_ctx* ctx, const double* edges_host);
+
+/* Reads / sets the evaluation counter that enters every Philox counter.
+ * Synchronous. */
+best_status best_get_call_counter(best_ctx* ctx, uint32_t* call);
+best_status best_set_call_counter(best_ctx* ctx, uint32_t call);
+
+/*
+ * Synchronises `stream` and reports errors that the device recorded since
+ * the last check: BEST_ERR_NUMERIC when an input f was not positive and
+ * finite, a(t) was not positive, or a result was not finite; BEST_ERR_CUDA
+ * for a failed launch.  Clears the recorded error.
+ */
+best_status best_check(best_ctx* ctx, void* stream);
+
+/*
+ * Timing of the sample kernel, for measurement.  While enabled, every launch
+ * of the sample kernel is bracketed by a pair of CUDA events recorded on the
+ * launching stream (events are created on first use and reused).
+ * best_profile_read waits for the recorded events, returns the summed kernel
+ * time in milliseconds and the number of launches since the last read or
+ * enable, and starts a new count.  Do not enable while capturing a graph.
+ */
+best_status best_profile_enable(best_ctx* ctx, int32_t enable);
+best_status best_profile_read(best_ctx* ctx, double* sample_kernel_ms, int64_t* launches);
+
+/* Number of kernels the last eval / Euler / Heun call enqueued. */
+int32_t best_last_launch_count(const best_ctx* ctx);
+
+/* Description of the last failure on ctx (or of the last failed init when
+ * ctx is NULL); never NULL. */
+const char* best_last_error(const best_ctx* ctx);
+
+/* Frees the context and its device memory.  Synchronises the device. */
+void best_collision_destroy(best_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEST_H */

@@ -21,8 +21,17 @@ The map and its refinement here follow Lepage's published algorithm
     d = 0), then choose new edges so that each new increment holds an equal
     share of the compressed weight, interpolating linearly inside old
     increments.  A dimension whose d is all zero keeps its edges.
+
+Reading (not in the paper or in Lepage's description): a smoothed,
+normalised share below EMPTY_SHARE = 1e-30 counts as an empty increment
+(compressed weight 0, like d = 0).  The compression jumps from about 0.1 for
+a tiny positive share to 0 for an exact zero, so without this rule the map
+would depend on where floating-point underflow of w^2 falls, i.e. on the
+overall scale of w and on the precision of the training data.
 """
 import numpy as np
+
+EMPTY_SHARE = 1e-30
 
 
 def uniform_edges(dim, nbins):
@@ -69,7 +78,7 @@ def refine_1d(edges, d, alpha):
     # compression (damping) with exponent alpha
     omega = np.zeros(nb)
     for b in range(nb):
-        if s[b] <= 0.0:
+        if s[b] < EMPTY_SHARE:
             omega[b] = 0.0
         elif s[b] >= 1.0:
             omega[b] = 1.0

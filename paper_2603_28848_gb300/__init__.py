@@ -1,0 +1,200 @@
+"""GB300 collision-integral library: Python binding of libbest.so.
+
+Every step of the Monte Carlo collision integral and of the time stepping
+runs in the CUDA kernels behind the C ABI of include/best.h; this module only
+marshals arguments.  PyTorch provides device memory and streams.  There is no
+CPU fallback: if libbest.so is missing or no CUDA device is present, calls
+fail.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import BestError, check
+
+__all__ = ["Collision", "BestError", "build", "config_from_problem"]
+
+
+def build(verbose=False, force=False):
+    from .buildlib import build as _build
+    return _build(verbose=verbose, force=force)
+
+
+def config_from_problem(problem, precision):
+    """best_config for a ``workloads.Problem`` (plus the arrays it points to,
+    which must outlive the init call)."""
+    keep = []
+    g = problem.grid
+    sp = (_lib.best_species * len(problem.species))()
+    for k, s in enumerate(problem.species):
+        sp[k].stat = int(s.stat)
+        sp[k].mass0 = float(s.mass0)
+        sp[k].mass1 = float(s.mass1)
+    pr = (_lib.best_process * len(problem.processes))()
+    for k, p in enumerate(problem.processes):
+        legs = tuple(p.species_in) + tuple(p.species_out)
+        if len(legs) > _lib.MAX_LEGS:
+            raise BestError(f"process {p.name}: more than {_lib.MAX_LEGS} legs")
+        pr[k].n_in = len(p.species_in)
+        pr[k].n_out = len(p.species_out)
+        for j, s in enumerate(legs):
+            pr[k].species[j] = int(s)
+        pr[k].coupling = float(p.coupling)
+        pr[k].sigma_E = float(p.sigma_E)
+        pr[k].neval = int(p.neval)
+        if p.neval_per_point is not None:
+            arr = (ctypes.c_int64 * len(p.neval_per_point))(*[int(v) for v in p.neval_per_point])
+            keep.append(arr)
+            pr[k].neval_per_point = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int64))
+        pr[k].nitn = int(p.nitn)
+        pr[k].nbins = int(p.nbins)
+        pr[k].alpha = float(p.alpha)
+    cfg = _lib.best_config()
+    cfg.grid.n = int(g.n)
+    cfg.grid.log_spaced = 1 if g.log_spaced else 0
+    cfg.grid.q_min = float(g.q_min)
+    cfg.grid.q_max = float(g.q_max)
+    cfg.n_species = len(problem.species)
+    cfg.n_processes = len(problem.processes)
+    cfg.species = ctypes.cast(sp, ctypes.POINTER(_lib.best_species))
+    cfg.processes = ctypes.cast(pr, ctypes.POINTER(_lib.best_process))
+    cfg.precision = int(precision)
+    cfg.tail_points = int(problem.tail_points)
+    cfg.seed = int(problem.seed) & 0xFFFFFFFFFFFFFFFF
+    cfg.e_cut = float(problem.e_cut)
+    if problem.expansion is not None:
+        cfg.expansion = 1
+        cfg.a0 = float(problem.expansion.a0)
+        cfg.t0 = float(problem.expansion.t0)
+    else:
+        cfg.expansion = 0
+        cfg.a0 = 1.0
+        cfg.t0 = 1.0
+    cfg.eps_dt = float(problem.eps_dt)
+    keep += [sp, pr]
+    return cfg, keep
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _require(t, n, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise BestError(f"{name} must be a contiguous CUDA float64 tensor")
+    if t.numel() != n:
+        raise BestError(f"{name} must have {n} elements, got {t.numel()}")
+
+
+class Collision:
+    """One context of libbest: the tasks, VEGAS maps and device state of a
+    problem.  ``precision``: workloads.PREC_FP64 or PREC_FP32."""
+
+    def __init__(self, problem, precision):
+        import torch
+        if not torch.cuda.is_available():
+            raise BestError("a CUDA device is required")
+        torch.cuda.init()
+        self.lib = _lib.load()
+        self.problem = problem
+        self.precision = precision
+        self.n_species = len(problem.species)
+        self.n_grid = problem.grid.n
+        cfg, keep = config_from_problem(problem, precision)
+        ctx = ctypes.c_void_p()
+        check(self.lib.best_collision_init(ctypes.byref(cfg), ctypes.byref(ctx)))
+        del keep
+        self.ctx = ctx
+        self.n_tasks = self.lib.best_num_tasks(ctx)
+        self.n_side = self.lib.best_num_side_integrals(ctx)
+
+    # -- the hot path ---------------------------------------------------------
+    def eval(self, f, t=0.0, C=None, err=None, stream=None):
+        """C[f] and its MC error at time t; f: (n_species, n_grid) float64 CUDA."""
+        import torch
+        n = self.n_species * self.n_grid
+        _require(f, n, "f")
+        if C is None:
+            C = torch.empty_like(f)
+        if err is None:
+            err = torch.empty_like(f)
+        check(self.lib.best_collision_eval(self.ctx, _ptr(f), float(t), _ptr(C), _ptr(err),
+                                           _stream(stream)), self.ctx)
+        return C, err
+
+    def step_euler(self, logf, t_dev, dt_dev, C=None, stream=None):
+        _require(logf, self.n_species * self.n_grid, "logf")
+        check(self.lib.best_step_euler(self.ctx, _ptr(logf), _ptr(t_dev), _ptr(dt_dev), _ptr(C),
+                                       _stream(stream)), self.ctx)
+
+    def step_heun(self, logf, t_dev, dt_dev, C=None, stream=None):
+        _require(logf, self.n_species * self.n_grid, "logf")
+        check(self.lib.best_step_heun(self.ctx, _ptr(logf), _ptr(t_dev), _ptr(dt_dev), _ptr(C),
+                                      _stream(stream)), self.ctx)
+
+    # -- inspection -------------------------------------------------------------
+    def check(self, stream=None):
+        check(self.lib.best_check(self.ctx, _stream(stream)), self.ctx)
+
+    def task_results(self, stream=None):
+        mean = np.zeros(self.n_tasks)
+        err = np.zeros(self.n_tasks)
+        check(self.lib.best_get_task_results(self.ctx, mean.ctypes.data_as(ctypes.c_void_p),
+                                             err.ctypes.data_as(ctypes.c_void_p), _stream(stream)), self.ctx)
+        return mean, err
+
+    def maps(self):
+        stride = self.lib.best_map_stride(self.ctx)
+        out = np.zeros(self.n_tasks * stride)
+        check(self.lib.best_get_maps(self.ctx, out.ctypes.data_as(ctypes.c_void_p)), self.ctx)
+        return out.reshape(self.n_tasks, stride)
+
+    def set_maps(self, edges):
+        edges = np.ascontiguousarray(edges, dtype=np.float64)
+        check(self.lib.best_set_maps(self.ctx, edges.ctypes.data_as(ctypes.c_void_p)), self.ctx)
+
+    @property
+    def call_counter(self):
+        c = ctypes.c_uint32()
+        check(self.lib.best_get_call_counter(self.ctx, ctypes.byref(c)), self.ctx)
+        return c.value
+
+    @call_counter.setter
+    def call_counter(self, value):
+        check(self.lib.best_set_call_counter(self.ctx, int(value)), self.ctx)
+
+    def profile(self, enable=True):
+        check(self.lib.best_profile_enable(self.ctx, 1 if enable else 0), self.ctx)
+
+    def profile_read(self):
+        """(summed sample-kernel milliseconds, launches) since the last read."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        check(self.lib.best_profile_read(self.ctx, ctypes.byref(ms), ctypes.byref(n)), self.ctx)
+        return ms.value, n.value
+
+    def sweep_samples(self, iteration=-1):
+        """Integrand evaluations per sweep (or in one VEGAS iteration)."""
+        return self.lib.best_sweep_samples(self.ctx, int(iteration))
+
+    def last_launch_count(self):
+        return self.lib.best_last_launch_count(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            self.lib.best_collision_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

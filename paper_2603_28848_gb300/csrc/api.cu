@@ -1,0 +1,695 @@
+// Host side of the C ABI declared in include/best.h: configuration checks,
+// the identical-particle decomposition into tasks (Sec. 2C, App. A), the
+// static work partition of the persistent sample kernel, device memory and
+// the launch sequences of a sweep, an Euler step and a Heun step.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace best {
+// kernels.cu
+__global__ void set_time_kernel(Geometry, TimeState*, const double*, double, int, const double*, const double*);
+__global__ void spline_build_kernel(Geometry, const double*, int, const double*, TimeState*, SpeciesConst*,
+                                    double*, double*, float*);
+__global__ void prepare_kernel(Geometry, const SideDesc*, const TaskDesc*, const double*, const double*,
+                               const TimeState*, const double*, TaskConst*, TaskAcc*);
+__global__ void refine_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskConst*, const int32_t*,
+                              const int32_t*, const Segment*, const double*, double*, TaskAcc*, TaskConst*);
+__global__ void assemble_kernel(Geometry, const SideDesc*, TaskAcc*, TimeState*, double*, double*, double*);
+__global__ void step_first_kernel(Geometry, double*, const double*, const double*, double*, double*, TimeState*,
+                                  double*, int);
+__global__ void heun_correct_kernel(Geometry, double*, const double*, const double*, const double*, double*,
+                                    double*, TimeState*);
+// eval_f32.cu / eval_f64.cu
+void* eval_kernel_ptr_f32(int nmax);
+void* eval_kernel_ptr_f64(int nmax);
+}  // namespace best
+
+using namespace best;
+
+namespace {
+
+thread_local std::string g_init_error = "no error";
+
+// Work of one VEGAS iteration index: the active tasks and their segments.
+struct IterPlan {
+    int n_active = 0;
+    int n_segs = 0;
+    int64_t partial_doubles = 0;
+    int32_t* d_active = nullptr;     // [n_active] task ids
+    int32_t* d_task_seg = nullptr;   // [n_active + 1]
+    Segment* d_segs = nullptr;       // [n_segs]
+    int32_t* d_cta_seg = nullptr;    // [grid + 1]
+};
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+}
+
+}  // namespace
+
+struct best_ctx {
+    std::string err = "no error";
+    Geometry geo{};
+    int precision = 0;
+    int nmax_legs = 0;
+    int grid = 0;                   // CTAs of the persistent sample kernel
+    size_t eval_smem = 0;
+    size_t spline_smem = 0;
+    size_t refine_smem = 0;
+    void* eval_fn = nullptr;
+    int launches = 0;
+    int max_nitn = 0;
+    std::vector<SideDesc> sides;
+    std::vector<TaskDesc> tasks;
+    std::vector<IterPlan> plans;
+    // device state
+    SideDesc* d_sides = nullptr;
+    TaskDesc* d_tasks = nullptr;
+    TaskConst* d_tconst = nullptr;
+    TaskAcc* d_acc = nullptr;
+    SpeciesConst* d_sconst = nullptr;
+    TimeState* d_ts = nullptr;
+    double* d_edges = nullptr;
+    double* d_knots = nullptr;
+    float* d_knots32 = nullptr;
+    double* d_coef64 = nullptr;
+    float* d_coef32 = nullptr;
+    double* d_fgrid = nullptr;
+    double* d_mass0 = nullptr;
+    double* d_mass1 = nullptr;
+    double* d_partials = nullptr;
+    double* d_k1 = nullptr;
+    double* d_k2 = nullptr;
+    double* d_fstar = nullptr;
+    double* d_prev = nullptr;       // |estimate| of every task from the last sweep (0: none)
+    // timing of the sample kernel (best_profile_*)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;    // start/stop pairs
+    size_t ev_used = 0;
+};
+
+namespace {
+
+best_status fail(best_ctx* c, best_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_init_error = buf;
+    return st;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? BEST_ERR_OOM : BEST_ERR_CUDA,   \
+                        "%s: %s", #call, cudaGetErrorString(e_));                             \
+        }                                                                                     \
+    } while (0)
+
+// Roles of App. A for an observed leg: conserved leg and integrated legs.
+void roles(int n_in, int n_out, int obs, int* cons, int* integ) {
+    const int n = n_in + n_out;
+    const bool obs_in = obs < n_in;
+    bool first_in;
+    if (n_in != n_out) first_in = n_in < n_out;
+    else first_in = obs_in;
+    int c = -1;
+    for (int k = first_in ? 0 : n_in; k < (first_in ? n_in : n); ++k)
+        if (k != obs) { c = k; break; }
+    if (c < 0)
+        for (int k = first_in ? n_in : 0; k < (first_in ? n : n_in); ++k)
+            if (k != obs) { c = k; break; }
+    *cons = c;
+    int j = 0;
+    for (int k = 0; k < n; ++k)
+        if (k != obs && k != c) integ[j++] = k;
+}
+
+void free_all(best_ctx* c) {
+    for (auto& p : c->plans) {
+        cudaFree(p.d_active); cudaFree(p.d_task_seg); cudaFree(p.d_segs); cudaFree(p.d_cta_seg);
+    }
+    c->plans.clear();
+    void* bufs[] = {c->d_sides, c->d_tasks, c->d_tconst, c->d_acc, c->d_sconst, c->d_ts, c->d_edges,
+                    c->d_knots, c->d_knots32, c->d_coef64, c->d_coef32, c->d_fgrid, c->d_mass0, c->d_mass1,
+                    c->d_partials, c->d_k1, c->d_k2, c->d_fstar, c->d_prev};
+    for (void* b : bufs) cudaFree(b);
+}
+
+best_status validate(const best_config* cfg) {
+    best_ctx* ctx = nullptr;
+    if (!cfg) return fail(ctx, BEST_ERR_INVALID, "cfg is NULL");
+    const best_grid& g = cfg->grid;
+    if (g.n < 4 || g.n > 4096) return fail(ctx, BEST_ERR_INVALID, "grid.n must be in [4, 4096]");
+    if (!(g.q_min > 0.0) || !(g.q_max > g.q_min) || !std::isfinite(g.q_max))
+        return fail(ctx, BEST_ERR_INVALID, "need 0 < q_min < q_max");
+    if (cfg->n_species < 1 || cfg->n_species > BEST_MAX_SPECIES || !cfg->species)
+        return fail(ctx, BEST_ERR_INVALID, "n_species must be in [1, %d]", BEST_MAX_SPECIES);
+    if (cfg->n_processes < 1 || cfg->n_processes > BEST_MAX_PROCESSES || !cfg->processes)
+        return fail(ctx, BEST_ERR_INVALID, "n_processes must be in [1, %d]", BEST_MAX_PROCESSES);
+    if (cfg->precision != BEST_FP64 && cfg->precision != BEST_FP32)
+        return fail(ctx, BEST_ERR_INVALID, "precision must be BEST_FP64 or BEST_FP32");
+    if (cfg->tail_points < 2 || cfg->tail_points > g.n)
+        return fail(ctx, BEST_ERR_INVALID, "tail_points must be in [2, grid.n]");
+    if (cfg->expansion && (!(cfg->a0 > 0.0) || !(cfg->t0 > 0.0)))
+        return fail(ctx, BEST_ERR_INVALID, "expansion needs a0 > 0 and t0 > 0");
+    if (!(cfg->eps_dt > 0.0)) return fail(ctx, BEST_ERR_INVALID, "eps_dt must be > 0");
+    for (int s = 0; s < cfg->n_species; ++s) {
+        const best_species& sp = cfg->species[s];
+        if (sp.stat < 0 || sp.stat > 2) return fail(ctx, BEST_ERR_INVALID, "species %d: bad stat", s);
+        if (!std::isfinite(sp.mass0) || !std::isfinite(sp.mass1))
+            return fail(ctx, BEST_ERR_INVALID, "species %d: bad mass", s);
+    }
+    for (int p = 0; p < cfg->n_processes; ++p) {
+        const best_process& pr = cfg->processes[p];
+        const int n = pr.n_in + pr.n_out;
+        if (pr.n_in < 1 || pr.n_out < 1 || n < 3 || n > BEST_MAX_LEGS)
+            return fail(ctx, BEST_ERR_INVALID, "process %d: need 3 <= n_in + n_out <= %d", p, BEST_MAX_LEGS);
+        for (int k = 0; k < n; ++k)
+            if (pr.species[k] < 0 || pr.species[k] >= cfg->n_species)
+                return fail(ctx, BEST_ERR_INVALID, "process %d: leg %d has a bad species", p, k);
+        if (!(pr.sigma_E > 0.0)) return fail(ctx, BEST_ERR_INVALID, "process %d: sigma_E must be > 0", p);
+        if (pr.nitn < 1 || pr.nitn > 1000) return fail(ctx, BEST_ERR_INVALID, "process %d: nitn in [1,1000]", p);
+        if (pr.nbins < 2 || pr.nbins > 256) return fail(ctx, BEST_ERR_INVALID, "process %d: nbins in [2,256]", p);
+        if (!(pr.alpha >= 0.0)) return fail(ctx, BEST_ERR_INVALID, "process %d: alpha must be >= 0", p);
+        for (int i = 0; i < g.n; ++i) {
+            const int64_t N = pr.neval_per_point ? pr.neval_per_point[i] : pr.neval;
+            if (N < 2 || N > (int64_t(1) << 31))
+                return fail(ctx, BEST_ERR_INVALID, "process %d: neval must be in [2, 2^31]", p);
+        }
+    }
+    return BEST_OK;
+}
+
+int group_size(int D, bool f32) {
+    const int per = f32 ? 4 : 2;
+    int a = D, b = per;
+    while (b) { int t = a % b; a = b; b = t; }
+    return per / a;
+}
+
+// Static partition of the active tasks of one iteration over `grid` CTAs,
+// balanced by an estimate of the cost of a sample group (its samples times
+// the number of dimensions plus a constant).  Segments come out ordered by
+// task, so each task's segment records are contiguous.
+best_status build_plan(best_ctx* ctx, int it, IterPlan& plan) {
+    const bool f32 = ctx->precision == BEST_FP32;
+    std::vector<int32_t> active;
+    for (size_t t = 0; t < ctx->tasks.size(); ++t)
+        if (ctx->tasks[t].nitn > it) active.push_back(static_cast<int32_t>(t));
+    const int A = static_cast<int>(active.size());
+    std::vector<int64_t> groups(A), cost(A), cum(A + 1, 0);
+    for (int a = 0; a < A; ++a) {
+        const TaskDesc& td = ctx->tasks[active[a]];
+        const int G = group_size(td.dim, f32);
+        groups[a] = (td.neval + G - 1) / G;
+        cost[a] = static_cast<int64_t>(G) * (td.dim + 6);
+        cum[a + 1] = cum[a] + groups[a] * cost[a];
+    }
+    const int64_t W = cum[A];
+    const int B = ctx->grid;
+    std::vector<Segment> segs;
+    std::vector<int32_t> cta_seg(B + 1, 0);
+    std::vector<int32_t> seg_active;
+    int a0 = 0;
+    for (int b = 0; b < B; ++b) {
+        cta_seg[b] = static_cast<int32_t>(segs.size());
+        const int64_t lo = W * b / B, hi = W * (b + 1) / B;
+        while (a0 < A && cum[a0 + 1] <= lo) ++a0;
+        for (int a = a0; a < A && cum[a] < hi; ++a) {
+            const int64_t c = cost[a];
+            const int64_t g0 = std::max<int64_t>(0, (lo - cum[a] + c - 1) / c);
+            const int64_t g1 = std::min<int64_t>(groups[a], (hi - cum[a] + c - 1) / c);
+            if (g1 <= g0) continue;
+            Segment s{};
+            s.task = active[a];
+            s.g0 = g0;
+            s.g1 = g1;
+            segs.push_back(s);
+            seg_active.push_back(a);
+        }
+    }
+    cta_seg[B] = static_cast<int32_t>(segs.size());
+    // partial records and per-task segment ranges
+    std::vector<int32_t> task_seg(A + 1, 0);
+    int64_t off = 0;
+    for (size_t k = 0; k < segs.size(); ++k) {
+        segs[k].part = off;
+        const TaskDesc& td = ctx->tasks[segs[k].task];
+        off += 2 + static_cast<int64_t>(td.dim) * td.nbins;
+    }
+    {
+        size_t k = 0;
+        for (int a = 0; a < A; ++a) {
+            task_seg[a] = static_cast<int32_t>(k);
+            while (k < segs.size() && seg_active[k] == a) ++k;
+        }
+        task_seg[A] = static_cast<int32_t>(k);
+        if (k != segs.size()) return fail(ctx, BEST_ERR_INVALID, "internal: segments not ordered by task");
+    }
+    plan.n_active = A;
+    plan.n_segs = static_cast<int>(segs.size());
+    plan.partial_doubles = off;
+    CK(dalloc(&plan.d_active, A));
+    CK(dalloc(&plan.d_task_seg, A + 1));
+    CK(dalloc(&plan.d_segs, segs.size()));
+    CK(dalloc(&plan.d_cta_seg, B + 1));
+    CK(cudaMemcpy(plan.d_active, active.data(), A * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(plan.d_task_seg, task_seg.data(), (A + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(plan.d_segs, segs.data(), segs.size() * sizeof(Segment), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(plan.d_cta_seg, cta_seg.data(), (B + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    return BEST_OK;
+}
+
+// Kernels of one collision sweep after set_time: spline, task constants,
+// nitn x (sample kernel + refinement), assembly into C / err.
+best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double* C, double* err,
+                          cudaStream_t st) {
+    const Geometry& g = ctx->geo;
+    spline_build_kernel<<<g.n_species, 256, ctx->spline_smem, st>>>(
+        g, src, src_mode, ctx->d_knots, ctx->d_ts, ctx->d_sconst, ctx->d_fgrid, ctx->d_coef64, ctx->d_coef32);
+    prepare_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_knots,
+                                                            ctx->d_fgrid, ctx->d_ts, ctx->d_prev, ctx->d_tconst,
+                                                            ctx->d_acc);
+    ctx->launches += 2;
+    const bool f32 = ctx->precision == BEST_FP32;
+    for (int it = 0; it < ctx->max_nitn; ++it) {
+        const IterPlan& pl = ctx->plans[it];
+        if (pl.n_active == 0) continue;
+        EvalParams P;
+        P.geo = g;
+        P.sides = ctx->d_sides;
+        P.tasks = ctx->d_tasks;
+        P.tconst = ctx->d_tconst;
+        P.sconst = ctx->d_sconst;
+        P.ts = ctx->d_ts;
+        P.edges = ctx->d_edges;
+        P.segs = pl.d_segs;
+        P.cta_seg = pl.d_cta_seg;
+        P.coef = f32 ? static_cast<const void*>(ctx->d_coef32) : static_cast<const void*>(ctx->d_coef64);
+        P.knots = f32 ? static_cast<const void*>(ctx->d_knots32) : static_cast<const void*>(ctx->d_knots);
+        P.partials = ctx->d_partials;
+        P.itn = static_cast<uint32_t>(it);
+        P.smem_spline_elems = g.n_species * 4 * (g.n_grid - 1) + g.n_grid;
+        void* args[] = {&P};
+        if (ctx->profiling) {
+            while (ctx->ev.size() < ctx->ev_used + 2) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                ctx->ev.push_back(e);
+            }
+            CK(cudaEventRecord(ctx->ev[ctx->ev_used], st));
+        }
+        CK(cudaLaunchKernel(ctx->eval_fn, dim3(ctx->grid), dim3(kThreads), args, ctx->eval_smem, st));
+        if (ctx->profiling) {
+            CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], st));
+            ctx->ev_used += 2;
+        }
+        refine_kernel<<<pl.n_active, 128, ctx->refine_smem, st>>>(
+            g, ctx->d_sides, ctx->d_tasks, ctx->d_tconst, pl.d_active, pl.d_task_seg, pl.d_segs,
+            ctx->d_partials, ctx->d_edges, ctx->d_acc, ctx->d_tconst);
+        ctx->launches += 2;
+    }
+    const int total = g.n_species * g.n_grid;
+    assemble_kernel<<<(total + 255) / 256, 256, 0, st>>>(g, ctx->d_sides, ctx->d_acc, ctx->d_ts, C, err,
+                                                         ctx->d_prev);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    return BEST_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+best_status best_collision_init(const best_config* cfg, best_ctx** out) {
+    if (!out) return fail(nullptr, BEST_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    best_status vs = validate(cfg);
+    if (vs != BEST_OK) return vs;
+    best_ctx* ctx = new best_ctx();
+    auto bail = [&](best_status s) {
+        g_init_error = ctx->err;
+        free_all(ctx);
+        delete ctx;
+        return s;
+    };
+    Geometry& g = ctx->geo;
+    g.n_grid = cfg->grid.n;
+    g.log_spaced = cfg->grid.log_spaced ? 1 : 0;
+    g.q_min = cfg->grid.q_min;
+    g.q_max = cfg->grid.q_max;
+    g.log_step = g.log_spaced ? std::log(g.q_max / g.q_min) / (g.n_grid - 1) : (g.q_max - g.q_min) / (g.n_grid - 1);
+    g.n_species = cfg->n_species;
+    g.expansion = cfg->expansion ? 1 : 0;
+    g.a0 = cfg->a0;
+    g.t0 = cfg->t0;
+    g.e_cut = cfg->e_cut;
+    g.eps_dt = cfg->eps_dt;
+    g.seed = cfg->seed;
+    g.tail_points = cfg->tail_points;
+    g.precision = cfg->precision;
+    ctx->precision = cfg->precision;
+    const bool f32 = cfg->precision == BEST_FP32;
+
+    // ---- side integrals (Eq. (7), Eq. (8)) and tasks -----------------------------
+    int nb_max = 2;
+    for (int p = 0; p < cfg->n_processes; ++p) {
+        const best_process& pr = cfg->processes[p];
+        const int n_in = pr.n_in, n_out = pr.n_out, n = n_in + n_out;
+        std::vector<int> a_in(pr.species, pr.species + n_in), a_out(pr.species + n_in, pr.species + n);
+        std::vector<int> s_in = a_in, s_out = a_out;
+        std::sort(s_in.begin(), s_in.end());
+        std::sort(s_out.begin(), s_out.end());
+        const bool symmetric = s_in == s_out;
+        nb_max = std::max(nb_max, pr.nbins);
+        ctx->nmax_legs = std::max(ctx->nmax_legs, n);
+        ctx->max_nitn = std::max(ctx->max_nitn, pr.nitn);
+        for (int side = 0; side < (symmetric ? 1 : 2); ++side) {
+            const std::vector<int>& sp = side == 0 ? a_in : a_out;
+            const int offset = side == 0 ? 0 : n_in;
+            std::vector<int> distinct = sp;
+            std::sort(distinct.begin(), distinct.end());
+            distinct.erase(std::unique(distinct.begin(), distinct.end()), distinct.end());
+            for (int a : distinct) {
+                SideDesc sd{};
+                sd.n = n;
+                sd.n_in = n_in;
+                sd.obs = offset + static_cast<int>(std::find(sp.begin(), sp.end(), a) - sp.begin());
+                sd.mult = static_cast<int>(std::count(sp.begin(), sp.end(), a));
+                sd.species_obs = a;
+                sd.process = p;
+                sd.side = side;
+                roles(n_in, n_out, sd.obs, &sd.cons, sd.integ);
+                for (int k = 0; k < n; ++k) {
+                    sd.leg_species[k] = pr.species[k];
+                    const bool kin = k < n_in;
+                    if (kin) sd.in_mask |= 1 << k;
+                    if (kin == (side == 0)) sd.own_mask |= 1 << k;
+                }
+                sd.coupling2 = pr.coupling * pr.coupling;
+                const int st_obs = cfg->species[a].stat;
+                sd.eta_obs = st_obs == BEST_BE ? 1.0 : (st_obs == BEST_FD ? -1.0 : 0.0);
+                sd.sigma = pr.sigma_E;
+                ctx->sides.push_back(sd);
+            }
+        }
+    }
+    g.n_side = static_cast<int>(ctx->sides.size());
+    g.nbins_max = nb_max;
+    g.map_stride = kMaxDim * (nb_max + 1);
+    for (int si = 0; si < g.n_side; ++si) {
+        const SideDesc& sd = ctx->sides[si];
+        const best_process& pr = cfg->processes[sd.process];
+        for (int i = 0; i < g.n_grid; ++i)
+            for (int term = 0; term < 2; ++term) {
+                TaskDesc td{};
+                td.si = si;
+                td.point = i;
+                td.term = term;
+                td.nitn = pr.nitn;
+                td.neval = pr.neval_per_point ? pr.neval_per_point[i] : pr.neval;
+                td.dim = 3 * (sd.n - 2);
+                td.nbins = pr.nbins;
+                td.alpha = pr.alpha;
+                ctx->tasks.push_back(td);
+            }
+    }
+    g.n_tasks = static_cast<int>(ctx->tasks.size());
+    if (static_cast<int64_t>(g.n_tasks) >= (int64_t(1) << 31)) return bail(fail(ctx, BEST_ERR_INVALID, "too many tasks"));
+
+    // ---- launch shape of the sample kernel -------------------------------------------------
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return bail(fail(ctx, BEST_ERR_CUDA, "no CUDA device"));
+    ctx->eval_fn = f32 ? eval_kernel_ptr_f32(ctx->nmax_legs) : eval_kernel_ptr_f64(ctx->nmax_legs);
+    {
+        const size_t rs = f32 ? 4 : 8;
+        const size_t spl = static_cast<size_t>(g.n_species) * 4 * (g.n_grid - 1) + g.n_grid;
+        const size_t map_elems = static_cast<size_t>(kMaxDim) * nb_max;
+        const size_t hist_elems = static_cast<size_t>(kThreads / 32) * map_elems;
+        ctx->eval_smem = rs * ((spl + 3) & ~size_t(3)) + 2 * rs * map_elems + rs * ((hist_elems + 3) & ~size_t(3)) +
+                         2 * 32 * sizeof(double);
+        int max_optin = 0;
+        cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (ctx->eval_smem > static_cast<size_t>(max_optin))
+            return bail(fail(ctx, BEST_ERR_INVALID, "spline and map tables need %zu B of shared memory (max %d)",
+                             ctx->eval_smem, max_optin));
+        if (cudaFuncSetAttribute(ctx->eval_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(ctx->eval_smem)) != cudaSuccess)
+            return bail(fail(ctx, BEST_ERR_CUDA, "cannot set shared memory of the sample kernel"));
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ctx->eval_fn, kThreads, ctx->eval_smem) != cudaSuccess || occ < 1)
+            return bail(fail(ctx, BEST_ERR_CUDA, "sample kernel does not fit on an SM"));
+        ctx->grid = nsm * occ;
+        ctx->spline_smem = 3 * sizeof(double) * g.n_grid;
+        if (cudaFuncSetAttribute(reinterpret_cast<const void*>(&spline_build_kernel),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(ctx->spline_smem)) != cudaSuccess)
+            return bail(fail(ctx, BEST_ERR_CUDA, "cannot set shared memory of the spline kernel"));
+        ctx->refine_smem = sizeof(double) * (static_cast<size_t>(kMaxDim) * nb_max + 2);
+    }
+
+    // ---- device state ----------------------------------------------------------------------------
+    const int S = g.n_species, n = g.n_grid, T = g.n_tasks;
+    std::vector<double> knots(n);
+    for (int j = 0; j < n; ++j) {
+        if (g.log_spaced) knots[j] = g.q_min * std::pow(g.q_max / g.q_min, static_cast<double>(j) / (n - 1));
+        else knots[j] = g.q_min + (g.q_max - g.q_min) * j / (n - 1);
+    }
+    knots[0] = g.q_min;
+    knots[n - 1] = g.q_max;
+    std::vector<float> knots32(knots.begin(), knots.end());
+    std::vector<SpeciesConst> sconst(S);
+    std::vector<double> m0(S), m1(S);
+    for (int s = 0; s < S; ++s) {
+        sconst[s] = SpeciesConst{};
+        sconst[s].stat = cfg->species[s].stat;
+        sconst[s].eta = cfg->species[s].stat == BEST_BE ? 1.0 : (cfg->species[s].stat == BEST_FD ? -1.0 : 0.0);
+        m0[s] = cfg->species[s].mass0;
+        m1[s] = cfg->species[s].mass1;
+    }
+    std::vector<double> edges(static_cast<size_t>(T) * g.map_stride, 0.0);
+    for (int t = 0; t < T; ++t) {
+        const TaskDesc& td = ctx->tasks[t];
+        for (int d = 0; d < td.dim; ++d)
+            for (int b = 0; b <= td.nbins; ++b)
+                edges[static_cast<size_t>(t) * g.map_stride + d * (td.nbins + 1) + b] =
+                    b == td.nbins ? 1.0 : static_cast<double>(b) / td.nbins;
+    }
+    TimeState ts{};
+    ts.a = 1.0;
+#define CKI(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return bail(fail(ctx, e_ == cudaErrorMemoryAllocation ? BEST_ERR_OOM : BEST_ERR_CUDA, "%s: %s", #x, cudaGetErrorString(e_))); } while (0)
+    CKI(dalloc(&ctx->d_sides, g.n_side));
+    CKI(dalloc(&ctx->d_tasks, T));
+    CKI(dalloc(&ctx->d_tconst, T));
+    CKI(dalloc(&ctx->d_acc, T));
+    CKI(dalloc(&ctx->d_sconst, S));
+    CKI(dalloc(&ctx->d_ts, 1));
+    CKI(dalloc(&ctx->d_edges, static_cast<size_t>(T) * g.map_stride));
+    CKI(dalloc(&ctx->d_knots, n));
+    CKI(dalloc(&ctx->d_knots32, n));
+    CKI(dalloc(&ctx->d_coef64, static_cast<size_t>(S) * (n - 1) * 4));
+    CKI(dalloc(&ctx->d_coef32, static_cast<size_t>(S) * (n - 1) * 4));
+    CKI(dalloc(&ctx->d_fgrid, static_cast<size_t>(S) * n));
+    CKI(dalloc(&ctx->d_mass0, S));
+    CKI(dalloc(&ctx->d_mass1, S));
+    CKI(dalloc(&ctx->d_k1, static_cast<size_t>(S) * n));
+    CKI(dalloc(&ctx->d_k2, static_cast<size_t>(S) * n));
+    CKI(dalloc(&ctx->d_fstar, static_cast<size_t>(S) * n));
+    CKI(dalloc(&ctx->d_prev, static_cast<size_t>(T)));
+    CKI(cudaMemset(ctx->d_prev, 0, sizeof(double) * T));
+    CKI(cudaMemcpy(ctx->d_sides, ctx->sides.data(), g.n_side * sizeof(SideDesc), cudaMemcpyHostToDevice));
+    CKI(cudaMemcpy(ctx->d_tasks, ctx->tasks.data(), T * sizeof(TaskDesc), cudaMemcpyHostToDevice));
+    CKI(cudaMemcpy(ctx->d_sconst, sconst.data(), S * sizeof(SpeciesConst), cudaMemcpyHostToDevice));
+    CKI(cudaMemcpy(ctx->d_ts, &ts, sizeof(TimeState), cudaMemcpyHostToDevice));
+    CKI(cudaMemcpy(ctx->d_edges, edges.data(), edges.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CKI(cudaMemcpy(ctx->d_knots, knots.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    CKI(cudaMemcpy(ctx->d_knots32, knots32.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    CKI(cudaMemcpy(ctx->d_mass0, m0.data(), S * sizeof(double), cudaMemcpyHostToDevice));
+    CKI(cudaMemcpy(ctx->d_mass1, m1.data(), S * sizeof(double), cudaMemcpyHostToDevice));
+    ctx->plans.resize(ctx->max_nitn);
+    int64_t part_max = 0;
+    for (int it = 0; it < ctx->max_nitn; ++it) {
+        best_status s = build_plan(ctx, it, ctx->plans[it]);
+        if (s != BEST_OK) return bail(s);
+        part_max = std::max(part_max, ctx->plans[it].partial_doubles);
+    }
+    CKI(dalloc(&ctx->d_partials, static_cast<size_t>(part_max)));
+    CKI(cudaDeviceSynchronize());
+#undef CKI
+    *out = ctx;
+    return BEST_OK;
+}
+
+best_status best_collision_eval(best_ctx* ctx, const double* f_dev, double t, double* C_dev, double* err_dev,
+                                void* stream) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    if (!f_dev || !C_dev) return fail(ctx, BEST_ERR_INVALID, "f_dev and C_dev must not be NULL");
+    if (!std::isfinite(t)) return fail(ctx, BEST_ERR_INVALID, "t must be finite");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ctx->launches = 0;
+    set_time_kernel<<<1, 32, 0, st>>>(ctx->geo, ctx->d_ts, nullptr, t, 0, ctx->d_mass0, ctx->d_mass1);
+    ctx->launches += 1;
+    return enqueue_sweep(ctx, f_dev, 0, C_dev, err_dev, st);
+}
+
+static best_status step_common(best_ctx* ctx, double* logf, double* t_dev, double* dt_dev, double* C_dev,
+                               void* stream, bool heun) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    if (!logf || !t_dev || !dt_dev) return fail(ctx, BEST_ERR_INVALID, "logf, t and dt must not be NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Geometry& g = ctx->geo;
+    ctx->launches = 0;
+    double* k1 = C_dev ? C_dev : ctx->d_k1;
+    set_time_kernel<<<1, 32, 0, st>>>(g, ctx->d_ts, t_dev, 0.0, 1, ctx->d_mass0, ctx->d_mass1);
+    ctx->launches += 1;
+    best_status s = enqueue_sweep(ctx, logf, 1, k1, nullptr, st);
+    if (s != BEST_OK) return s;
+    step_first_kernel<<<1, 1024, 0, st>>>(g, logf, ctx->d_fgrid, k1, t_dev, dt_dev, ctx->d_ts, ctx->d_fstar,
+                                          heun ? 1 : 0);
+    ctx->launches += 1;
+    if (heun) {
+        set_time_kernel<<<1, 32, 0, st>>>(g, ctx->d_ts, t_dev, 0.0, 2, ctx->d_mass0, ctx->d_mass1);
+        ctx->launches += 1;
+        s = enqueue_sweep(ctx, ctx->d_fstar, 0, ctx->d_k2, nullptr, st);
+        if (s != BEST_OK) return s;
+        heun_correct_kernel<<<1, 1024, 0, st>>>(g, logf, ctx->d_fstar, k1, ctx->d_k2, t_dev, dt_dev, ctx->d_ts);
+        ctx->launches += 1;
+    }
+    CK(cudaGetLastError());
+    return BEST_OK;
+}
+
+best_status best_step_euler(best_ctx* ctx, double* logf_dev, double* t_dev, double* dt_dev, double* C_dev,
+                            void* stream) {
+    return step_common(ctx, logf_dev, t_dev, dt_dev, C_dev, stream, false);
+}
+
+best_status best_step_heun(best_ctx* ctx, double* logf_dev, double* t_dev, double* dt_dev, double* C_dev,
+                           void* stream) {
+    return step_common(ctx, logf_dev, t_dev, dt_dev, C_dev, stream, true);
+}
+
+int32_t best_num_tasks(const best_ctx* ctx) { return ctx ? ctx->geo.n_tasks : 0; }
+int32_t best_num_side_integrals(const best_ctx* ctx) { return ctx ? ctx->geo.n_side : 0; }
+int64_t best_map_stride(const best_ctx* ctx) { return ctx ? ctx->geo.map_stride : 0; }
+int32_t best_last_launch_count(const best_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int64_t best_sweep_samples(const best_ctx* ctx, int32_t iteration) {
+    if (!ctx) return 0;
+    int64_t tot = 0;
+    for (const TaskDesc& td : ctx->tasks) {
+        if (iteration < 0) tot += td.neval * td.nitn;
+        else if (td.nitn > iteration) tot += td.neval;
+    }
+    return tot;
+}
+
+best_status best_get_task_results(best_ctx* ctx, double* mean, double* err, void* stream) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    std::vector<TaskAcc> acc(ctx->geo.n_tasks);
+    CK(cudaMemcpy(acc.data(), ctx->d_acc, acc.size() * sizeof(TaskAcc), cudaMemcpyDeviceToHost));
+    for (size_t t = 0; t < acc.size(); ++t) {
+        if (mean) mean[t] = acc[t].mean;
+        if (err) err[t] = acc[t].err;
+    }
+    return BEST_OK;
+}
+
+best_status best_get_maps(best_ctx* ctx, double* edges_host) {
+    if (!ctx || !edges_host) return fail(ctx, BEST_ERR_INVALID, "NULL argument");
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(edges_host, ctx->d_edges, sizeof(double) * ctx->geo.n_tasks * ctx->geo.map_stride,
+                  cudaMemcpyDeviceToHost));
+    return BEST_OK;
+}
+
+best_status best_set_maps(best_ctx* ctx, const double* edges_host) {
+    if (!ctx || !edges_host) return fail(ctx, BEST_ERR_INVALID, "NULL argument");
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(ctx->d_edges, edges_host, sizeof(double) * ctx->geo.n_tasks * ctx->geo.map_stride,
+                  cudaMemcpyHostToDevice));
+    return BEST_OK;
+}
+
+best_status best_get_call_counter(best_ctx* ctx, uint32_t* call) {
+    if (!ctx || !call) return fail(ctx, BEST_ERR_INVALID, "NULL argument");
+    CK(cudaDeviceSynchronize());
+    TimeState ts;
+    CK(cudaMemcpy(&ts, ctx->d_ts, sizeof(TimeState), cudaMemcpyDeviceToHost));
+    *call = ts.call;
+    return BEST_OK;
+}
+
+best_status best_set_call_counter(best_ctx* ctx, uint32_t call) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(reinterpret_cast<char*>(ctx->d_ts) + offsetof(TimeState, call), &call, sizeof(uint32_t),
+                  cudaMemcpyHostToDevice));
+    return BEST_OK;
+}
+
+best_status best_check(best_ctx* ctx, void* stream) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    CK(cudaGetLastError());
+    int32_t e = 0;
+    CK(cudaMemcpy(&e, reinterpret_cast<char*>(ctx->d_ts) + offsetof(TimeState, error), sizeof(int32_t),
+                  cudaMemcpyDeviceToHost));
+    if (e != 0) {
+        const int32_t z = 0;
+        CK(cudaMemcpy(reinterpret_cast<char*>(ctx->d_ts) + offsetof(TimeState, error), &z, sizeof(int32_t),
+                      cudaMemcpyHostToDevice));
+        return fail(ctx, BEST_ERR_NUMERIC, "non-positive or non-finite f, or a non-finite result");
+    }
+    return BEST_OK;
+}
+
+best_status best_profile_enable(best_ctx* ctx, int32_t enable) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    ctx->profiling = enable != 0;
+    ctx->ev_used = 0;
+    return BEST_OK;
+}
+
+best_status best_profile_read(best_ctx* ctx, double* sample_kernel_ms, int64_t* launches) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    double total = 0.0;
+    for (size_t k = 0; k + 1 < ctx->ev_used; k += 2) {
+        CK(cudaEventSynchronize(ctx->ev[k + 1]));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev[k], ctx->ev[k + 1]));
+        total += ms;
+    }
+    if (sample_kernel_ms) *sample_kernel_ms = total;
+    if (launches) *launches = static_cast<int64_t>(ctx->ev_used / 2);
+    ctx->ev_used = 0;
+    return BEST_OK;
+}
+
+const char* best_last_error(const best_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_error.c_str(); }
+
+void best_collision_destroy(best_ctx* ctx) {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    free_all(ctx);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,382 @@
+// Sample kernel of one VEGAS iteration over every active task (one
+// persistent launch for all grid points, species, processes and pinned
+// sides).  Included by eval_f32.cu and eval_f64.cu, which instantiate it for
+// FP32 and FP64 integrand arithmetic.
+//
+// Per sample (Sec. 2D, App. A):
+//   uniforms (Philox stream) -> VEGAS map -> (r, theta, phi) per integrated
+//   leg -> physical momenta p = r/a -> conserved leg from momentum
+//   conservation (Eq. (10)) -> energies -> Gaussian delta of Eq. (11) ->
+//   statistical factor of Eq. (5) with spline / Eq. (13) lookups -> weight of
+//   Eq. (12) -> compensated sums of w and w^2 and per-increment sums of w^2.
+//
+// Normalisation: the kernel accumulates w_n = w / (K * scale) with the FP64
+// per-task constants K = |M|^2 nb^D a^{-3(n-2)} / ((2pi)^{3(n-1)-4} 2^n
+// E_obs sigma sqrt(2pi)) and scale = f_obs, so that w_n is O(1) near
+// equilibrium and w_n^2 stays inside the FP32 range.  The map table in
+// shared memory holds, per dimension and increment, the scaled left edge Y0
+// and width dY of the physical variable, so y = Y0 + dY * (x nb - b) and the
+// Jacobian times the volume of the linear scaling is nb^D prod dY.
+#pragma once
+
+#include <cstdint>
+
+#include "internal.cuh"
+#include "philox.cuh"
+
+namespace best {
+
+template <typename R>
+struct Real2 { R y0, dy; };
+
+template <typename R> struct RMath;
+
+template <> struct RMath<float> {
+    static constexpr bool kF32 = true;
+    __device__ static __forceinline__ void sincos_(float x, float* s, float* c) { __sincosf(x, s, c); }
+    __device__ static __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+    __device__ static __forceinline__ float exp2_(float x) { return exp2f(x); }
+    __device__ static __forceinline__ float expm1_(float x) { return expm1f(x); }
+    __device__ static __forceinline__ float exp_(float x) { return __expf(x); }
+    __device__ static __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
+};
+
+template <> struct RMath<double> {
+    static constexpr bool kF32 = false;
+    __device__ static __forceinline__ void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
+    __device__ static __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+    __device__ static __forceinline__ double exp2_(double x) { return exp2(x); }
+    __device__ static __forceinline__ double expm1_(double x) { return expm1(x); }
+    __device__ static __forceinline__ double exp_(double x) { return exp(x); }
+    __device__ static __forceinline__ double rcp_(double x) { return 1.0 / x; }
+};
+
+// Compensated (Kahan) sum for the FP32 path; a plain sum for FP64.
+template <typename R>
+struct Acc {
+    R s = 0, c = 0;
+    __device__ __forceinline__ void add(R x) {
+        if constexpr (sizeof(R) == 4) {
+            const R y = x - c;
+            const R t = s + y;
+            c = (t - s) - y;
+            s = t;
+        } else {
+            s += x;
+        }
+    }
+    __device__ __forceinline__ double value() const {
+        return static_cast<double>(s) - static_cast<double>(c);
+    }
+};
+
+// Spline lookup tables of one species in shared memory.
+template <typename R>
+struct SplineView {
+    const R* coef;          // [n-1][4]: c0 + c1 t + c2 t^2 + c3 t^3, t = q - q_j
+    const R* knot;          // [n]
+};
+
+
+// Per-segment constants held in registers (uniform across the CTA).
+template <typename R, int NLEG>
+struct SegConst {
+    static constexpr int NI = NLEG - 2;
+    R pobs_sig;             // sigma_obs * p_obs (z component of the obs leg in p_cons)
+    R sgn_obs_E;            // s_obs * E_obs (its share of E_in - E_out)
+    R sig[NI];              // +-1: share of integrated leg j in p_cons
+    R sgnE[NI];             // +-1: initial / final leg j in E_in - E_out
+    R sgn_cons;             // same for the conserved leg
+    R m2[NI];               // masses^2
+    R m2c;
+    R ca[NI], cb[NI];       // statistical factor of leg j: ca + cb f
+    R cac, cbc;             // ... of the conserved leg
+    int spc[NI];            // species of leg j
+    int sp_cons;
+    R inv_a, a;
+    R c0;                   // obs factor / scale
+    R gauss_k;              // -log2(e) / (2 sigma^2)
+    R e_cut;
+    R eta_c;                // eta of the conserved leg (tail formula)
+    int fd_c;               // conserved leg is FD (clamp f <= 1)
+    int fd[NI];
+};
+
+// Cubic spline value at comoving q inside [q_0, q_{n-1}] (Sec. 3B).
+template <typename R>
+__device__ __forceinline__ R spline_eval(const SplineView<R>& sv, R q, const Geometry& g,
+                                         R inv_step, R q0, R inv_q0) {
+    // interval index from the grid formula (a guess within one interval of
+    // the exact one; the cubic pieces agree to C^2 at the knots)
+    int j;
+    if (g.log_spaced) {
+        j = static_cast<int>(__log2f(static_cast<float>(q * inv_q0)) * static_cast<float>(inv_step));
+    } else {
+        j = static_cast<int>(static_cast<float>((q - q0) * inv_step));
+    }
+    j = min(max(j, 0), g.n_grid - 2);
+    const R t = q - sv.knot[j];
+    const R* c = sv.coef + 4 * j;
+    R f = fma(fma(fma(c[3], t, c[2]), t, c[1]), t, c[0]);
+    return f > R(0) ? f : R(0);
+}
+
+template <typename R, int NLEG>
+__device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& seg,
+                                            const SideDesc& sd, const TaskDesc& td,
+                                            const TaskConst& tc, R* s_spline,
+                                            Real2<R>* s_map, R* s_hist, double* s_red,
+                                            const PhiloxKey& key) {
+    constexpr int NI = NLEG - 2;
+    constexpr int D = 3 * NI;
+    constexpr bool F32 = RMath<R>::kF32;
+    using SS = StreamShape<D, F32>;
+    constexpr int G = SS::kGroup;
+    const Geometry& g = P.geo;
+    const int nb = td.nbins;
+    const int tid = threadIdx.x;
+
+    // ---- map table of this task in shared memory ---------------------------
+    const double* edges = P.edges + static_cast<int64_t>(seg.task) * g.map_stride;
+    for (int k = tid; k < D * nb; k += blockDim.x) {
+        const int d = k / nb;
+        const int b = k - d * nb;
+        const double e0 = edges[d * (nb + 1) + b];
+        const double e1 = edges[d * (nb + 1) + b + 1];
+        double lo, sc;
+        switch (d % 3) {
+            case 0: lo = g.q_min; sc = g.q_max - g.q_min; break;   // r (comoving)
+            case 1: lo = 0.0; sc = kPi; break;                     // theta
+            default: lo = -kPi; sc = kTwoPi; break;                // phi - pi
+        }
+        Real2<R> v;
+        v.y0 = static_cast<R>(lo + sc * e0);
+        v.dy = static_cast<R>(sc * (e1 - e0));
+        s_map[k] = v;
+    }
+    // per-warp histograms: atomics from different warps never share an
+    // address, and the warps are summed in a fixed order at the end, so the
+    // training data do not depend on warp scheduling
+    const int map_elems = kMaxDim * g.nbins_max;
+    const int nwarps = blockDim.x >> 5;
+    for (int k = tid; k < nwarps * map_elems; k += blockDim.x) s_hist[k] = R(0);
+    R* w_hist = s_hist + (tid >> 5) * map_elems;
+
+    // ---- per-segment constants --------------------------------------------
+    SegConst<R, NLEG> C;
+    const TimeState& ts = *P.ts;
+    const int cons = sd.cons;
+    const bool cons_in = (sd.in_mask >> cons) & 1;
+    const R flip = cons_in ? R(-1) : R(1);     // p_cons = flip * sum_{k != c} s_k p_k
+    const bool is_loss = td.term == 1;
+    {
+        const R s_obs = ((sd.in_mask >> sd.obs) & 1) ? R(1) : R(-1);
+        C.pobs_sig = flip * s_obs * static_cast<R>(tc.p_obs);
+        C.sgn_obs_E = s_obs * static_cast<R>(tc.E_obs);
+    }
+#pragma unroll
+    for (int j = 0; j < NI; ++j) {
+        const int k = sd.integ[j];
+        const bool kin = (sd.in_mask >> k) & 1;
+        const bool own = (sd.own_mask >> k) & 1;
+        const int sp = sd.leg_species[k];
+        const double eta = P.sconst[sp].eta;
+        C.sig[j] = flip * (kin ? R(1) : R(-1));
+        C.sgnE[j] = kin ? R(1) : R(-1);
+        const double m = ts.mass[sp];
+        C.m2[j] = static_cast<R>(m * m);
+        const bool enh = own != is_loss;
+        C.ca[j] = enh ? R(1) : R(0);
+        C.cb[j] = enh ? static_cast<R>(eta) : R(1);
+        C.spc[j] = sp;
+        C.fd[j] = P.sconst[sp].stat == BEST_FD;
+    }
+    {
+        const int sp = sd.leg_species[cons];
+        const bool own = (sd.own_mask >> cons) & 1;
+        const double eta = P.sconst[sp].eta;
+        const double m = ts.mass[sp];
+        C.sgn_cons = cons_in ? R(1) : R(-1);
+        C.m2c = static_cast<R>(m * m);
+        const bool enh = own != is_loss;
+        C.cac = enh ? R(1) : R(0);
+        C.cbc = enh ? static_cast<R>(eta) : R(1);
+        C.sp_cons = sp;
+        C.eta_c = static_cast<R>(eta);
+        C.fd_c = P.sconst[sp].stat == BEST_FD;
+    }
+    C.a = static_cast<R>(ts.a);
+    C.inv_a = static_cast<R>(1.0 / ts.a);
+    // the observed leg's own cut (App. A) removes the whole task
+    C.c0 = tc.E_obs < g.e_cut ? R(0) : static_cast<R>(tc.obs_factor / tc.scale);
+    C.gauss_k = static_cast<R>(-1.4426950408889634 / (2.0 * sd.sigma * sd.sigma));
+    C.e_cut = static_cast<R>(g.e_cut);
+    const R nbR = static_cast<R>(nb);
+    const R q0 = static_cast<R>(g.q_min);
+    const R inv_q0 = static_cast<R>(1.0 / g.q_min);
+    const R qN = static_cast<R>(g.q_max);
+    const R inv_step = static_cast<R>(1.0 / (g.log_spaced ? g.log_step / 0.6931471805599453 : g.log_step));
+    const int ncoef = 4 * (g.n_grid - 1);
+    const R* knots = s_spline + g.n_species * ncoef;
+    const SpeciesConst* scst = P.sconst;
+    __syncthreads();
+
+    // ---- samples ------------------------------------------------------------
+    Acc<R> acc_w, acc_w2;
+    const int64_t N = td.neval;
+    const uint32_t task = static_cast<uint32_t>(seg.task);
+    for (int64_t grp = seg.g0 + tid; grp < seg.g1; grp += blockDim.x) {
+        R u[SS::kUniforms];
+        group_uniforms<D, F32, R>(u, grp, P.itn, ts.call, task, key.k);
+#pragma unroll
+        for (int sgi = 0; sgi < G; ++sgi) {
+            const int64_t s = grp * G + sgi;
+            if (s >= N) break;
+            const R* us = u + sgi * D;
+            // VEGAS map and scaling to (r, theta, phi - pi)
+            R y[D];
+            int bin[D];
+            R jac = R(1);
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const R t = us[d] * nbR;
+                int b = static_cast<int>(t);
+                b = b < nb - 1 ? b : nb - 1;
+                const Real2<R> e = s_map[d * nb + b];
+                y[d] = fma(e.dy, t - static_cast<R>(b), e.y0);
+                jac *= e.dy;
+                bin[d] = b;
+            }
+            // integrated legs
+            R px = R(0), py = R(0), pz = C.pobs_sig;
+            R dE = C.sgn_obs_E;
+            R meas = jac;
+            R stat = C.c0;
+            R rinvE_prod = R(1);
+            bool cut = false;
+#pragma unroll
+            for (int j = 0; j < NI; ++j) {
+                const R r = y[3 * j];
+                R st, ct, sp, cp;
+                RMath<R>::sincos_(y[3 * j + 1], &st, &ct);
+                RMath<R>::sincos_(y[3 * j + 2], &sp, &cp);   // angle phi - pi
+                const R p = r * C.inv_a;
+                const R ps = p * st;
+                const R sg = C.sig[j];
+                px = fma(-sg * ps, cp, px);                    // cos(phi) = -cos(phi - pi)
+                py = fma(-sg * ps, sp, py);
+                pz = fma(sg * p, ct, pz);
+                const R E2 = fma(p, p, C.m2[j]);
+                const R rE = RMath<R>::rsqrt_(E2);
+                const R E = E2 * rE;
+                cut |= E < C.e_cut;
+                dE = fma(C.sgnE[j], E, dE);
+                meas *= r * r * st;
+                rinvE_prod *= rE;
+                const SplineView<R> sv{s_spline + C.spc[j] * ncoef, knots};
+                R f = spline_eval<R>(sv, r, g, inv_step, q0, inv_q0);
+                if (C.fd[j]) f = f < R(1) ? f : R(1);
+                stat *= fma(C.cb[j], f, C.ca[j]);
+            }
+            // conserved leg (Eq. (10), App. A)
+            const R pc2 = fma(px, px, fma(py, py, pz * pz));
+            const R Ec2 = pc2 + C.m2c;
+            const R rEc = RMath<R>::rsqrt_(Ec2 > R(0) ? Ec2 : R(1e-30));
+            const R Ec = Ec2 * rEc;
+            cut |= Ec < C.e_cut;
+            dE = fma(C.sgn_cons, Ec, dE);
+            R fc;
+            {
+                const R qc = pc2 * (pc2 > R(0) ? RMath<R>::rsqrt_(pc2) : R(0)) * C.a;
+                if (qc >= q0 && qc <= qN) {
+                    const SplineView<R> sv{s_spline + C.sp_cons * ncoef, knots};
+                    fc = spline_eval<R>(sv, qc, g, inv_step, q0, inv_q0);
+                } else {
+                    const SpeciesConst& sc = scst[C.sp_cons];
+                    const R x = qc < q0 ? static_cast<R>(sc.tail_lo_a) + static_cast<R>(sc.tail_lo_b) * Ec
+                                        : static_cast<R>(sc.tail_hi_a) + static_cast<R>(sc.tail_hi_b) * Ec;
+                    const R den = C.eta_c == R(1) ? RMath<R>::expm1_(x) : RMath<R>::exp_(x) - C.eta_c;
+                    fc = den > R(0) ? R(1) / den : R(0);
+                }
+                if (C.fd_c) fc = fc < R(1) ? fc : R(1);
+            }
+            stat *= fma(C.cbc, fc, C.cac);
+            const R gauss = RMath<R>::exp2_(C.gauss_k * dE * dE);
+            R w = stat * meas * rinvE_prod * rEc * gauss;
+            w = cut ? R(0) : w;
+            const R w2 = w * w;
+            acc_w.add(w);
+            acc_w2.add(w2);
+#pragma unroll
+            for (int d = 0; d < D; ++d) atomicAdd(&w_hist[d * nb + bin[d]], w2);
+        }
+    }
+
+    // ---- segment reduction into its partial record (FP64) -------------------
+    double vw = acc_w.value(), vw2 = acc_w2.value();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        vw += __shfl_xor_sync(0xffffffffu, vw, o);
+        vw2 += __shfl_xor_sync(0xffffffffu, vw2, o);
+    }
+    const int warp = tid >> 5, lane = tid & 31;
+    if (lane == 0) {
+        s_red[2 * warp] = vw;
+        s_red[2 * warp + 1] = vw2;
+    }
+    __syncthreads();
+    double* part = P.partials + seg.part;
+    if (tid == 0) {
+        double a0 = 0.0, a1 = 0.0;
+        for (int k = 0; k < static_cast<int>(blockDim.x >> 5); ++k) {
+            a0 += s_red[2 * k];
+            a1 += s_red[2 * k + 1];
+        }
+        part[0] = a0;
+        part[1] = a1;
+    }
+    for (int k = tid; k < D * nb; k += blockDim.x) {
+        double v = 0.0;
+        for (int w = 0; w < nwarps; ++w) v += static_cast<double>(s_hist[w * map_elems + k]);
+        part[2 + k] = v;
+    }
+    __syncthreads();
+}
+
+template <typename R, int NMAX>
+__global__ void __launch_bounds__(kThreads, 1) eval_kernel(EvalParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* s_spline = reinterpret_cast<R*>(smem_raw);
+    const int nsp = P.smem_spline_elems;
+    Real2<R>* s_map = reinterpret_cast<Real2<R>*>(s_spline + ((nsp + 3) & ~3));
+    const int map_elems = kMaxDim * P.geo.nbins_max;
+    R* s_hist = reinterpret_cast<R*>(s_map + map_elems);      // [warps][map_elems]
+    double* s_red = reinterpret_cast<double*>(s_hist + (((kThreads / 32) * map_elems + 3) & ~3));
+
+    // spline tables of all species, once per CTA
+    {
+        const R* gc = static_cast<const R*>(P.coef);
+        const int ncoef = 4 * (P.geo.n_grid - 1) * P.geo.n_species;
+        for (int k = threadIdx.x; k < ncoef; k += blockDim.x) s_spline[k] = gc[k];
+        const R* gk = static_cast<const R*>(P.knots);
+        for (int k = threadIdx.x; k < P.geo.n_grid; k += blockDim.x) s_spline[ncoef + k] = gk[k];
+    }
+    const PhiloxKey key = philox_key(P.geo.seed);
+    const int s0 = P.cta_seg[blockIdx.x], s1 = P.cta_seg[blockIdx.x + 1];
+    for (int si = s0; si < s1; ++si) {
+        const Segment seg = P.segs[si];
+        const TaskDesc td = P.tasks[seg.task];
+        const SideDesc& sd = P.sides[td.si];
+        const TaskConst tc = P.tconst[seg.task];
+        __syncthreads();
+        switch (sd.n) {
+            case 3: if constexpr (NMAX >= 3) run_segment<R, 3>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, key); break;
+            case 4: if constexpr (NMAX >= 4) run_segment<R, 4>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, key); break;
+            case 5: if constexpr (NMAX >= 5) run_segment<R, 5>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, key); break;
+            case 6: if constexpr (NMAX >= 6) run_segment<R, 6>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, key); break;
+            default: break;
+        }
+    }
+}
+
+}  // namespace best

@@ -1,0 +1,135 @@
+// Device-side data layout of libbest shared by its translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/best.h"
+
+namespace best {
+
+constexpr int kMaxLegs = BEST_MAX_LEGS;
+constexpr int kMaxDim = 3 * (BEST_MAX_LEGS - 2);
+constexpr int kThreads = 256;          // threads per CTA of the sample kernel
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwoPi = 6.28318530717958647692;
+
+// One side integral of Eq. (7): a process, the side of the observed leg and
+// the observed species, with the roles of App. A already assigned.
+struct SideDesc {
+    int32_t n;              // legs
+    int32_t n_in;
+    int32_t obs;            // observed leg
+    int32_t cons;           // conserved leg
+    int32_t mult;           // n_S^a of Eq. (7)
+    int32_t species_obs;
+    int32_t process;
+    int32_t side;           // 0: observed leg initial, 1: final
+    int32_t leg_species[kMaxLegs];
+    int32_t integ[kMaxLegs];   // integrated legs in dimension order
+    int32_t own_mask;       // bit k: leg k on the observed side
+    int32_t in_mask;        // bit k: leg k initial
+    double coupling2;       // |M|^2
+    double sigma;           // sigma_E
+    double eta_obs;         // eta of the observed species
+};
+
+// One task: side integral x grid point x {gain, loss}.
+struct TaskDesc {
+    int32_t si;
+    int32_t point;
+    int32_t term;           // 0 gain, 1 loss
+    int32_t nitn;
+    int64_t neval;
+    int32_t dim;
+    int32_t nbins;
+    double alpha;
+};
+
+// Per-task values recomputed at the start of every sweep (FP64).
+struct TaskConst {
+    double K;               // constant factor of the weight (see eval kernel)
+    double scale;           // the kernel accumulates w / (K * scale)
+    double obs_factor;      // f_obs (loss) or 1 + eta f_obs (gain)
+    double f_obs;           // f_a(q_i), the grid value of the observed leg
+    double E_obs;           // energy of the observed leg
+    double p_obs;           // physical momentum of the observed leg
+};
+
+// Per-task VEGAS iteration combination accumulators (FP64).
+struct TaskAcc {
+    double sum_inv_var;     // sum 1/var_k
+    double sum_mean_inv_var;// sum mean_k/var_k
+    double sum_exact;       // sum of means of zero-variance iterations
+    double n_exact;         // number of zero-variance iterations
+    double mean;            // combined result (written by the assemble kernel)
+    double err;
+};
+
+// A contiguous piece of one task's samples handled by one CTA.
+struct Segment {
+    int32_t task;
+    int32_t pad_;
+    int64_t g0, g1;         // sample groups [g0, g1) of the task
+    int64_t part;           // offset (in doubles) of this segment's partial record
+};
+
+// Time-dependent scalars of the current sweep, resident on the device so
+// that whole steps can be captured in a CUDA graph.
+struct TimeState {
+    double t;               // time of the current sweep
+    double a;               // scale factor a(t)
+    double dt;              // step used by the current Euler / Heun step
+    double t_step;          // time at the start of the current step
+    double mass[BEST_MAX_SPECIES];
+    uint32_t call;          // evaluation counter (Philox counter word 2)
+    int32_t error;          // sticky numeric-error flag (BEST_ERR_NUMERIC)
+};
+
+// Spline table of one species (FP64 master copy; the FP32 copy mirrors it).
+struct SpeciesConst {
+    double eta;             // +1 BE, -1 FD, 0 MB
+    double tail_lo_a, tail_lo_b, tail_hi_a, tail_hi_b;
+    int32_t stat;
+    int32_t pad_;
+};
+
+// Everything the kernels of one context need, by value.
+struct Geometry {
+    int32_t n_grid;
+    int32_t log_spaced;
+    double q_min, q_max;
+    double log_step;        // ln(q_{j+1}/q_j) (log grid) or step (linear grid)
+    int32_t n_species;
+    int32_t n_tasks;
+    int32_t n_side;
+    int32_t map_stride;     // doubles per task in the edges array
+    int32_t nbins_max;
+    int32_t expansion;
+    double a0, t0;
+    double e_cut;
+    double eps_dt;
+    uint64_t seed;
+    int32_t tail_points;
+    int32_t precision;
+};
+
+// Arguments of the sample kernel.
+struct EvalParams {
+    Geometry geo;
+    const SideDesc* sides;
+    const TaskDesc* tasks;
+    const TaskConst* tconst;
+    const SpeciesConst* sconst;
+    const TimeState* ts;
+    const double* edges;        // [task][map_stride]
+    const Segment* segs;
+    const int32_t* cta_seg;     // segments of CTA b: [cta_seg[b], cta_seg[b+1])
+    const void* coef;           // [species][n-1][4] in R
+    const void* knots;          // [n] in R
+    double* partials;
+    uint32_t itn;
+    int32_t smem_spline_elems;  // R elements of spline coefficients + knots
+};
+
+}  // namespace best

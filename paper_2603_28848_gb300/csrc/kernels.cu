@@ -1,0 +1,403 @@
+// FP64 kernels around the sample kernel: time state, spline construction
+// (Sec. 3B), per-task constants, iteration reduction and VEGAS refinement,
+// assembly of C_a (Eq. (7)) and the Euler / Heun updates (Sec. 3C).
+#include <cmath>
+#include <cstdint>
+
+#include "internal.cuh"
+
+namespace best {
+
+// ---------------------------------------------------------------------------
+// Time state: a(t) (Sec. 3E) and m_s(t) (Sec. 3A) of the current sweep.
+// mode 0: t = t_host; mode 1: t = *t_dev; mode 2: t = *t_dev + state dt.
+// ---------------------------------------------------------------------------
+__global__ void set_time_kernel(Geometry g, TimeState* ts, const double* t_dev, double t_host,
+                                int mode, const double* mass0, const double* mass1) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double t = t_host;
+    if (mode == 1) t = *t_dev;
+    if (mode == 2) t = *t_dev + ts->dt;
+    ts->t = t;
+    ts->a = g.expansion ? g.a0 * sqrt(t / g.t0) : 1.0;
+    if (!(ts->a > 0.0) || !isfinite(ts->a)) ts->error = BEST_ERR_NUMERIC;
+    for (int s = 0; s < g.n_species; ++s) ts->mass[s] = mass0[s] + mass1[s] * t;
+}
+
+// ---------------------------------------------------------------------------
+// Spline of one species per CTA: not-a-knot cubic spline of (q_j, f_j)
+// through the tridiagonal system for the second derivatives M_j, with the
+// not-a-knot conditions (third derivative continuous at q_1 and q_{n-2})
+// eliminated into the first and last rows; then the interval coefficients
+// and the least-squares end fits of log(1/f + eta) against E(q/a) (Eq. (13)).
+// src_mode 0: f given; 1: f = exp(src) (log f).
+// Dynamic shared memory: 3 n doubles.
+// ---------------------------------------------------------------------------
+__global__ void spline_build_kernel(Geometry g, const double* __restrict__ src, int src_mode,
+                                    const double* __restrict__ knots, TimeState* ts,
+                                    SpeciesConst* sc, double* fgrid, double* coef64,
+                                    float* coef32) {
+    extern __shared__ double sh[];
+    const int n = g.n_grid;
+    const int s = blockIdx.x;
+    double* f = sh;
+    double* cp = sh + n;
+    double* M = sh + 2 * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double v = src[static_cast<int64_t>(s) * n + j];
+        if (src_mode == 1) v = exp(v);
+        if (!(v > 0.0) || !isfinite(v)) ts->error = BEST_ERR_NUMERIC;
+        f[j] = v;
+        fgrid[static_cast<int64_t>(s) * n + j] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // rows i = 1 .. n-2 : h_{i-1} M_{i-1} + 2 (h_{i-1} + h_i) M_i + h_i M_{i+1} = r_i
+        // M_0 = ((h0 + h1) M_1 - h0 M_2) / h1, M_{n-1} symmetric.
+        const int m = n - 2;    // unknowns M_1 .. M_{n-2}
+        auto h = [&](int i) { return knots[i + 1] - knots[i]; };
+        auto rhs = [&](int i) { return 6.0 * ((f[i + 1] - f[i]) / h(i) - (f[i] - f[i - 1]) / h(i - 1)); };
+        // Thomas algorithm on rows k = 0 .. m-1 (unknown M_{k+1}); cp holds the
+        // normalised upper diagonal, M[k+1] the normalised right-hand side.
+        for (int k = 0; k < m; ++k) {
+            const int i = k + 1;
+            double a = h(i - 1), b = 2.0 * (h(i - 1) + h(i)), c = h(i), d = rhs(i);
+            if (k == 0) {
+                const double h0 = h(0), h1 = h(1);
+                b += h0 * (h0 + h1) / h1;
+                c -= h0 * h0 / h1;
+                a = 0.0;
+            }
+            if (k == m - 1) {
+                const double hl = h(n - 2), hp = h(n - 3);
+                a -= hl * hl / hp;
+                b += hl * (hl + hp) / hp;
+                c = 0.0;
+            }
+            if (k > 0) {
+                const double den = b - a * cp[k - 1];
+                cp[k] = c / den;
+                M[k + 1] = (d - a * M[k]) / den;
+            } else {
+                cp[k] = c / b;
+                M[k + 1] = d / b;
+            }
+        }
+        for (int k = m - 2; k >= 0; --k) M[k + 1] -= cp[k] * M[k + 2];
+        const double h0 = h(0), h1 = h(1);
+        M[0] = ((h0 + h1) * M[1] - h0 * M[2]) / h1;
+        const double hl = h(n - 2), hp = h(n - 3);
+        M[n - 1] = ((hl + hp) * M[n - 2] - hl * M[n - 3]) / hp;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n - 1; j += blockDim.x) {
+        const double hj = knots[j + 1] - knots[j];
+        const double c0 = f[j];
+        const double c1 = (f[j + 1] - f[j]) / hj - hj * (2.0 * M[j] + M[j + 1]) / 6.0;
+        const double c2 = 0.5 * M[j];
+        const double c3 = (M[j + 1] - M[j]) / (6.0 * hj);
+        const int64_t o = (static_cast<int64_t>(s) * (n - 1) + j) * 4;
+        coef64[o + 0] = c0; coef64[o + 1] = c1; coef64[o + 2] = c2; coef64[o + 3] = c3;
+        coef32[o + 0] = static_cast<float>(c0); coef32[o + 1] = static_cast<float>(c1);
+        coef32[o + 2] = static_cast<float>(c2); coef32[o + 3] = static_cast<float>(c3);
+    }
+    if (threadIdx.x == 0) {
+        const double eta = sc[s].eta;
+        const double m = ts->mass[s];
+        const double a = ts->a;
+        const int K = g.tail_points;
+        for (int end = 0; end < 2; ++end) {
+            double xm = 0.0, ym = 0.0;
+            for (int k = 0; k < K; ++k) {
+                const int j = end == 0 ? k : n - K + k;
+                const double p = knots[j] / a;
+                xm += sqrt(p * p + m * m);
+                ym += log(1.0 / f[j] + eta);
+            }
+            xm /= K;
+            ym /= K;
+            double sxy = 0.0, sxx = 0.0;
+            for (int k = 0; k < K; ++k) {
+                const int j = end == 0 ? k : n - K + k;
+                const double p = knots[j] / a;
+                const double x = sqrt(p * p + m * m) - xm;
+                sxy += x * (log(1.0 / f[j] + eta) - ym);
+                sxx += x * x;
+            }
+            const double b = sxy / sxx;
+            const double a0 = ym - b * xm;
+            if (end == 0) { sc[s].tail_lo_a = a0; sc[s].tail_lo_b = b; }
+            else { sc[s].tail_hi_a = a0; sc[s].tail_hi_b = b; }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-task constants of the sweep and reset of the iteration accumulators.
+// ---------------------------------------------------------------------------
+// Accumulation scale: the kernel sums w_n = w / (K scale).  With a previous
+// estimate I of the task (last sweep) scale = |I| / K, so that w_n averages
+// to about 1; otherwise scale = f_obs.  The scale is kept within 2^+-100 of
+// the observed-leg factor so that obs_factor / scale fits in FP32.
+__device__ inline double clamp_scale(double scale, double obs_factor) {
+    if (!(obs_factor > 0.0)) return scale > 0.0 && isfinite(scale) ? scale : 1.0;
+    const double lo = obs_factor * 7.888609052210118e-31, hi = obs_factor * 1.2676506002282294e30;
+    if (!(scale > 0.0) || !isfinite(scale)) return obs_factor;
+    return scale < lo ? lo : (scale > hi ? hi : scale);
+}
+
+__global__ void prepare_kernel(Geometry g, const SideDesc* __restrict__ sides,
+                               const TaskDesc* __restrict__ tasks, const double* __restrict__ knots,
+                               const double* __restrict__ fgrid, const TimeState* ts,
+                               const double* __restrict__ prev, TaskConst* tconst, TaskAcc* acc) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.n_tasks) return;
+    const TaskDesc td = tasks[t];
+    const SideDesc& sd = sides[td.si];
+    const double a = ts->a;
+    const double m = ts->mass[sd.species_obs];
+    const double p = knots[td.point] / a;
+    const double E = sqrt(p * p + m * m);
+    const int n = sd.n;
+    const int D = 3 * (n - 2);
+    const double nbD = pow(static_cast<double>(td.nbins), D);
+    const double two_pi_pow = pow(kTwoPi, 3 * (n - 1) - 4);
+    const double a3 = pow(a, -3.0 * (n - 2));
+    TaskConst c;
+    c.p_obs = p;
+    c.E_obs = E;
+    c.f_obs = fgrid[static_cast<int64_t>(sd.species_obs) * g.n_grid + td.point];
+    c.K = sd.coupling2 * nbD * a3 /
+          (two_pi_pow * ldexp(1.0, n) * E * sd.sigma * sqrt(kTwoPi));
+    c.obs_factor = td.term == 1 ? c.f_obs : 1.0 + sd.eta_obs * c.f_obs;
+    const double est = prev[t];
+    c.scale = clamp_scale(est > 0.0 && c.K > 0.0 ? est / c.K : (c.f_obs > 0.0 ? c.f_obs : 1.0), c.obs_factor);
+    tconst[t] = c;
+    TaskAcc z;
+    z.sum_inv_var = 0.0; z.sum_mean_inv_var = 0.0; z.sum_exact = 0.0; z.n_exact = 0.0;
+    z.mean = 0.0; z.err = 0.0;
+    acc[t] = z;
+}
+
+// ---------------------------------------------------------------------------
+// End of one VEGAS iteration, one CTA per active task: sum the task's
+// segment records in a fixed order (deterministic), form the iteration
+// estimate and its variance, add them to the combination accumulators, and
+// refine the map (Lepage): smooth the per-increment sums of w^2 with the
+// (7,1)/8, (1,6,1)/8, (1,7)/8 stencil, normalise, compress with
+// ((1-d)/ln(1/d))^alpha, and re-partition into equal shares of the
+// compressed weight.  A normalised share below 1e-30 counts as an empty
+// increment (weight 0, like an exact zero) so that the map does not depend on
+// where underflow of w^2 falls.  Dynamic shared memory: (kMaxDim * nbins_max
+// + 2) doubles.
+// ---------------------------------------------------------------------------
+__global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
+                              const TaskDesc* __restrict__ tasks, const TaskConst* tconst,
+                              const int32_t* __restrict__ active, const int32_t* __restrict__ task_seg,
+                              const Segment* __restrict__ segs, const double* __restrict__ partials,
+                              double* edges, TaskAcc* acc, TaskConst* tconst_next) {
+    extern __shared__ double hist[];
+    const int t = active[blockIdx.x];
+    const TaskDesc td = tasks[t];
+    const int nb = td.nbins;
+    const int D = td.dim;
+    const int s0 = task_seg[blockIdx.x], s1 = task_seg[blockIdx.x + 1];
+    const int L = 2 + D * nb;
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+        double v = 0.0;
+        for (int s = s0; s < s1; ++s) v += partials[segs[s].part + k];
+        hist[k] = v;
+    }
+    __syncthreads();
+    // Sum w^2 >= (sum w)^2 / N holds exactly; if the computed sums violate it,
+    // squares of tiny weights underflowed (FP32 path with a poor scale): the
+    // iteration is discarded (no estimate, no refinement) and only the scale
+    // is corrected for the next iteration.
+    const double N = static_cast<double>(td.neval);
+    const double mean_n = hist[0] / N;
+    const bool underflow = hist[1] / N < (1.0 - 1e-6) * mean_n * mean_n;
+    if (threadIdx.x == 0) {
+        const TaskConst c = tconst[t];
+        double var_n = N > 1.0 ? (hist[1] / N - mean_n * mean_n) / (N - 1.0) : 0.0;
+        var_n = var_n > 0.0 ? var_n : 0.0;
+        const double sc = c.K * c.scale;
+        const double mean = mean_n * sc;
+        const double var = var_n * sc * sc;
+        if (!underflow) {
+            TaskAcc& A = acc[t];
+            if (var > 0.0) {
+                A.sum_inv_var += 1.0 / var;
+                A.sum_mean_inv_var += mean / var;
+            } else {
+                A.sum_exact += mean;
+                A.n_exact += 1.0;
+            }
+        }
+        if (mean_n != 0.0) tconst_next[t].scale = clamp_scale(fabs(mean_n) * c.scale, c.obs_factor);
+    }
+    if (underflow) return;
+    if (threadIdx.x < D) {
+        const int d = threadIdx.x;
+        const double* dd = hist + 2 + d * nb;
+        double* e = edges + static_cast<int64_t>(t) * g.map_stride + d * (nb + 1);
+        bool any = false;
+        for (int b = 0; b < nb; ++b) any |= dd[b] > 0.0;
+        if (any) {
+            double sm[256];
+            double om[256];
+            double tot = 0.0;
+            for (int b = 0; b < nb; ++b) {
+                double v;
+                if (nb == 1) v = dd[0];
+                else if (b == 0) v = (7.0 * dd[0] + dd[1]) / 8.0;
+                else if (b == nb - 1) v = (dd[nb - 2] + 7.0 * dd[nb - 1]) / 8.0;
+                else v = (dd[b - 1] + 6.0 * dd[b] + dd[b + 1]) / 8.0;
+                sm[b] = v;
+                tot += v;
+            }
+            double otot = 0.0;
+            for (int b = 0; b < nb; ++b) {
+                const double v = sm[b] / tot;
+                double o;
+                if (v < 1e-30) o = 0.0;            // numerically empty increment
+                else if (v >= 1.0) o = 1.0;
+                else o = pow((1.0 - v) / -log(v), td.alpha);
+                om[b] = o;
+                otot += o;
+            }
+            const double target = otot / nb;
+            double old[257];
+            for (int b = 0; b <= nb; ++b) old[b] = e[b];
+            double accw = 0.0;
+            int i = 0;
+            for (int k = 1; k < nb; ++k) {
+                const double goal = k * target;
+                while (i < nb - 1 && accw + om[i] < goal) {
+                    accw += om[i];
+                    ++i;
+                }
+                double fr = om[i] > 0.0 ? (goal - accw) / om[i] : 0.0;
+                fr = fr < 0.0 ? 0.0 : (fr > 1.0 ? 1.0 : fr);
+                e[k] = old[i] + fr * (old[i + 1] - old[i]);
+            }
+            e[0] = 0.0;
+            e[nb] = 1.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Combination of the iterations per task (inverse-variance weights; zero-
+// variance iterations are exact) and assembly of Eq. (7):
+// C_a(p_i) = sum_sides mult (I_gain - I_loss), err^2 = sum mult^2
+// (sigma_gain^2 + sigma_loss^2).  One thread per (species, grid point), each
+// owning the tasks observed there; thread 0 advances the evaluation counter.
+// ---------------------------------------------------------------------------
+__device__ inline void combine_task(TaskAcc& A) {
+    if (A.n_exact > 0.0) {
+        A.mean = A.sum_exact / A.n_exact;
+        A.err = 0.0;
+    } else if (A.sum_inv_var > 0.0) {
+        A.mean = A.sum_mean_inv_var / A.sum_inv_var;
+        A.err = sqrt(1.0 / A.sum_inv_var);
+    } else {
+        A.mean = 0.0;
+        A.err = 0.0;
+    }
+}
+
+__global__ void assemble_kernel(Geometry g, const SideDesc* __restrict__ sides, TaskAcc* acc,
+                                TimeState* ts, double* C, double* err, double* prev) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = g.n_grid;
+    if (k < g.n_species * n) {
+        const int s = k / n;
+        const int i = k - s * n;
+        double c = 0.0, v = 0.0;
+        for (int si = 0; si < g.n_side; ++si) {
+            const SideDesc& sd = sides[si];
+            if (sd.species_obs != s) continue;
+            const int tg = (si * n + i) * 2;
+            TaskAcc& G = acc[tg];
+            TaskAcc& L = acc[tg + 1];
+            combine_task(G);
+            combine_task(L);
+            if (G.mean != 0.0) prev[tg] = fabs(G.mean);
+            if (L.mean != 0.0) prev[tg + 1] = fabs(L.mean);
+            c += sd.mult * (G.mean - L.mean);
+            v += static_cast<double>(sd.mult) * sd.mult * (G.err * G.err + L.err * L.err);
+        }
+        if (!isfinite(c) || !isfinite(v)) ts->error = BEST_ERR_NUMERIC;
+        C[k] = c;
+        if (err) err[k] = sqrt(v);
+    }
+    if (k == 0) ts->call += 1u;
+}
+
+// ---------------------------------------------------------------------------
+// Time stepping (Sec. 3C), one CTA of 1024 threads over all species and grid
+// points.  max |C/f| is reduced in FP64 and the step used is
+// dt = min(dt_requested, eps / max |C/f|) (Eq. (16)).
+// ---------------------------------------------------------------------------
+__device__ double block_max(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0) red[0] = v;
+    }
+    __syncthreads();
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// Euler (Eq. (14)) or the Heun predictor: dt from k1, logf_out = logf + dt k1/f.
+// heun != 0: writes f* = exp(logf + dt k1/f) to fstar and leaves logf alone.
+__global__ void step_first_kernel(Geometry g, double* logf, const double* __restrict__ fgrid,
+                                  const double* __restrict__ k1, double* t_dev, double* dt_dev,
+                                  TimeState* ts, double* fstar, int heun) {
+    __shared__ double red[32];
+    const int total = g.n_species * g.n_grid;
+    double mx = 0.0;
+    for (int k = threadIdx.x; k < total; k += blockDim.x) mx = fmax(mx, fabs(k1[k] / fgrid[k]));
+    mx = block_max(mx, red);
+    double dt = *dt_dev;
+    if (mx > 0.0) dt = fmin(dt, g.eps_dt / mx);
+    for (int k = threadIdx.x; k < total; k += blockDim.x) {
+        const double step = dt * k1[k] / fgrid[k];
+        if (heun) fstar[k] = exp(logf[k] + step);
+        else logf[k] += step;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ts->dt = dt;
+        ts->t_step = *t_dev;
+        if (!heun) {
+            *t_dev += dt;
+            *dt_dev = dt;
+        }
+        if (!isfinite(dt)) ts->error = BEST_ERR_NUMERIC;
+    }
+}
+
+// Heun corrector (Eq. (15)): logf += dt/2 (k1/f + k2/f*), f = exp(logf)
+// (log f is left untouched by the predictor).
+__global__ void heun_correct_kernel(Geometry g, double* logf, const double* __restrict__ fstar, const double* __restrict__ k1,
+                                    const double* __restrict__ k2, double* t_dev, double* dt_dev,
+                                    TimeState* ts) {
+    const int total = g.n_species * g.n_grid;
+    const double dt = ts->dt;
+    for (int k = threadIdx.x; k < total; k += blockDim.x)
+        logf[k] += 0.5 * dt * (k1[k] / exp(logf[k]) + k2[k] / fstar[k]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *t_dev = ts->t_step + dt;
+        *dt_dev = dt;
+    }
+}
+
+}  // namespace best

@@ -1,0 +1,205 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+FP64 path: identical Philox samples, so every task's combined estimate and
+every refined VEGAS map agree with the oracle to 1e-5 relative (the bar for
+the FP64 path); in practice the difference is rounding order only.
+FP32 path: the same uniform stream in FP32 form; every task agrees with the
+oracle run on that stream within 3 standard errors, and C agrees within
+3 sigma of the combined error.
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import workloads as W
+from tests._helpers import oracle_sweep, rel_diff, side_integrals, task_arrays
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-5
+
+
+def _gpu(problem, precision):
+    from paper_2603_28848_gb300 import Collision
+    return Collision(problem, precision)
+
+
+def _f(f0):
+    import torch
+    return torch.tensor(np.ascontiguousarray(f0), dtype=torch.float64, device="cuda")
+
+
+def _significance(problem, om):
+    """Per task: the largest |mean| among the tasks of the same side integral
+    and term; tasks 1e12 below it do not contribute to C at any grid point."""
+    n = problem.grid.n
+    m = np.abs(om).reshape(-1, n, 2)
+    return np.repeat(np.max(m, axis=1, keepdims=True), n, axis=1).reshape(-1)
+
+
+def _compare_fp64(problem, f0, t=0.0, sweeps=1):
+    """Run `sweeps` consecutive evaluations on both sides (maps and the call
+    counter carry over) and compare every task, C per grid point and the maps."""
+    col = _gpu(problem, W.PREC_FP64)
+    f = _f(f0)
+    state = None
+    for _ in range(sweeps):
+        C, err = col.eval(f, t)
+        Co, erro, detail, state = oracle_sweep(problem, f0, t, "f64", state)
+    col.check()
+    mean, terr = col.task_results()
+    om, oe = task_arrays(detail, col.n_tasks)
+    assert np.all(np.isfinite(om)) and np.all(np.isfinite(mean))
+    sig = _significance(problem, om)
+    bad = np.abs(mean - om) > FP64_TOL * np.abs(om) + 1e-12 * sig
+    assert not np.any(bad), [(k, mean[k], om[k]) for k in np.flatnonzero(bad)[:5]]
+    bad_e = np.abs(terr - oe) > 1e-4 * np.abs(oe) + 1e-12 * sig
+    assert not np.any(bad_e), [(k, terr[k], oe[k]) for k in np.flatnonzero(bad_e)[:5]]
+    # C per grid point against the scale of its gain and loss terms
+    n = problem.grid.n
+    scale = np.zeros_like(Co)
+    for k, si in enumerate(side_integrals(problem)):
+        for i in range(n):
+            tg = (k * n + i) * 2
+            scale[si.species, i] += si.mult * (abs(om[tg]) + abs(om[tg + 1]))
+    Cg = C.cpu().numpy()
+    assert np.all(np.abs(Cg - Co) <= FP64_TOL * scale + 1e-300)
+    # Maps of significant tasks.  Refinement amplifies rounding differences
+    # over iterations (1e-9 after one, ~1e-6 after five), hence 1e-4; tasks
+    # 1e12 below their side integral's scale can have every oracle weight
+    # underflow to 0 (no refinement there) and are skipped.
+    maps = col.maps()
+    for tid, edges in state.maps.items():
+        if abs(om[tid]) <= 1e-12 * sig[tid]:
+            continue
+        D, nb1 = edges.shape
+        got = maps[tid][: D * nb1].reshape(D, nb1)
+        assert np.max(np.abs(got - edges)) < 1e-4, tid
+    col.close()
+    return Cg, Co
+
+
+def test_c1_maxwell_fp64_full_size():
+    """The MB 2 -> 2 workload at its full size (32 points, 5 x 1e4)."""
+    prob, f0 = W.c1_maxwell_2to2()
+    _compare_fp64(prob, f0)
+
+
+def test_c1_two_sweeps_reuse_maps():
+    """Maps and the evaluation counter carry over between sweeps (Sec. 3D)."""
+    prob, f0 = W.c1_maxwell_2to2(n=12, neval=3001, nitn=2)
+    _compare_fp64(prob, f0, sweeps=2)
+
+
+def test_bose_massless_ragged_fp64():
+    """Massless BE with the IR-enhanced low end, a ragged budget, 17
+    increments per dimension and a non-default alpha."""
+    prob, f0 = W.c2_bose_2to2(n=10, neval=2999, nitn=3)
+    prob = replace(prob, processes=tuple(replace(p, nbins=17, alpha=0.8) for p in prob.processes))
+    _compare_fp64(prob, f0)
+
+
+def test_cannibal_2to3_both_sides_fp64():
+    prob, f0 = W.c3_cannibal_2to3(n=8, neval=2001, nitn=2, with_2to2=True)
+    _compare_fp64(prob, f0)
+
+
+def test_multi_species_expansion_uneven_fp64():
+    """Two species, three processes (2->2, 2->3, 3->2), FRW expansion with a
+    time-dependent mass and uneven per-point budgets, evaluated at t = 2."""
+    prob, f0 = W.c4_multi_species(n=8, nmin=500, nmax=3000, nitn=2)
+    _compare_fp64(prob, f0, t=2.0)
+
+
+def test_2to4_fp64():
+    prob, f0 = W.c5_2to4(n=6, neval=1500, nitn=2)
+    _compare_fp64(prob, f0)
+
+
+def test_linear_grid_minimal_fp64():
+    """Smallest grid (4 points, linear), 2 increments, 2 tail points."""
+    g = W.Grid(4, 0.5, 6.0, False)
+    prob = W.Problem(g, (W.Species("phi", W.STAT_FD, 0.7),),
+                     (W.Process("pp", (0, 0), (0, 0), 0.8, 0.05, 777, 2, 0.5, 2),), seed=42, tail_points=2)
+    q = np.linspace(0.5, 6.0, 4)
+    f0 = (1.0 / (np.exp(np.sqrt(q * q + 0.49) / 1.3) + 1.0))[None, :]
+    _compare_fp64(prob, f0)
+
+
+def _compare_fp32(problem, f0, t=0.0):
+    """FP32 path against the oracle on the same (FP32-form) uniform stream.
+
+    One iteration: the samples are identical, so the tasks differ by FP32
+    rounding only (checked to 5e-3 relative).  Several iterations: the FP32
+    and FP64 training data refine the maps slightly differently and the maps
+    drift apart on high-variance tasks, so the later iterations are only
+    partly correlated; the check is then statistical: at least 95% of the
+    significant tasks within 3 combined standard errors, none beyond 6."""
+    one = problem.with_budget(nitn=1)
+    col = _gpu(one, W.PREC_FP32)
+    col.eval(_f(f0), t)
+    mean, _ = col.task_results()
+    _, _, detail, _ = oracle_sweep(one, f0, t, "f32")
+    om, _ = task_arrays(detail, col.n_tasks)
+    sig = _significance(one, om)
+    keep = np.abs(om) > 1e-8 * sig
+    assert np.max(rel_diff(mean[keep], om[keep])) < 5e-3
+    col.close()
+
+    col = _gpu(problem, W.PREC_FP32)
+    C, err = col.eval(_f(f0), t)
+    col.check()
+    Co, erro, detail, state = oracle_sweep(problem, f0, t, "f32")
+    mean, terr = col.task_results()
+    om, oe = task_arrays(detail, col.n_tasks)
+    sig = _significance(problem, om)
+    keep = np.abs(om) > 1e-8 * sig
+    z = np.abs(mean - om)[keep] / np.sqrt(terr ** 2 + oe ** 2)[keep]
+    assert np.mean(z < 3.0) >= 0.95 and np.max(z) < 6.0, (np.mean(z < 3.0), np.max(z))
+    zc = np.abs(C.cpu().numpy() - Co) / np.sqrt(err.cpu().numpy() ** 2 + erro ** 2 + 1e-300)
+    assert np.mean(zc < 3.0) >= 0.95 and np.max(zc) < 6.0
+    col.close()
+
+
+def test_c1_fp32_within_three_sigma():
+    prob, f0 = W.c1_maxwell_2to2()
+    _compare_fp32(prob, f0)
+
+
+def test_2to3_fp32_within_three_sigma():
+    prob, f0 = W.c3_cannibal_2to3(n=8, neval=4001, nitn=2)
+    _compare_fp32(prob, f0)
+
+
+def test_multi_species_fp32_within_three_sigma():
+    prob, f0 = W.c4_multi_species(n=8, nmin=1000, nmax=4000, nitn=2)
+    _compare_fp32(prob, f0, t=2.0)
+
+
+def test_fp32_against_fp64_oracle_stream():
+    """FP32 path against the FP64 oracle on the FP64 stream (independent
+    samples): agreement within 3 sigma of the combined error."""
+    prob, f0 = W.c1_maxwell_2to2(n=12, neval=20000, nitn=4)
+    col = _gpu(prob, W.PREC_FP32)
+    C, err = col.eval(_f(f0), 0.0)
+    mean, terr = col.task_results()
+    Co, erro, detail, _ = oracle_sweep(prob, f0, 0.0, "f64")
+    om, oe = task_arrays(detail, col.n_tasks)
+    z = np.abs(mean - om) / np.sqrt(terr ** 2 + oe ** 2)
+    assert np.mean(z < 3.0) >= 0.95 and np.all(z < 6.0)
+
+
+def test_deterministic_replay():
+    """The static partition and fixed-order reductions make a sweep bitwise
+    reproducible: two fresh contexts give identical results."""
+    prob, f0 = W.c3_cannibal_2to3(n=8, neval=5000, nitn=2)
+    out = []
+    for _ in range(2):
+        col = _gpu(prob, W.PREC_FP32)
+        C, _ = col.eval(_f(f0), 0.0)
+        C2, _ = col.eval(_f(f0), 0.0)
+        out.append((col.task_results()[0], C.cpu().numpy(), C2.cpu().numpy(), col.maps()))
+        col.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)

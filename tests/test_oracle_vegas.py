@@ -116,3 +116,21 @@ def test_combine_inverse_variance():
     assert np.isclose(m, 2.0) and np.isclose(e * e, 0.8)
     m, e = vegas.combine([0.0, 0.0], [0.0, 0.0])
     assert m == 0.0 and e == 0.0
+
+
+def test_refine_is_scale_invariant():
+    """Training data that differ by a constant factor give the same map,
+    even when the factor moves w^2 across the floating-point underflow
+    threshold (the empty-share reading)."""
+    rng = np.random.default_rng(5)
+    e = vegas.uniform_edges(1, 50)[0]
+    x = rng.uniform(size=4000)
+    w = np.exp(-((x - 0.37) / 0.004) ** 2 / 2)          # a narrow peak: most w^2 underflow
+    b = np.minimum((x * 50).astype(int), 49)
+    ref = None
+    for sc in (1.0, 1e-5, 1e5, 1e20, 1e-20):
+        d = np.bincount(b, weights=(sc * w) ** 2, minlength=50)
+        new = vegas.refine_1d(e, d, 0.5)
+        if ref is None:
+            ref = new
+        assert np.max(np.abs(new - ref)) < 1e-12
