@@ -449,7 +449,12 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
         if (ctx->eval_smem > static_cast<size_t>(max_optin))
             return bail(fail(ctx, BEST_ERR_INVALID, "spline and map tables need %zu B of shared memory (max %d)",
                              ctx->eval_smem, max_optin));
-        if (cudaFuncSetAttribute(ctx->eval_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        // raise, never lower, the kernel's limit: other live contexts may need more
+        cudaFuncAttributes fa{};
+        if (cudaFuncGetAttributes(&fa, ctx->eval_fn) != cudaSuccess)
+            return bail(fail(ctx, BEST_ERR_CUDA, "cannot query the sample kernel"));
+        if (static_cast<size_t>(fa.maxDynamicSharedSizeBytes) < ctx->eval_smem &&
+            cudaFuncSetAttribute(ctx->eval_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(ctx->eval_smem)) != cudaSuccess)
             return bail(fail(ctx, BEST_ERR_CUDA, "cannot set shared memory of the sample kernel"));
         int occ = 0;
@@ -457,7 +462,10 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
             return bail(fail(ctx, BEST_ERR_CUDA, "sample kernel does not fit on an SM"));
         ctx->grid = nsm * occ;
         ctx->spline_smem = 3 * sizeof(double) * g.n_grid;
-        if (cudaFuncSetAttribute(reinterpret_cast<const void*>(&spline_build_kernel),
+        if (cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(&spline_build_kernel)) != cudaSuccess)
+            return bail(fail(ctx, BEST_ERR_CUDA, "cannot query the spline kernel"));
+        if (static_cast<size_t>(fa.maxDynamicSharedSizeBytes) < ctx->spline_smem &&
+            cudaFuncSetAttribute(reinterpret_cast<const void*>(&spline_build_kernel),
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(ctx->spline_smem)) != cudaSuccess)
             return bail(fail(ctx, BEST_ERR_CUDA, "cannot set shared memory of the spline kernel"));
         ctx->refine_smem = sizeof(double) * (static_cast<size_t>(kMaxDim) * nb_max + 2);
