@@ -202,6 +202,40 @@ best_status best_profile_read(best_ctx* ctx, double* sample_kernel_ms, int64_t* 
 /* Number of kernels the last eval / Euler / Heun call enqueued. */
 int32_t best_last_launch_count(const best_ctx* ctx);
 
+/*
+ * One VEGAS iteration of one task without allocating device memory.  The
+ * paper has no counterpart: this serves callers that cannot call cudaMalloc
+ * at the point of use, for example code running inside CUDA-graph capture,
+ * or a host application whose device memory is handed out only by its own
+ * pool allocator.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine, and needs no context.
+ *
+ * Inputs: cfg (host, as for best_collision_init; precision selects the
+ * FP32 or FP64 sample kernel), task (task id in the enumeration of
+ * best_get_task_results), f_dev [n_species * n_grid] FP64, time t (host),
+ * edges_dev (device FP64, the task's VEGAS map, [D][nbins + 1] with
+ * D = 3 (n_legs - 2); read only), the iteration index and evaluation
+ * counter that enter the Philox counter.  Output out_dev (device FP64,
+ * 2 + D * nbins values): out[0] = sum of the task's sample weights w,
+ * out[1] = sum of w^2, out[2 + d*nbins + b] = sum of w^2 over the samples
+ * falling in increment b of dimension d (the training data of the map).
+ * The estimate of the iteration is out[0] / neval with variance
+ * (out[1]/neval - mean^2) / (neval - 1).
+ *
+ * Device scratch comes from one static array of about 3.5 MiB that every
+ * GPU loading the library holds until the process exits.  Limits: grid.n
+ * <= 512, nbins <= 64; larger sizes return BEST_ERR_INVALID with a message
+ * in best_last_error(NULL).  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents: calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race and give wrong results; order
+ * them on one stream.
+ */
+best_status best_vegas_iteration_noalloc(const best_config* cfg, int32_t task, const double* f_dev,
+                                         double t, const double* edges_dev, uint32_t iteration,
+                                         uint32_t call, double* out_dev, void* stream);
+
 /* Description of the last failure on ctx (or of the last failed init when
  * ctx is NULL); never NULL. */
 const char* best_last_error(const best_ctx* ctx);

@@ -60,6 +60,8 @@ SIGNATURES = {
     "best_profile_read": ([c_void_p, POINTER(c_double), POINTER(c_int64)], c_int32),
     "best_last_error": ([c_void_p], c_char_p),
     "best_collision_destroy": ([c_void_p], None),
+    "best_vegas_iteration_noalloc": ([POINTER(best_config), c_int32, c_void_p, c_double, c_void_p, c_uint32,
+                                      c_uint32, c_void_p, c_void_p], c_int32),
 }
 
 _lib = None

@@ -35,7 +35,7 @@ using namespace best;
 
 namespace {
 
-thread_local std::string g_init_error = "no error";
+thread_local char g_init_error[512] = "no error";
 
 // Work of one VEGAS iteration index: the active tasks and their segments.
 struct IterPlan {
@@ -107,7 +107,7 @@ best_status fail(best_ctx* c, best_status st, const char* fmt, ...) {
     vsnprintf(buf, sizeof(buf), fmt, ap);
     va_end(ap);
     if (c) c->err = buf;
-    else g_init_error = buf;
+    else snprintf(g_init_error, sizeof(g_init_error), "%s", buf);
     return st;
 }
 
@@ -334,6 +334,83 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
 
 }  // namespace
 
+namespace best {
+
+// Checks a configuration like best_collision_init does (messages go to the
+// fixed-size buffer read by best_last_error(NULL); nothing is allocated).
+best_status check_config(const best_config* cfg) { return validate(cfg); }
+
+best_status report(best_status st, const char* msg) { return fail(nullptr, st, "%s", msg); }
+
+// Side integral and task descriptors of task `task` in the enumeration of
+// best_collision_init, built without heap memory.  Returns false when the
+// task id is out of range.
+bool describe_task(const best_config* cfg, int32_t task, SideDesc* out_sd, TaskDesc* out_td) {
+    const int n_grid = cfg->grid.n;
+    int si = 0;
+    for (int p = 0; p < cfg->n_processes; ++p) {
+        const best_process& pr = cfg->processes[p];
+        const int n_in = pr.n_in, n_out = pr.n_out, n = n_in + n_out;
+        int s_in[BEST_MAX_LEGS], s_out[BEST_MAX_LEGS];
+        for (int k = 0; k < n_in; ++k) s_in[k] = pr.species[k];
+        for (int k = 0; k < n_out; ++k) s_out[k] = pr.species[n_in + k];
+        std::sort(s_in, s_in + n_in);
+        std::sort(s_out, s_out + n_out);
+        const bool symmetric = n_in == n_out && std::equal(s_in, s_in + n_in, s_out);
+        for (int side = 0; side < (symmetric ? 1 : 2); ++side) {
+            const int offset = side == 0 ? 0 : n_in;
+            const int cnt = side == 0 ? n_in : n_out;
+            const int* sorted = side == 0 ? s_in : s_out;
+            for (int u = 0; u < cnt; ++u) {
+                if (u > 0 && sorted[u] == sorted[u - 1]) continue;     // distinct species, ascending
+                const int a = sorted[u];
+                if (task / (2 * n_grid) == si) {
+                    SideDesc sd{};
+                    sd.n = n;
+                    sd.n_in = n_in;
+                    sd.obs = -1;
+                    sd.mult = 0;
+                    for (int k = 0; k < cnt; ++k) {
+                        if (pr.species[offset + k] != a) continue;
+                        if (sd.obs < 0) sd.obs = offset + k;
+                        ++sd.mult;
+                    }
+                    sd.species_obs = a;
+                    sd.process = p;
+                    sd.side = side;
+                    roles(n_in, n_out, sd.obs, &sd.cons, sd.integ);
+                    for (int k = 0; k < n; ++k) {
+                        sd.leg_species[k] = pr.species[k];
+                        const bool kin = k < n_in;
+                        if (kin) sd.in_mask |= 1 << k;
+                        if (kin == (side == 0)) sd.own_mask |= 1 << k;
+                    }
+                    sd.coupling2 = pr.coupling * pr.coupling;
+                    const int st_obs = cfg->species[a].stat;
+                    sd.eta_obs = st_obs == BEST_BE ? 1.0 : (st_obs == BEST_FD ? -1.0 : 0.0);
+                    sd.sigma = pr.sigma_E;
+                    TaskDesc td{};
+                    td.si = 0;
+                    td.point = (task / 2) % n_grid;
+                    td.term = task % 2;
+                    td.nitn = 1;
+                    td.neval = pr.neval_per_point ? pr.neval_per_point[td.point] : pr.neval;
+                    td.dim = 3 * (n - 2);
+                    td.nbins = pr.nbins;
+                    td.alpha = pr.alpha;
+                    *out_sd = sd;
+                    *out_td = td;
+                    return true;
+                }
+                ++si;
+            }
+        }
+    }
+    return false;
+}
+
+}  // namespace best
+
 extern "C" {
 
 best_status best_collision_init(const best_config* cfg, best_ctx** out) {
@@ -343,7 +420,7 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     if (vs != BEST_OK) return vs;
     best_ctx* ctx = new best_ctx();
     auto bail = [&](best_status s) {
-        g_init_error = ctx->err;
+        snprintf(g_init_error, sizeof(g_init_error), "%s", ctx->err.c_str());
         free_all(ctx);
         delete ctx;
         return s;
@@ -690,7 +767,7 @@ best_status best_profile_read(best_ctx* ctx, double* sample_kernel_ms, int64_t* 
     return BEST_OK;
 }
 
-const char* best_last_error(const best_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_error.c_str(); }
+const char* best_last_error(const best_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_error; }
 
 void best_collision_destroy(best_ctx* ctx) {
     if (!ctx) return;
