@@ -52,8 +52,13 @@ def mufu_per_sample(n_legs):
     return 6 * (n_legs - 2) + 4
 
 
+NEVAL = None      # per-task samples per iteration; None = the workload's own (1e6)
+
+
 def workload():
     import workloads as W
+    if NEVAL is not None:
+        return W.c2_bose_2to2(neval=NEVAL)
     return W.c2_bose_2to2()
 
 
@@ -258,7 +263,7 @@ def run_native(args, rank, world):
         "data": "synthetic (seeded; BE(T=1) + Gaussian bump, no dataset)",
         "config": {"workload": f"{WORKLOAD}: 2 species (m=0, m=0.5) BE 2->2, 128 log points [1e-3,30], "
                                "sigma_E=0.005, 1e6 samples x 8 iterations per task, 512 tasks, Heun steps",
-                   "grid_points": prob.grid.n, "tasks": 512, "neval": 1_000_000, "nitn": 8,
+                   "grid_points": prob.grid.n, "tasks": 512, "neval": prob.processes[0].neval, "nitn": 8,
                    "step": "one Heun step = 2 sweeps", "l2": "flushed between steps (512 MiB write, in the "
                    "timed region)", "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "evals_per_s": sweeps_per_s * evals,
@@ -347,7 +352,11 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--neval", type=int, default=None,
+                    help="samples per task per iteration (smaller cases for profiling)")
     args = ap.parse_args()
+    global NEVAL
+    NEVAL = args.neval
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
