@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "philox.cuh"
 
 namespace best {
 // kernels.cu
@@ -305,6 +306,8 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
         P.partials = ctx->d_partials;
         P.itn = static_cast<uint32_t>(it);
         P.smem_spline_elems = g.n_species * 4 * (g.n_grid - 1) + g.n_grid;
+        const PhiloxKey key = philox_key(g.seed);
+        for (int r = 0; r < 20; ++r) P.rk[r] = key.k[r];
         void* args[] = {&P};
         if (ctx->profiling) {
             while (ctx->ev.size() < ctx->ev_used + 2) {

@@ -98,6 +98,7 @@ struct SegConst {
     R gauss_k;              // -log2(e) / (2 sigma^2)
     R e_cut;
     R eta_c;                // eta of the conserved leg (tail formula)
+    R tlo_a, tlo_b, thi_a, thi_b;   // Eq. (13) end fits of the conserved leg's species
     int fd_c;               // conserved leg is FD (clamp f <= 1)
     int fd[NI];
 };
@@ -116,17 +117,32 @@ __device__ __forceinline__ R spline_eval(const SplineView<R>& sv, R q, const Geo
     }
     j = min(max(j, 0), g.n_grid - 2);
     const R t = q - sv.knot[j];
-    const R* c = sv.coef + 4 * j;
-    R f = fma(fma(fma(c[3], t, c[2]), t, c[1]), t, c[0]);
+    R f;
+    if constexpr (sizeof(R) == 4) {
+        const float4 c = reinterpret_cast<const float4*>(sv.coef)[j];
+        f = fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
+    } else {
+        const double2* cp = reinterpret_cast<const double2*>(sv.coef) + 2 * j;
+        const double2 lo = cp[0], hi = cp[1];
+        f = fma(fma(fma(hi.y, t, hi.x), t, lo.y), t, lo.x);
+    }
     return f > R(0) ? f : R(0);
+}
+
+// 1 / (exp(x) - eta) of the Eq. (13) tails, FP32, without branches: for BE
+// small x uses exp(x) - 1 = x (1 + x/2 + x^2/6) to avoid cancellation.
+__device__ __forceinline__ float tail_f32(float x, float eta) {
+    const float e = __expf(x);
+    const float small = x * fmaf(x, fmaf(x, 0.16666667f, 0.5f), 1.0f);
+    const float den = (eta == 1.0f && fabsf(x) < 0.03f) ? small : e - eta;
+    return den > 0.0f ? __frcp_rn(den) : 0.0f;
 }
 
 template <typename R, int NLEG>
 __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& seg,
                                             const SideDesc& sd, const TaskDesc& td,
                                             const TaskConst& tc, R* s_spline,
-                                            Real2<R>* s_map, R* s_hist, double* s_red,
-                                            const PhiloxKey& key) {
+                                            Real2<R>* s_map, R* s_hist, double* s_red) {
     constexpr int NI = NLEG - 2;
     constexpr int D = 3 * NI;
     constexpr bool F32 = RMath<R>::kF32;
@@ -204,6 +220,10 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
         C.sp_cons = sp;
         C.eta_c = static_cast<R>(eta);
         C.fd_c = P.sconst[sp].stat == BEST_FD;
+        C.tlo_a = static_cast<R>(P.sconst[sp].tail_lo_a);
+        C.tlo_b = static_cast<R>(P.sconst[sp].tail_lo_b);
+        C.thi_a = static_cast<R>(P.sconst[sp].tail_hi_a);
+        C.thi_b = static_cast<R>(P.sconst[sp].tail_hi_b);
     }
     C.a = static_cast<R>(ts.a);
     C.inv_a = static_cast<R>(1.0 / ts.a);
@@ -227,7 +247,7 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
     const uint32_t task = static_cast<uint32_t>(seg.task);
     for (int64_t grp = seg.g0 + tid; grp < seg.g1; grp += blockDim.x) {
         R u[SS::kUniforms];
-        group_uniforms<D, F32, R>(u, grp, P.itn, ts.call, task, key.k);
+        group_uniforms<D, F32, R>(u, grp, P.itn, ts.call, task, P.rk);
 #pragma unroll
         for (int sgi = 0; sgi < G; ++sgi) {
             const int64_t s = grp * G + sgi;
@@ -275,7 +295,7 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
                 rinvE_prod *= rE;
                 const SplineView<R> sv{s_spline + C.spc[j] * ncoef, knots};
                 R f = spline_eval<R>(sv, r, g, inv_step, q0, inv_q0);
-                if (C.fd[j]) f = f < R(1) ? f : R(1);
+                f = C.fd[j] ? (f < R(1) ? f : R(1)) : f;
                 stat *= fma(C.cb[j], f, C.ca[j]);
             }
             // conserved leg (Eq. (10), App. A)
@@ -288,17 +308,25 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
             R fc;
             {
                 const R qc = pc2 * (pc2 > R(0) ? RMath<R>::rsqrt_(pc2) : R(0)) * C.a;
-                if (qc >= q0 && qc <= qN) {
+                const bool below = qc < q0, above = qc > qN;
+                if constexpr (F32) {
+                    // both lookups, then a select: no divergence on the tail
                     const SplineView<R> sv{s_spline + C.sp_cons * ncoef, knots};
-                    fc = spline_eval<R>(sv, qc, g, inv_step, q0, inv_q0);
+                    const float fs = spline_eval<R>(sv, fminf(fmaxf(qc, q0), qN), g, inv_step, q0, inv_q0);
+                    const float x = below ? fmaf(C.tlo_b, Ec, C.tlo_a) : fmaf(C.thi_b, Ec, C.thi_a);
+                    const float ft = tail_f32(x, C.eta_c);
+                    fc = (below || above) ? ft : fs;
                 } else {
-                    const SpeciesConst& sc = scst[C.sp_cons];
-                    const R x = qc < q0 ? static_cast<R>(sc.tail_lo_a) + static_cast<R>(sc.tail_lo_b) * Ec
-                                        : static_cast<R>(sc.tail_hi_a) + static_cast<R>(sc.tail_hi_b) * Ec;
-                    const R den = C.eta_c == R(1) ? RMath<R>::expm1_(x) : RMath<R>::exp_(x) - C.eta_c;
-                    fc = den > R(0) ? R(1) / den : R(0);
+                    if (!below && !above) {
+                        const SplineView<R> sv{s_spline + C.sp_cons * ncoef, knots};
+                        fc = spline_eval<R>(sv, qc, g, inv_step, q0, inv_q0);
+                    } else {
+                        const R x = below ? C.tlo_a + C.tlo_b * Ec : C.thi_a + C.thi_b * Ec;
+                        const R den = C.eta_c == R(1) ? RMath<R>::expm1_(x) : RMath<R>::exp_(x) - C.eta_c;
+                        fc = den > R(0) ? R(1) / den : R(0);
+                    }
                 }
-                if (C.fd_c) fc = fc < R(1) ? fc : R(1);
+                fc = C.fd_c ? (fc < R(1) ? fc : R(1)) : fc;
             }
             stat *= fma(C.cbc, fc, C.cac);
             const R gauss = RMath<R>::exp2_(C.gauss_k * dE * dE);
@@ -344,7 +372,7 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
 }
 
 template <typename R, int NMAX>
-__global__ void __launch_bounds__(kThreads, 1) eval_kernel(EvalParams P) {
+__global__ void __launch_bounds__(kThreads, (sizeof(R) == 8 ? 1 : (NMAX <= 4 ? 3 : 2))) eval_kernel(EvalParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* s_spline = reinterpret_cast<R*>(smem_raw);
     const int nsp = P.smem_spline_elems;
@@ -361,7 +389,6 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(EvalParams P) {
         const R* gk = static_cast<const R*>(P.knots);
         for (int k = threadIdx.x; k < P.geo.n_grid; k += blockDim.x) s_spline[ncoef + k] = gk[k];
     }
-    const PhiloxKey key = philox_key(P.geo.seed);
     const int s0 = P.cta_seg[blockIdx.x], s1 = P.cta_seg[blockIdx.x + 1];
     for (int si = s0; si < s1; ++si) {
         const Segment seg = P.segs[si];
@@ -370,10 +397,10 @@ __global__ void __launch_bounds__(kThreads, 1) eval_kernel(EvalParams P) {
         const TaskConst tc = P.tconst[seg.task];
         __syncthreads();
         switch (sd.n) {
-            case 3: if constexpr (NMAX >= 3) run_segment<R, 3>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, key); break;
-            case 4: if constexpr (NMAX >= 4) run_segment<R, 4>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, key); break;
-            case 5: if constexpr (NMAX >= 5) run_segment<R, 5>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, key); break;
-            case 6: if constexpr (NMAX >= 6) run_segment<R, 6>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, key); break;
+            case 3: if constexpr (NMAX >= 3) run_segment<R, 3>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red); break;
+            case 4: if constexpr (NMAX >= 4) run_segment<R, 4>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red); break;
+            case 5: if constexpr (NMAX >= 5) run_segment<R, 5>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red); break;
+            case 6: if constexpr (NMAX >= 6) run_segment<R, 6>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red); break;
             default: break;
         }
     }

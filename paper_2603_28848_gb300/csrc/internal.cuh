@@ -130,6 +130,7 @@ struct EvalParams {
     double* partials;
     uint32_t itn;
     int32_t smem_spline_elems;  // R elements of spline coefficients + knots
+    uint32_t rk[20];            // Philox round keys (kernel parameters: read from the constant bank)
 };
 
 }  // namespace best

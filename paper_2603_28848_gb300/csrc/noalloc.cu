@@ -13,6 +13,7 @@
 #include <cstring>
 
 #include "internal.cuh"
+#include "philox.cuh"
 
 namespace best {
 __global__ void spline_build_kernel(Geometry, const double*, int, const double*, TimeState*, SpeciesConst*,
@@ -268,6 +269,8 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     P.partials = reinterpret_cast<double*>(base + kOffPart);
     P.itn = iteration;
     P.smem_spline_elems = static_cast<int32_t>(spl);
+    const PhiloxKey key = philox_key(g.seed);
+    for (int r = 0; r < 20; ++r) P.rk[r] = key.k[r];
     void* args[] = {&P};
     if (cudaLaunchKernel(fn, dim3(ctas), dim3(kThreads), args, smem, st) != cudaSuccess)
         return report(BEST_ERR_CUDA, "noalloc: sample kernel launch failed");

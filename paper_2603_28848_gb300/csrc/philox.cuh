@@ -32,8 +32,9 @@ __host__ __device__ inline PhiloxKey philox_key(uint64_t seed) {
 
 // Ten rounds: (c0, c2) are multiplied by the round multipliers; the high
 // halves are mixed with the other words and the round key.
+template <typename Keys>
 __device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
-                                              const uint32_t* __restrict__ rk) {
+                                              const Keys& rk) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         const uint32_t lo0 = 0xD2511F53u * c0;
@@ -70,9 +71,11 @@ struct StreamShape {
 };
 
 // Fills u[0 .. G*D) with the uniforms of sample group g of one task stream.
-template <int D, bool F32, typename R>
+// rk: the 20 round keys (pass the kernel-parameter array so that they are
+// read from the constant bank rather than held in registers).
+template <int D, bool F32, typename R, typename Keys>
 __device__ __forceinline__ void group_uniforms(R* u, int64_t g, uint32_t itn, uint32_t call,
-                                               uint32_t task, const uint32_t* __restrict__ rk) {
+                                               uint32_t task, const Keys& rk) {
     using S = StreamShape<D, F32>;
     const uint64_t b0 = static_cast<uint64_t>(g) * S::kBlocks;
 #pragma unroll
