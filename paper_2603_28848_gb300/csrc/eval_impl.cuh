@@ -106,12 +106,14 @@ struct SegConst {
 // Cubic spline value at comoving q inside [q_0, q_{n-1}] (Sec. 3B).
 template <typename R>
 __device__ __forceinline__ R spline_eval(const SplineView<R>& sv, R q, const Geometry& g,
-                                         R inv_step, R q0, R inv_q0) {
+                                         R inv_step, R q0, R lq0_step) {
     // interval index from the grid formula (a guess within one interval of
     // the exact one; the cubic pieces agree to C^2 at the knots)
     int j;
     if (g.log_spaced) {
-        j = static_cast<int>(__log2f(static_cast<float>(q * inv_q0)) * static_cast<float>(inv_step));
+        // log2(q / q0) / step = log2(q) / step - log2(q0) / step
+        j = static_cast<int>(fmaf(__log2f(static_cast<float>(q)), static_cast<float>(inv_step),
+                                  -static_cast<float>(lq0_step)));
     } else {
         j = static_cast<int>(static_cast<float>((q - q0) * inv_step));
     }
@@ -233,7 +235,8 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
     C.e_cut = static_cast<R>(g.e_cut);
     const R nbR = static_cast<R>(nb);
     const R q0 = static_cast<R>(g.q_min);
-    const R inv_q0 = static_cast<R>(1.0 / g.q_min);
+    // for log grids: log2(q0) / step (the spline index offset); unused otherwise
+    const R lq0_step = static_cast<R>(g.log_spaced ? std::log2(g.q_min) / (g.log_step / 0.6931471805599453) : 0.0);
     const R qN = static_cast<R>(g.q_max);
     const R inv_step = static_cast<R>(1.0 / (g.log_spaced ? g.log_step / 0.6931471805599453 : g.log_step));
     const int ncoef = 4 * (g.n_grid - 1);
@@ -246,24 +249,37 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
     const int64_t N = td.neval;
     const uint32_t task = static_cast<uint32_t>(seg.task);
     for (int64_t grp = seg.g0 + tid; grp < seg.g1; grp += blockDim.x) {
-        R u[SS::kUniforms];
-        group_uniforms<D, F32, R>(u, grp, P.itn, ts.call, task, P.rk);
+        // FP32: raw words; FP64: 52-bit uniforms
+        uint32_t uw[F32 ? SS::kUniforms : 1];
+        R u[F32 ? 1 : SS::kUniforms];
+        if constexpr (F32) group_words<D>(uw, grp, P.itn, ts.call, task, P.rk);
+        else group_uniforms<D, F32, R>(u, grp, P.itn, ts.call, task, P.rk);
 #pragma unroll
         for (int sgi = 0; sgi < G; ++sgi) {
             const int64_t s = grp * G + sgi;
             if (s >= N) break;
-            const R* us = u + sgi * D;
             // VEGAS map and scaling to (r, theta, phi - pi)
             R y[D];
             int bin[D];
             R jac = R(1);
 #pragma unroll
             for (int d = 0; d < D; ++d) {
-                const R t = us[d] * nbR;
-                int b = static_cast<int>(t);
-                b = b < nb - 1 ? b : nb - 1;
+                int b;
+                R fr;
+                if constexpr (F32) {
+                    // x nb = (2k + 1) nb / 2^24 with k = word >> 9: increment and
+                    // fraction exactly, in integer arithmetic
+                    const uint32_t m = (uw[sgi * D + d] >> 9) * (2u * nb) + static_cast<uint32_t>(nb);
+                    b = static_cast<int>(m >> 24);
+                    fr = static_cast<float>(m & 0xFFFFFFu) * 5.9604644775390625e-08f;   // 2^-24
+                } else {
+                    const R t = u[sgi * D + d] * nbR;
+                    b = static_cast<int>(t);
+                    b = b < nb - 1 ? b : nb - 1;
+                    fr = t - static_cast<R>(b);
+                }
                 const Real2<R> e = s_map[d * nb + b];
-                y[d] = fma(e.dy, t - static_cast<R>(b), e.y0);
+                y[d] = fma(e.dy, fr, e.y0);
                 jac *= e.dy;
                 bin[d] = b;
             }
@@ -294,7 +310,7 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
                 meas *= r * r * st;
                 rinvE_prod *= rE;
                 const SplineView<R> sv{s_spline + C.spc[j] * ncoef, knots};
-                R f = spline_eval<R>(sv, r, g, inv_step, q0, inv_q0);
+                R f = spline_eval<R>(sv, r, g, inv_step, q0, lq0_step);
                 f = C.fd[j] ? (f < R(1) ? f : R(1)) : f;
                 stat *= fma(C.cb[j], f, C.ca[j]);
             }
@@ -312,14 +328,14 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
                 if constexpr (F32) {
                     // both lookups, then a select: no divergence on the tail
                     const SplineView<R> sv{s_spline + C.sp_cons * ncoef, knots};
-                    const float fs = spline_eval<R>(sv, fminf(fmaxf(qc, q0), qN), g, inv_step, q0, inv_q0);
+                    const float fs = spline_eval<R>(sv, fminf(fmaxf(qc, q0), qN), g, inv_step, q0, lq0_step);
                     const float x = below ? fmaf(C.tlo_b, Ec, C.tlo_a) : fmaf(C.thi_b, Ec, C.thi_a);
                     const float ft = tail_f32(x, C.eta_c);
                     fc = (below || above) ? ft : fs;
                 } else {
                     if (!below && !above) {
                         const SplineView<R> sv{s_spline + C.sp_cons * ncoef, knots};
-                        fc = spline_eval<R>(sv, qc, g, inv_step, q0, inv_q0);
+                        fc = spline_eval<R>(sv, qc, g, inv_step, q0, lq0_step);
                     } else {
                         const R x = below ? C.tlo_a + C.tlo_b * Ec : C.thi_a + C.thi_b * Ec;
                         const R den = C.eta_c == R(1) ? RMath<R>::expm1_(x) : RMath<R>::exp_(x) - C.eta_c;
