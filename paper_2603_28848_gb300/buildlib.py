@@ -20,18 +20,21 @@ def nvcc():
     return path
 
 
-def build(verbose=False, force=False):
-    """Compile every translation unit (in parallel) and link libbest.so."""
-    os.makedirs(os.path.join(HERE, "_build"), exist_ok=True)
+def build(verbose=False, force=False, out=None, defines=()):
+    """Compile every translation unit (in parallel) and link libbest.so
+    (or `out`, with extra -D `defines`, for launch-shape experiments)."""
+    lib = out or LIB
+    bdir = os.path.join(HERE, "_build") if out is None else out + ".build"
+    os.makedirs(bdir, exist_ok=True)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(HERE, "..", "include", "best.h")]
     newest = max(os.path.getmtime(p) for p in deps)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
-        return LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= newest:
+        return lib
     cc = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(HERE, "_build", src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(bdir, src.replace(".cu", ".o"))
+        cmd = [cc, *ARCH, *FLAGS, *[f"-D{d}" for d in defines], "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -43,13 +46,13 @@ def build(verbose=False, force=False):
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fPIC"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -189,8 +189,9 @@ best_status validate(const best_config* cfg) {
         if (!(pr.alpha >= 0.0)) return fail(ctx, BEST_ERR_INVALID, "process %d: alpha must be >= 0", p);
         for (int i = 0; i < g.n; ++i) {
             const int64_t N = pr.neval_per_point ? pr.neval_per_point[i] : pr.neval;
-            if (N < 2 || N > (int64_t(1) << 31))
-                return fail(ctx, BEST_ERR_INVALID, "process %d: neval must be in [2, 2^31]", p);
+            // the Philox block index of a task's last sample must fit the 32-bit counter word
+            if (N < 2 || N > (int64_t(1) << 31) || N * 3 * (n - 2) > (int64_t(1) << 33))
+                return fail(ctx, BEST_ERR_INVALID, "process %d: need 2 <= neval, neval * dim <= 2^33", p);
         }
     }
     return BEST_OK;

@@ -248,7 +248,8 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
     Acc<R> acc_w, acc_w2;
     const int64_t N = td.neval;
     const uint32_t task = static_cast<uint32_t>(seg.task);
-    for (int64_t grp = seg.g0 + tid; grp < seg.g1; grp += blockDim.x) {
+    const int32_t g1 = static_cast<int32_t>(seg.g1);
+    for (int32_t grp = static_cast<int32_t>(seg.g0) + tid; grp < g1; grp += blockDim.x) {
         // FP32: raw words; FP64: 52-bit uniforms
         uint32_t uw[F32 ? SS::kUniforms : 1];
         R u[F32 ? 1 : SS::kUniforms];
@@ -256,8 +257,9 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
         else group_uniforms<D, F32, R>(u, grp, P.itn, ts.call, task, P.rk);
 #pragma unroll
         for (int sgi = 0; sgi < G; ++sgi) {
-            const int64_t s = grp * G + sgi;
-            if (s >= N) break;
+            // samples past the budget (only in a task's last group) are
+            // computed and given weight 0: no branch inside the group
+            const bool valid = static_cast<int64_t>(grp) * G + sgi < N;
             // VEGAS map and scaling to (r, theta, phi - pi)
             R y[D];
             int bin[D];
@@ -326,12 +328,15 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
                 const R qc = pc2 * (pc2 > R(0) ? RMath<R>::rsqrt_(pc2) : R(0)) * C.a;
                 const bool below = qc < q0, above = qc > qN;
                 if constexpr (F32) {
-                    // both lookups, then a select: no divergence on the tail
+                    // spline and tail for every lane, then a select: the warp
+                    // never diverges on the conserved leg
                     const SplineView<R> sv{s_spline + C.sp_cons * ncoef, knots};
-                    const float fs = spline_eval<R>(sv, fminf(fmaxf(qc, q0), qN), g, inv_step, q0, lq0_step);
-                    const float x = below ? fmaf(C.tlo_b, Ec, C.tlo_a) : fmaf(C.thi_b, Ec, C.thi_a);
-                    const float ft = tail_f32(x, C.eta_c);
-                    fc = (below || above) ? ft : fs;
+                    fc = spline_eval<R>(sv, fminf(fmaxf(qc, q0), qN), g, inv_step, q0, lq0_step);
+                    {
+                        const float x = below ? fmaf(C.tlo_b, Ec, C.tlo_a) : fmaf(C.thi_b, Ec, C.thi_a);
+                        const float ft = tail_f32(x, C.eta_c);
+                        fc = (below || above) ? ft : fc;
+                    }
                 } else {
                     if (!below && !above) {
                         const SplineView<R> sv{s_spline + C.sp_cons * ncoef, knots};
@@ -347,7 +352,7 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
             stat *= fma(C.cbc, fc, C.cac);
             const R gauss = RMath<R>::exp2_(C.gauss_k * dE * dE);
             R w = stat * meas * rinvE_prod * rEc * gauss;
-            w = cut ? R(0) : w;
+            w = (cut || !valid) ? R(0) : w;
             const R w2 = w * w;
             acc_w.add(w);
             acc_w2.add(w2);
@@ -387,8 +392,15 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
     __syncthreads();
 }
 
+#ifndef BEST_EVAL_MIN_BLOCKS_N4
+#define BEST_EVAL_MIN_BLOCKS_N4 5      // CTAs per SM the FP32 2->2 kernel is register-limited to
+#endif
+#ifndef BEST_EVAL_MIN_BLOCKS_N6
+#define BEST_EVAL_MIN_BLOCKS_N6 2
+#endif
 template <typename R, int NMAX>
-__global__ void __launch_bounds__(kThreads, (sizeof(R) == 8 ? 1 : (NMAX <= 4 ? 3 : 2))) eval_kernel(EvalParams P) {
+__global__ void __launch_bounds__(kThreads, (sizeof(R) == 8 ? 1 : (NMAX <= 4 ? BEST_EVAL_MIN_BLOCKS_N4 : BEST_EVAL_MIN_BLOCKS_N6)))
+eval_kernel(EvalParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* s_spline = reinterpret_cast<R*>(smem_raw);
     const int nsp = P.smem_spline_elems;
