@@ -32,6 +32,7 @@ import numpy as np  # noqa: E402
 METRIC = "C[f] grid sweeps/s and integrand evals/s, FP32 vs FP64 path, at 1e-4 rel MC err"
 UNIT = "sweeps/s"
 WORKLOAD = "c2_bose_2to2"
+DT = 0.5          # requested Heun step (bounded by Eq. (16) inside each step)
 FP32_PEAK_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
@@ -141,40 +142,40 @@ def run_native(args, rank, world):
             torch.distributed.barrier()
 
     # ---------------- FP32 path: the headline ----------------------------------------
+    # Heun steps replayed from a CUDA graph (best_evolve) after the launch
+    # shape was picked by the autotuner (best_autotune).
     col = Collision(prob, W.PREC_FP32)
     evals = col.sweep_samples()
     samples_per_launch = col.sweep_samples(0)
     logf = torch.tensor(np.log(f0), dtype=torch.float64, device="cuda").contiguous()
     t = torch.zeros(1, dtype=torch.float64, device="cuda")
-    dt = torch.full((1,), 0.5, dtype=torch.float64, device="cuda")
-    C = torch.empty_like(logf)
-    for _ in range(args.warmup):
-        dt.fill_(0.5)
-        col.step_heun(logf, t, dt, C)
-    col.check()
-    stream = torch.cuda.current_stream()
-    clocks = Clocks(dev)
-    col.profile(True)
-    torch.cuda.synchronize()
-    barrier()
-    clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    launches = 0
-    for _ in range(args.steps):
-        dt.fill_(0.5)
-        col.step_heun(logf, t, dt, C)
-        launches += col.last_launch_count()
-        flush.zero_()                                  # evict L2 between steps
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    kern_ms, kern_n = col.profile_read()
-    col.profile(False)
-    col.check()
+    dt = torch.full((1,), DT, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctas_per_sm = col.autotune(torch.exp(logf), 0.0)
+        col.profile(True)
+        col.evolve(logf, t, dt, args.warmup, DT, "heun", stream=stream)
+        col.check(stream)
+        clocks = Clocks(dev)
+        torch.cuda.synchronize()
+        barrier()
+        clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        launches = 0
+        for _ in range(args.steps):
+            col.evolve(logf, t, dt, 1, DT, "heun", stream=stream)
+            launches += col.last_launch_count()
+            flush.zero_()                                  # evict L2 between steps
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        kern_ms, kern_n = col.profile_read()               # launches of the last timed step
+        col.profile(False)
+        col.check(stream)
     if world > 1:
         tt = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
@@ -186,24 +187,23 @@ def run_native(args, rank, world):
     # ---------------- e2e: host buffers through the public API --------------------------
     h_logf = torch.tensor(np.log(f0), dtype=torch.float64).pin_memory()
     h_t = torch.zeros(1, dtype=torch.float64).pin_memory()
-    h_dt = torch.full((1,), 0.5, dtype=torch.float64).pin_memory()
     h_out = torch.empty_like(h_logf).pin_memory()
-    h_C = torch.empty_like(h_logf).pin_memory()
-    torch.cuda.synchronize()
-    barrier()
-    e2 = torch.cuda.Event(enable_timing=True)
-    e3 = torch.cuda.Event(enable_timing=True)
-    e2.record(stream)
-    for _ in range(args.steps):
-        logf.copy_(h_logf, non_blocking=True)
-        t.copy_(h_t, non_blocking=True)
-        dt.copy_(h_dt, non_blocking=True)
-        col.step_heun(logf, t, dt, C)
-        h_out.copy_(logf, non_blocking=True)
-        h_C.copy_(C, non_blocking=True)
-        flush.zero_()
-    e3.record(stream)
-    torch.cuda.synchronize()
+    h_tout = torch.empty_like(h_t).pin_memory()
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize()
+        barrier()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for _ in range(args.steps):
+            logf.copy_(h_logf, non_blocking=True)
+            t.copy_(h_t, non_blocking=True)
+            col.evolve(logf, t, dt, 1, DT, "heun", stream=stream)
+            h_out.copy_(logf, non_blocking=True)
+            h_tout.copy_(t, non_blocking=True)
+            flush.zero_()
+        e3.record(stream)
+        torch.cuda.synchronize()
     ms_e2e = e2.elapsed_time(e3)
     if world > 1:
         tt = torch.tensor([ms_e2e], device="cuda")
@@ -222,13 +222,14 @@ def run_native(args, rank, world):
         col64.eval(f64, 0.0)                          # warm-up sweep (maps adapt)
         torch.cuda.synchronize()
         col64.profile(True)
+        s64 = torch.cuda.current_stream()
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
+        a0.record(s64)
         for _ in range(args.fp64_steps):
-            dt64.fill_(0.5)
+            dt64.fill_(DT)
             col64.step_heun(logf64, t64, dt64)
-        a1.record(stream)
+        a1.record(s64)
         torch.cuda.synchronize()
         ms64 = a0.elapsed_time(a1)
         k64_ms, k64_n = col64.profile_read()
@@ -275,7 +276,9 @@ def run_native(args, rank, world):
         if fp64 else None,
         "roofline": roof,
         "e2e": {"value": sweeps / (ms_e2e / 1e3), "unit": UNIT,
-                "h2d_bytes_per_step": logf.numel() * 8 + 16, "d2h_bytes_per_step": 2 * logf.numel() * 8},
+                "h2d_bytes_per_step": logf.numel() * 8 + 8, "d2h_bytes_per_step": logf.numel() * 8 + 8},
+        "graph": "Heun steps replayed from a CUDA graph (best_evolve)",
+        "autotune_ctas_per_sm": ctas_per_sm,
         "gpu_launches": launches,
         "clocks": clk,
     }

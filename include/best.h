@@ -147,6 +147,35 @@ best_status best_step_euler(best_ctx* ctx, double* logf_dev, double* t_dev,
 best_status best_step_heun(best_ctx* ctx, double* logf_dev, double* t_dev,
                            double* dt_dev, double* C_dev, void* stream);
 
+/*
+ * n_steps Euler (method 0, Eq. (14)) or Heun (method 1, Eq. (15)) steps
+ * replayed from a CUDA graph: the first call (and any call whose logf / t /
+ * dt pointers or method differ from the previous one) captures one step on
+ * `stream` into a graph owned by the context; every call then launches it
+ * n_steps times.  Each step starts from the requested step dt_request
+ * (written into *dt_dev inside the graph) and bounds it by Eq. (16); on
+ * return *dt_dev holds the step used by the last step.  `stream` must be a
+ * created stream (not the legacy or per-thread default stream).  Results
+ * are bitwise identical to n_steps calls of best_step_euler / best_step_heun
+ * with *dt_dev reset to dt_request before each.
+ */
+best_status best_evolve(best_ctx* ctx, int32_t method, int32_t n_steps, double* logf_dev,
+                        double* t_dev, double* dt_dev, double dt_request, void* stream);
+
+/*
+ * Project autotuner of the sample kernel's launch shape: runs one sweep of
+ * f_dev at time t with each compiled variant of the sample kernel (register
+ * budgets for 2..5 CTAs per SM; the persistent grid and the work partition
+ * follow from the variant's occupancy), times the sample-kernel launches
+ * with CUDA events, keeps the fastest, and restores the VEGAS maps, the
+ * per-task scales and the evaluation counter, so that the context's later
+ * results do not depend on whether it was tuned (beyond summation order in
+ * the FP32 path).  Synchronous; allocates a temporary copy of the maps.
+ * *ctas_per_sm (may be NULL) receives the chosen budget.
+ */
+best_status best_autotune(best_ctx* ctx, const double* f_dev, double t, int32_t* ctas_per_sm,
+                          void* stream);
+
 /* Context geometry. */
 int32_t best_num_tasks(const best_ctx* ctx);
 int32_t best_num_side_integrals(const best_ctx* ctx);
@@ -194,7 +223,9 @@ best_status best_check(best_ctx* ctx, void* stream);
  * launching stream (events are created on first use and reused).
  * best_profile_read waits for the recorded events, returns the summed kernel
  * time in milliseconds and the number of launches since the last read or
- * enable, and starts a new count.  Do not enable while capturing a graph.
+ * enable, and starts a new count.  When best_evolve captures its step graph
+ * with timing enabled, the events become part of the graph and the read
+ * returns the launches of the last replayed step.
  */
 best_status best_profile_enable(best_ctx* ctx, int32_t enable);
 best_status best_profile_read(best_ctx* ctx, double* sample_kernel_ms, int64_t* launches);

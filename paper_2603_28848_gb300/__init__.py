@@ -140,6 +140,29 @@ class Collision:
         check(self.lib.best_step_heun(self.ctx, _ptr(logf), _ptr(t_dev), _ptr(dt_dev), _ptr(C),
                                       _stream(stream)), self.ctx)
 
+    def evolve(self, logf, t_dev, dt_dev, n_steps, dt_request, method="heun", stream=None):
+        """n_steps Euler/Heun steps replayed from a CUDA graph captured on
+        `stream` (a created torch.cuda.Stream; defaults to a private one)."""
+        import torch
+        _require(logf, self.n_species * self.n_grid, "logf")
+        if stream is None:
+            if getattr(self, "_graph_stream", None) is None:
+                self._graph_stream = torch.cuda.Stream()
+            stream = self._graph_stream
+            stream.wait_stream(torch.cuda.current_stream())
+        m = {"euler": 0, "heun": 1}[method]
+        check(self.lib.best_evolve(self.ctx, m, int(n_steps), _ptr(logf), _ptr(t_dev), _ptr(dt_dev),
+                                   float(dt_request), ctypes.c_void_p(stream.cuda_stream)), self.ctx)
+        torch.cuda.current_stream().wait_stream(stream)
+
+    def autotune(self, f, t=0.0, stream=None):
+        """Pick the fastest sample-kernel variant on this workload; returns
+        the chosen CTAs per SM.  Maps, scales and counter are preserved."""
+        _require(f, self.n_species * self.n_grid, "f")
+        mb = ctypes.c_int32(0)
+        check(self.lib.best_autotune(self.ctx, _ptr(f), float(t), ctypes.byref(mb), _stream(stream)), self.ctx)
+        return mb.value
+
     # -- inspection -------------------------------------------------------------
     def check(self, stream=None):
         check(self.lib.best_check(self.ctx, _stream(stream)), self.ctx)

@@ -27,9 +27,8 @@ __global__ void step_first_kernel(Geometry, double*, const double*, const double
                                   double*, int);
 __global__ void heun_correct_kernel(Geometry, double*, const double*, const double*, const double*, double*,
                                     double*, TimeState*);
-// eval_f32.cu / eval_f64.cu
-void* eval_kernel_ptr_f32(int nmax);
-void* eval_kernel_ptr_f64(int nmax);
+// variants.cu
+int eval_variants(bool f32, int nmax, void** fn, int* mb);
 }  // namespace best
 
 using namespace best;
@@ -68,6 +67,11 @@ struct best_ctx {
     size_t spline_smem = 0;
     size_t refine_smem = 0;
     void* eval_fn = nullptr;
+    int n_variants = 0;             // sample-kernel variants (CTAs-per-SM register budgets)
+    void* variant_fn[4] = {};
+    int variant_mb[4] = {};
+    int variant = 0;
+    int64_t partial_capacity = 0;   // doubles allocated at d_partials
     int launches = 0;
     int max_nitn = 0;
     std::vector<SideDesc> sides;
@@ -93,6 +97,15 @@ struct best_ctx {
     double* d_k2 = nullptr;
     double* d_fstar = nullptr;
     double* d_prev = nullptr;       // |estimate| of every task from the last sweep (0: none)
+    // CUDA graph of one step (best_evolve), keyed by its arguments
+    cudaGraphExec_t graph = nullptr;
+    double* g_logf = nullptr;
+    double* g_t = nullptr;
+    double* g_dt = nullptr;
+    int g_method = -1;
+    int g_launches = 0;
+    size_t g_events = 0;            // timing events recorded by one replay
+    double* d_dtreq = nullptr;      // requested step, read by the graph
     // timing of the sample kernel (best_profile_*)
     bool profiling = false;
     std::vector<cudaEvent_t> ev;    // start/stop pairs
@@ -147,7 +160,9 @@ void free_all(best_ctx* c) {
     c->plans.clear();
     void* bufs[] = {c->d_sides, c->d_tasks, c->d_tconst, c->d_acc, c->d_sconst, c->d_ts, c->d_edges,
                     c->d_knots, c->d_knots32, c->d_coef64, c->d_coef32, c->d_fgrid, c->d_mass0, c->d_mass1,
-                    c->d_partials, c->d_k1, c->d_k2, c->d_fstar, c->d_prev};
+                    c->d_partials, c->d_k1, c->d_k2, c->d_fstar, c->d_prev, c->d_dtreq};
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
     for (void* b : bufs) cudaFree(b);
 }
 
@@ -277,6 +292,48 @@ best_status build_plan(best_ctx* ctx, int it, IterPlan& plan) {
     return BEST_OK;
 }
 
+// Selects sample-kernel variant v: raises its shared-memory limit, sizes the
+// persistent grid from its occupancy and rebuilds the work partition.
+best_status set_variant(best_ctx* ctx, int v) {
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    void* fn = ctx->variant_fn[v];
+    cudaFuncAttributes fa{};
+    CK(cudaFuncGetAttributes(&fa, fn));
+    if (static_cast<size_t>(fa.maxDynamicSharedSizeBytes) < ctx->eval_smem)
+        CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(ctx->eval_smem)));
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, ctx->eval_smem));
+    if (occ < 1) return fail(ctx, BEST_ERR_INVALID, "sample kernel does not fit on an SM");
+    // a captured step graph refers to the old partition: drop it
+    if (ctx->graph) {
+        CK(cudaGraphExecDestroy(ctx->graph));
+        ctx->graph = nullptr;
+    }
+    ctx->eval_fn = fn;
+    ctx->variant = v;
+    ctx->grid = nsm * occ;
+    for (auto& pl : ctx->plans) {
+        cudaFree(pl.d_active); cudaFree(pl.d_task_seg); cudaFree(pl.d_segs); cudaFree(pl.d_cta_seg);
+    }
+    ctx->plans.assign(ctx->max_nitn, IterPlan{});
+    int64_t part_max = 0;
+    for (int it = 0; it < ctx->max_nitn; ++it) {
+        best_status s = build_plan(ctx, it, ctx->plans[it]);
+        if (s != BEST_OK) return s;
+        part_max = std::max(part_max, ctx->plans[it].partial_doubles);
+    }
+    if (part_max > ctx->partial_capacity) {
+        cudaFree(ctx->d_partials);
+        ctx->d_partials = nullptr;
+        ctx->partial_capacity = 0;
+        CK(dalloc(&ctx->d_partials, static_cast<size_t>(part_max)));
+        ctx->partial_capacity = part_max;
+    }
+    return BEST_OK;
+}
+
 // Kernels of one collision sweep after set_time: spline, task constants,
 // nitn x (sample kernel + refinement), assembly into C / err.
 best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double* C, double* err,
@@ -339,6 +396,9 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
 }  // namespace
 
 namespace best {
+
+__global__ void store_scalar_kernel(double* dst, double v) { *dst = v; }
+__global__ void copy_scalar_kernel(double* dst, const double* src) { *dst = *src; }
 
 // Checks a configuration like best_collision_init does (messages go to the
 // fixed-size buffer read by best_last_error(NULL); nothing is allocated).
@@ -517,7 +577,7 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return bail(fail(ctx, BEST_ERR_CUDA, "no CUDA device"));
-    ctx->eval_fn = f32 ? eval_kernel_ptr_f32(ctx->nmax_legs) : eval_kernel_ptr_f64(ctx->nmax_legs);
+    ctx->n_variants = eval_variants(f32, ctx->nmax_legs, ctx->variant_fn, ctx->variant_mb);
     {
         const size_t rs = f32 ? 4 : 8;
         const size_t spl = static_cast<size_t>(g.n_species) * 4 * (g.n_grid - 1) + g.n_grid;
@@ -530,18 +590,7 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
         if (ctx->eval_smem > static_cast<size_t>(max_optin))
             return bail(fail(ctx, BEST_ERR_INVALID, "spline and map tables need %zu B of shared memory (max %d)",
                              ctx->eval_smem, max_optin));
-        // raise, never lower, the kernel's limit: other live contexts may need more
         cudaFuncAttributes fa{};
-        if (cudaFuncGetAttributes(&fa, ctx->eval_fn) != cudaSuccess)
-            return bail(fail(ctx, BEST_ERR_CUDA, "cannot query the sample kernel"));
-        if (static_cast<size_t>(fa.maxDynamicSharedSizeBytes) < ctx->eval_smem &&
-            cudaFuncSetAttribute(ctx->eval_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(ctx->eval_smem)) != cudaSuccess)
-            return bail(fail(ctx, BEST_ERR_CUDA, "cannot set shared memory of the sample kernel"));
-        int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ctx->eval_fn, kThreads, ctx->eval_smem) != cudaSuccess || occ < 1)
-            return bail(fail(ctx, BEST_ERR_CUDA, "sample kernel does not fit on an SM"));
-        ctx->grid = nsm * occ;
         ctx->spline_smem = 3 * sizeof(double) * g.n_grid;
         if (cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(&spline_build_kernel)) != cudaSuccess)
             return bail(fail(ctx, BEST_ERR_CUDA, "cannot query the spline kernel"));
@@ -600,6 +649,7 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     CKI(dalloc(&ctx->d_k2, static_cast<size_t>(S) * n));
     CKI(dalloc(&ctx->d_fstar, static_cast<size_t>(S) * n));
     CKI(dalloc(&ctx->d_prev, static_cast<size_t>(T)));
+    CKI(dalloc(&ctx->d_dtreq, 1));
     CKI(cudaMemset(ctx->d_prev, 0, sizeof(double) * T));
     CKI(cudaMemcpy(ctx->d_sides, ctx->sides.data(), g.n_side * sizeof(SideDesc), cudaMemcpyHostToDevice));
     CKI(cudaMemcpy(ctx->d_tasks, ctx->tasks.data(), T * sizeof(TaskDesc), cudaMemcpyHostToDevice));
@@ -610,14 +660,10 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     CKI(cudaMemcpy(ctx->d_knots32, knots32.data(), n * sizeof(float), cudaMemcpyHostToDevice));
     CKI(cudaMemcpy(ctx->d_mass0, m0.data(), S * sizeof(double), cudaMemcpyHostToDevice));
     CKI(cudaMemcpy(ctx->d_mass1, m1.data(), S * sizeof(double), cudaMemcpyHostToDevice));
-    ctx->plans.resize(ctx->max_nitn);
-    int64_t part_max = 0;
-    for (int it = 0; it < ctx->max_nitn; ++it) {
-        best_status s = build_plan(ctx, it, ctx->plans[it]);
-        if (s != BEST_OK) return bail(s);
-        part_max = std::max(part_max, ctx->plans[it].partial_doubles);
+    {
+        best_status sv = set_variant(ctx, 0);
+        if (sv != BEST_OK) return bail(sv);
     }
-    CKI(dalloc(&ctx->d_partials, static_cast<size_t>(part_max)));
     CKI(cudaDeviceSynchronize());
 #undef CKI
     *out = ctx;
@@ -671,6 +717,115 @@ best_status best_step_euler(best_ctx* ctx, double* logf_dev, double* t_dev, doub
 best_status best_step_heun(best_ctx* ctx, double* logf_dev, double* t_dev, double* dt_dev, double* C_dev,
                            void* stream) {
     return step_common(ctx, logf_dev, t_dev, dt_dev, C_dev, stream, true);
+}
+
+best_status best_evolve(best_ctx* ctx, int32_t method, int32_t n_steps, double* logf_dev, double* t_dev,
+                        double* dt_dev, double dt_request, void* stream) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    if (method != 0 && method != 1) return fail(ctx, BEST_ERR_INVALID, "method must be 0 (Euler) or 1 (Heun)");
+    if (n_steps < 0) return fail(ctx, BEST_ERR_INVALID, "n_steps must be >= 0");
+    if (!logf_dev || !t_dev || !dt_dev) return fail(ctx, BEST_ERR_INVALID, "logf, t and dt must not be NULL");
+    if (!(dt_request > 0.0)) return fail(ctx, BEST_ERR_INVALID, "dt_request must be > 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread)
+        return fail(ctx, BEST_ERR_INVALID, "best_evolve needs a created (non-default) stream to capture on");
+    const bool same = ctx->graph && ctx->g_logf == logf_dev && ctx->g_t == t_dev && ctx->g_dt == dt_dev &&
+                      ctx->g_method == method;
+    if (!same) {
+        if (ctx->graph) {
+            CK(cudaGraphExecDestroy(ctx->graph));
+            ctx->graph = nullptr;
+        }
+        // With profiling enabled the timing events are captured too: after the
+        // replays they hold the sample-kernel times of the last replayed step.
+        ctx->ev_used = 0;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        copy_scalar_kernel<<<1, 1, 0, st>>>(dt_dev, ctx->d_dtreq);
+        best_status s = step_common(ctx, logf_dev, t_dev, dt_dev, nullptr, stream, method == 1);
+        cudaGraph_t gr = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(st, &gr);
+        ctx->g_events = ctx->ev_used;
+        if (s != BEST_OK) {
+            if (gr) cudaGraphDestroy(gr);
+            return s;
+        }
+        if (ec != cudaSuccess) return fail(ctx, BEST_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ec));
+        const cudaError_t ei = cudaGraphInstantiate(&ctx->graph, gr, 0);
+        cudaGraphDestroy(gr);
+        if (ei != cudaSuccess) {
+            ctx->graph = nullptr;
+            return fail(ctx, BEST_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+        }
+        ctx->g_logf = logf_dev;
+        ctx->g_t = t_dev;
+        ctx->g_dt = dt_dev;
+        ctx->g_method = method;
+        ctx->g_launches = ctx->launches + 1;
+    }
+    store_scalar_kernel<<<1, 1, 0, st>>>(ctx->d_dtreq, dt_request);
+    CK(cudaGetLastError());
+    for (int k = 0; k < n_steps; ++k) CK(cudaGraphLaunch(ctx->graph, st));
+    if (n_steps > 0) ctx->ev_used = ctx->g_events;     // events of the last replay
+    ctx->launches = 1 + n_steps * ctx->g_launches;
+    return BEST_OK;
+}
+
+best_status best_autotune(best_ctx* ctx, const double* f_dev, double t, int32_t* ctas_per_sm, void* stream) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    if (!f_dev) return fail(ctx, BEST_ERR_INVALID, "f_dev must not be NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaStreamSynchronize(st));
+    const Geometry& g = ctx->geo;
+    const size_t ne = static_cast<size_t>(g.n_tasks) * g.map_stride;
+    double *edges0 = nullptr, *prev0 = nullptr, *Ctmp = nullptr;
+    TimeState ts0;
+    auto release = [&]() { cudaFree(edges0); cudaFree(prev0); cudaFree(Ctmp); };
+    if (dalloc(&edges0, ne) != cudaSuccess || dalloc(&prev0, g.n_tasks) != cudaSuccess ||
+        dalloc(&Ctmp, static_cast<size_t>(g.n_species) * g.n_grid) != cudaSuccess) {
+        release();
+        return fail(ctx, BEST_ERR_OOM, "autotune: no memory for the state backup");
+    }
+    auto restore = [&]() -> best_status {
+        CK(cudaMemcpyAsync(ctx->d_edges, edges0, ne * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(ctx->d_prev, prev0, g.n_tasks * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(ctx->d_ts, &ts0, sizeof(TimeState), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        return BEST_OK;
+    };
+    best_status s = BEST_OK;
+    do {
+        if (cudaMemcpy(edges0, ctx->d_edges, ne * sizeof(double), cudaMemcpyDeviceToDevice) != cudaSuccess ||
+            cudaMemcpy(prev0, ctx->d_prev, g.n_tasks * sizeof(double), cudaMemcpyDeviceToDevice) != cudaSuccess ||
+            cudaMemcpy(&ts0, ctx->d_ts, sizeof(TimeState), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            s = fail(ctx, BEST_ERR_CUDA, "autotune: state backup failed");
+            break;
+        }
+        const bool prof = ctx->profiling;
+        int best_v = ctx->variant;
+        double best_ms = 1e300;
+        for (int v = 0; v < ctx->n_variants && s == BEST_OK; ++v) {
+            if ((s = set_variant(ctx, v)) != BEST_OK) break;
+            if ((s = restore()) != BEST_OK) break;
+            ctx->profiling = true;
+            ctx->ev_used = 0;
+            s = best_collision_eval(ctx, f_dev, t, Ctmp, nullptr, stream);
+            double ms = 0.0;
+            int64_t n = 0;
+            if (s == BEST_OK) s = best_profile_read(ctx, &ms, &n);
+            ctx->profiling = prof;
+            ctx->ev_used = 0;
+            if (s == BEST_OK && ms < best_ms) {
+                best_ms = ms;
+                best_v = v;
+            }
+        }
+        if (s != BEST_OK) break;
+        if ((s = set_variant(ctx, best_v)) != BEST_OK) break;
+        s = restore();
+        if (ctas_per_sm) *ctas_per_sm = ctx->variant_mb[best_v];
+    } while (false);
+    release();
+    return s;
 }
 
 int32_t best_num_tasks(const best_ctx* ctx) { return ctx ? ctx->geo.n_tasks : 0; }
@@ -753,6 +908,13 @@ best_status best_profile_enable(best_ctx* ctx, int32_t enable) {
     if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
     ctx->profiling = enable != 0;
     ctx->ev_used = 0;
+    // events for two sweeps of launches, created now rather than during a capture
+    const size_t want = 4 * static_cast<size_t>(ctx->max_nitn) + 8;
+    while (ctx->profiling && ctx->ev.size() < want) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        ctx->ev.push_back(e);
+    }
     return BEST_OK;
 }
 

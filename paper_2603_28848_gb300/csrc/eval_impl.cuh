@@ -392,14 +392,10 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
     __syncthreads();
 }
 
-#ifndef BEST_EVAL_MIN_BLOCKS_N4
-#define BEST_EVAL_MIN_BLOCKS_N4 5      // CTAs per SM the FP32 2->2 kernel is register-limited to
-#endif
-#ifndef BEST_EVAL_MIN_BLOCKS_N6
-#define BEST_EVAL_MIN_BLOCKS_N6 2
-#endif
-template <typename R, int NMAX>
-__global__ void __launch_bounds__(kThreads, (sizeof(R) == 8 ? 1 : (NMAX <= 4 ? BEST_EVAL_MIN_BLOCKS_N4 : BEST_EVAL_MIN_BLOCKS_N6)))
+// MB: CTAs per SM the kernel is register-limited to (__launch_bounds__);
+// several values are instantiated and the autotuner picks one at run time.
+template <typename R, int NMAX, int MB>
+__global__ void __launch_bounds__(kThreads, MB)
 eval_kernel(EvalParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* s_spline = reinterpret_cast<R*>(smem_raw);
