@@ -253,7 +253,7 @@ def run_native(args, rank, world):
             "kernel": "best::eval_kernel<float,4> (persistent sample kernel)",
             "flops_per_sample": flops_per_sample(n_legs), "mufu_per_sample": mufu_per_sample(n_legs),
             "samples_per_launch": samples_per_launch, "launch_ms": per_launch_ms,
-            "share_of_step": kern_ms / ms if ms > 0 else None,
+            "share_of_step": kern_ms / (ms / args.steps) if ms > 0 else None,
             "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz max SM clock (nominal unit "
                           "counts; MEASURED_PEAKS.json has no FP32 figure)"}
 

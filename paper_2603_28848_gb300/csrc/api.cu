@@ -367,17 +367,22 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
         const PhiloxKey key = philox_key(g.seed);
         for (int r = 0; r < 20; ++r) P.rk[r] = key.k[r];
         void* args[] = {&P};
+        // inside a stream capture the events must become event-record nodes
+        unsigned rec_flags = cudaEventRecordDefault;
         if (ctx->profiling) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            CK(cudaStreamIsCapturing(st, &cs));
+            if (cs == cudaStreamCaptureStatusActive) rec_flags = cudaEventRecordExternal;
             while (ctx->ev.size() < ctx->ev_used + 2) {
                 cudaEvent_t e;
                 CK(cudaEventCreate(&e));
                 ctx->ev.push_back(e);
             }
-            CK(cudaEventRecord(ctx->ev[ctx->ev_used], st));
+            CK(cudaEventRecordWithFlags(ctx->ev[ctx->ev_used], st, rec_flags));
         }
         CK(cudaLaunchKernel(ctx->eval_fn, dim3(ctx->grid), dim3(kThreads), args, ctx->eval_smem, st));
         if (ctx->profiling) {
-            CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], st));
+            CK(cudaEventRecordWithFlags(ctx->ev[ctx->ev_used + 1], st, rec_flags));
             ctx->ev_used += 2;
         }
         refine_kernel<<<pl.n_active, 128, ctx->refine_smem, st>>>(

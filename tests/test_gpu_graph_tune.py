@@ -68,3 +68,17 @@ def test_autotune_preserves_state_and_parity():
     z = np.abs(mean - om) / np.sqrt(terr ** 2 + oe ** 2)
     assert np.mean(z < 3) >= 0.95 and np.max(z) < 6
     col.close()
+
+
+def test_profiling_inside_graph():
+    """Timing events captured into the step graph report the sample-kernel
+    launches of the last replayed step."""
+    import torch
+    prob, f0 = W.c1_maxwell_2to2(n=12, neval=5000, nitn=3)
+    col, logf, t, dt = _state(prob, f0, W.PREC_FP32)
+    col.profile(True)
+    col.evolve(logf, t, dt, 2, 0.1, "heun")
+    ms, n = col.profile_read()
+    assert n == 2 * 3 and ms > 0
+    col.profile(False)
+    col.close()
