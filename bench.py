@@ -33,6 +33,8 @@ METRIC = "C[f] grid sweeps/s and integrand evals/s, FP32 vs FP64 path, at 1e-4 r
 UNIT = "sweeps/s"
 WORKLOAD = "c2_bose_2to2"
 DT = 0.5          # requested Heun step (bounded by Eq. (16) inside each step)
+# DRAM bytes per sample-kernel launch from the last ncu capture of this kernel version
+TRAFFIC_BYTES_PER_LAUNCH = 1.493248e6
 FP32_PEAK_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
@@ -249,7 +251,10 @@ def run_native(args, rank, world):
     peaks = measured_peaks()
     peak = FP32_PEAK_TFLOPS_NOMINAL
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the sample kernel "
+                              "(profiles/eval_kernel_f32_c2_bose_2to2.md); the tables it reads do not "
+                              "grow with the sample count",
             "kernel": "best::eval_kernel<float,4> (persistent sample kernel)",
             "flops_per_sample": flops_per_sample(n_legs), "mufu_per_sample": mufu_per_sample(n_legs),
             "samples_per_launch": samples_per_launch, "launch_ms": per_launch_ms,
