@@ -176,6 +176,25 @@ best_status best_evolve(best_ctx* ctx, int32_t method, int32_t n_steps, double* 
 best_status best_autotune(best_ctx* ctx, const double* f_dev, double t, int32_t* ctas_per_sm,
                           void* stream);
 
+/*
+ * Vector-Jacobian product of the fixed-sample collision integral (the paper
+ * has no gradients; Eq. (3), (7), (12) define the function).  C~ is C of
+ * Eq. (7) estimated with one VEGAS iteration per task on the context's
+ * current maps and a reserved Philox iteration index, the evaluation counter
+ * left unchanged: common random numbers, so repeated calls use identical
+ * samples and C~ is a deterministic, piecewise smooth function of f, the
+ * masses and the couplings.  For L = sum_{a,i} v[a*n+i] C~_a(p_i) the call
+ * writes C~ (C_dev [n_species*n_grid]), dL/df (gf_dev [n_species*n_grid],
+ * through the spline and the Eq. (13) tail fits), dL/dm_s (gm_dev
+ * [n_species], at the masses m_s(t)) and dL/dcoupling (gcoupling_dev
+ * [n_processes]).  Samples are recomputed, not stored.  Maps and the
+ * counter are not modified.  Gradient sums use FP64 atomics, so their last
+ * bits can vary between calls.
+ */
+best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, const double* v_dev,
+                               double* C_dev, double* gf_dev, double* gm_dev, double* gcoupling_dev,
+                               void* stream);
+
 /* Context geometry. */
 int32_t best_num_tasks(const best_ctx* ctx);
 int32_t best_num_side_integrals(const best_ctx* ctx);

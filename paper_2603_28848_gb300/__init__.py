@@ -13,7 +13,7 @@ import numpy as np
 from . import _lib
 from ._lib import BestError, check
 
-__all__ = ["Collision", "BestError", "build", "config_from_problem"]
+__all__ = ["Collision", "BestError", "build", "config_from_problem", "fixed_sample_collision"]
 
 
 def build(verbose=False, force=False):
@@ -163,6 +163,21 @@ class Collision:
         check(self.lib.best_autotune(self.ctx, _ptr(f), float(t), ctypes.byref(mb), _stream(stream)), self.ctx)
         return mb.value
 
+    def vjp(self, f, v, t=0.0, stream=None):
+        """(C~, dL/df, dL/dm, dL/dcoupling) of L = sum(v * C~) for the
+        fixed-sample integral C~ (one iteration on the current maps)."""
+        import torch
+        n = self.n_species * self.n_grid
+        _require(f, n, "f")
+        _require(v, n, "v")
+        C = torch.empty_like(f)
+        gf = torch.empty_like(f)
+        gm = torch.empty(self.n_species, dtype=torch.float64, device=f.device)
+        gl = torch.empty(len(self.problem.processes), dtype=torch.float64, device=f.device)
+        check(self.lib.best_collision_vjp(self.ctx, _ptr(f), float(t), _ptr(v), _ptr(C), _ptr(gf), _ptr(gm),
+                                          _ptr(gl), _stream(stream)), self.ctx)
+        return C, gf, gm, gl
+
     # -- inspection -------------------------------------------------------------
     def check(self, stream=None):
         check(self.lib.best_check(self.ctx, _stream(stream)), self.ctx)
@@ -221,3 +236,56 @@ class Collision:
             self.close()
         except Exception:
             pass
+
+
+def _autograd_function():
+    import torch
+
+    class FixedSampleCollision(torch.autograd.Function):
+        """C~(f, m, lambda): the fixed-sample collision integral of a context
+        (one VEGAS iteration per task on its current maps, common random
+        numbers).  Forward and backward both run best_collision_vjp; the
+        backward pass recomputes the samples instead of storing them."""
+
+        @staticmethod
+        def forward(ctx, col, f, masses, couplings, t):
+            zero = torch.zeros_like(f)
+            C, _, _, _ = col.vjp(f.detach().contiguous(), zero, t)
+            ctx.col = col
+            ctx.t = t
+            ctx.save_for_backward(f)
+            return C
+
+        @staticmethod
+        def backward(ctx, grad_C):
+            (f,) = ctx.saved_tensors
+            _, gf, gm, gl = ctx.col.vjp(f.detach().contiguous(), grad_C.contiguous(), ctx.t)
+            return None, gf, gm, gl, None
+
+    return FixedSampleCollision
+
+
+_FSC = None
+
+
+def fixed_sample_collision(col, f, t=0.0, masses=None, couplings=None):
+    """Differentiable C~ of context `col` at grid values f (CUDA float64,
+    (n_species, n_grid)).  `masses` (n_species,) and `couplings`
+    (n_processes,) are optional tensors that must equal the context's m_s(t)
+    and couplings; pass them with requires_grad to receive dL/dm, dL/dlambda."""
+    import torch
+    global _FSC
+    if _FSC is None:
+        _FSC = _autograd_function()
+    prob = col.problem
+    m_now = torch.tensor([s.mass0 + s.mass1 * t for s in prob.species], dtype=torch.float64, device=f.device)
+    lam_now = torch.tensor([p.coupling for p in prob.processes], dtype=torch.float64, device=f.device)
+    if masses is None:
+        masses = m_now
+    elif not torch.allclose(masses.detach(), m_now, rtol=1e-12, atol=0):
+        raise BestError("masses must equal the context's m_s(t)")
+    if couplings is None:
+        couplings = lam_now
+    elif not torch.allclose(couplings.detach(), lam_now, rtol=1e-12, atol=0):
+        raise BestError("couplings must equal the context's couplings")
+    return _FSC.apply(col, f, masses, couplings, float(t))

@@ -47,6 +47,8 @@ SIGNATURES = {
     "best_step_heun": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "best_evolve": ([c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_double, c_void_p], c_int32),
     "best_autotune": ([c_void_p, c_void_p, c_double, POINTER(c_int32), c_void_p], c_int32),
+    "best_collision_vjp": ([c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                            c_void_p], c_int32),
     "best_num_tasks": ([c_void_p], c_int32),
     "best_num_side_integrals": ([c_void_p], c_int32),
     "best_sweep_samples": ([c_void_p, c_int32], c_int64),

@@ -19,7 +19,7 @@ __global__ void set_time_kernel(Geometry, TimeState*, const double*, double, int
 __global__ void spline_build_kernel(Geometry, const double*, int, const double*, TimeState*, SpeciesConst*,
                                     double*, double*, float*);
 __global__ void prepare_kernel(Geometry, const SideDesc*, const TaskDesc*, const double*, const double*,
-                               const TimeState*, const double*, TaskConst*, TaskAcc*);
+                               const TimeState*, const double*, TaskConst*, TaskAcc*, int);
 __global__ void refine_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskConst*, const int32_t*,
                               const int32_t*, const Segment*, const double*, double*, TaskAcc*, TaskConst*);
 __global__ void assemble_kernel(Geometry, const SideDesc*, TaskAcc*, TimeState*, double*, double*, double*);
@@ -29,6 +29,15 @@ __global__ void heun_correct_kernel(Geometry, double*, const double*, const doub
                                     double*, TimeState*);
 // variants.cu
 int eval_variants(bool f32, int nmax, void** fn, int* mb);
+// vjp.cu
+void* vjp_kernel_ptr(bool f32, int nmax);
+__global__ void vjp_seed_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskConst*, const double*, double*);
+__global__ void vjp_task_kernel(Geometry, const int32_t*, const int32_t*, const Segment*, const double*, int, double*);
+__global__ void vjp_finish_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskConst*, const SpeciesConst*,
+                                  const TimeState*, const double*, const double*, const double*, const double*,
+                                  double*, double*, double*, double*, double*, int);
+__global__ void spline_adjoint_kernel(Geometry, const double*, const double*, const SpeciesConst*, const TimeState*,
+                                      const double*, const double*, double*, double*);
 }  // namespace best
 
 using namespace best;
@@ -106,6 +115,14 @@ struct best_ctx {
     int g_launches = 0;
     size_t g_events = 0;            // timing events recorded by one replay
     double* d_dtreq = nullptr;      // requested step, read by the graph
+    // adjoint (best_collision_vjp)
+    double* d_gcoef = nullptr;      // [species][n-1][4]
+    double* d_vjp_tot = nullptr;    // [task][16]
+    double* d_u = nullptr;          // [task]
+    double* d_gtail = nullptr;      // [species][4]
+    double* d_coupling = nullptr;   // [process]
+    int n_processes = 0;
+    size_t vjp_smem = 0;
     // timing of the sample kernel (best_profile_*)
     bool profiling = false;
     std::vector<cudaEvent_t> ev;    // start/stop pairs
@@ -160,7 +177,8 @@ void free_all(best_ctx* c) {
     c->plans.clear();
     void* bufs[] = {c->d_sides, c->d_tasks, c->d_tconst, c->d_acc, c->d_sconst, c->d_ts, c->d_edges,
                     c->d_knots, c->d_knots32, c->d_coef64, c->d_coef32, c->d_fgrid, c->d_mass0, c->d_mass1,
-                    c->d_partials, c->d_k1, c->d_k2, c->d_fstar, c->d_prev, c->d_dtreq};
+                    c->d_partials, c->d_k1, c->d_k2, c->d_fstar, c->d_prev, c->d_dtreq,
+                    c->d_gcoef, c->d_vjp_tot, c->d_u, c->d_gtail, c->d_coupling};
     if (c->graph) cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
     for (void* b : bufs) cudaFree(b);
@@ -267,7 +285,7 @@ best_status build_plan(best_ctx* ctx, int it, IterPlan& plan) {
     for (size_t k = 0; k < segs.size(); ++k) {
         segs[k].part = off;
         const TaskDesc& td = ctx->tasks[segs[k].task];
-        off += 2 + static_cast<int64_t>(td.dim) * td.nbins;
+        off += record_doubles(td.dim, td.nbins);
     }
     {
         size_t k = 0;
@@ -343,7 +361,7 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
         g, src, src_mode, ctx->d_knots, ctx->d_ts, ctx->d_sconst, ctx->d_fgrid, ctx->d_coef64, ctx->d_coef32);
     prepare_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_knots,
                                                             ctx->d_fgrid, ctx->d_ts, ctx->d_prev, ctx->d_tconst,
-                                                            ctx->d_acc);
+                                                            ctx->d_acc, 1);
     ctx->launches += 2;
     const bool f32 = ctx->precision == BEST_FP32;
     for (int it = 0; it < ctx->max_nitn; ++it) {
@@ -655,6 +673,23 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     CKI(dalloc(&ctx->d_fstar, static_cast<size_t>(S) * n));
     CKI(dalloc(&ctx->d_prev, static_cast<size_t>(T)));
     CKI(dalloc(&ctx->d_dtreq, 1));
+    CKI(dalloc(&ctx->d_gcoef, static_cast<size_t>(S) * (n - 1) * 4));
+    CKI(dalloc(&ctx->d_vjp_tot, static_cast<size_t>(T) * 16));
+    CKI(dalloc(&ctx->d_u, static_cast<size_t>(T)));
+    CKI(dalloc(&ctx->d_gtail, static_cast<size_t>(S) * 4));
+    CKI(dalloc(&ctx->d_coupling, static_cast<size_t>(cfg->n_processes)));
+    {
+        std::vector<double> lam(cfg->n_processes);
+        for (int p = 0; p < cfg->n_processes; ++p) lam[p] = cfg->processes[p].coupling;
+        CKI(cudaMemcpy(ctx->d_coupling, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice));
+        ctx->n_processes = cfg->n_processes;
+        const size_t rs = f32 ? 4 : 8;
+        const size_t spl = static_cast<size_t>(S) * 4 * (n - 1) + n;
+        const size_t ngc = static_cast<size_t>(S) * 4 * (n - 1);
+        const size_t map_elems = static_cast<size_t>(kMaxDim) * nb_max;
+        ctx->vjp_smem = rs * ((spl + 3) & ~size_t(3)) + 2 * rs * map_elems + sizeof(double) * ngc +
+                        12 * 8 * sizeof(double);
+    }
     CKI(cudaMemset(ctx->d_prev, 0, sizeof(double) * T));
     CKI(cudaMemcpy(ctx->d_sides, ctx->sides.data(), g.n_side * sizeof(SideDesc), cudaMemcpyHostToDevice));
     CKI(cudaMemcpy(ctx->d_tasks, ctx->tasks.data(), T * sizeof(TaskDesc), cudaMemcpyHostToDevice));
@@ -831,6 +866,70 @@ best_status best_autotune(best_ctx* ctx, const double* f_dev, double t, int32_t*
     } while (false);
     release();
     return s;
+}
+
+best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, const double* v_dev, double* C_dev,
+                               double* gf_dev, double* gm_dev, double* gcoupling_dev, void* stream) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    if (!f_dev || !v_dev || !C_dev || !gf_dev || !gm_dev || !gcoupling_dev)
+        return fail(ctx, BEST_ERR_INVALID, "f, v, C, gf, gm and gcoupling must not be NULL");
+    if (!std::isfinite(t)) return fail(ctx, BEST_ERR_INVALID, "t must be finite");
+    const Geometry& g = ctx->geo;
+    const bool f32 = ctx->precision == BEST_FP32;
+    void* fn = vjp_kernel_ptr(f32, ctx->nmax_legs);
+    int max_optin = 0, dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (ctx->vjp_smem > static_cast<size_t>(max_optin))
+        return fail(ctx, BEST_ERR_INVALID, "adjoint tables need %zu B of shared memory (max %d)", ctx->vjp_smem, max_optin);
+    cudaFuncAttributes fa{};
+    CK(cudaFuncGetAttributes(&fa, fn));
+    if (static_cast<size_t>(fa.maxDynamicSharedSizeBytes) < ctx->vjp_smem)
+        CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(ctx->vjp_smem)));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ctx->launches = 0;
+    set_time_kernel<<<1, 32, 0, st>>>(g, ctx->d_ts, nullptr, t, 0, ctx->d_mass0, ctx->d_mass1);
+    spline_build_kernel<<<g.n_species, 256, ctx->spline_smem, st>>>(
+        g, f_dev, 0, ctx->d_knots, ctx->d_ts, ctx->d_sconst, ctx->d_fgrid, ctx->d_coef64, ctx->d_coef32);
+    prepare_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_knots, ctx->d_fgrid,
+                                                            ctx->d_ts, ctx->d_prev, ctx->d_tconst, ctx->d_acc, 0);
+    vjp_seed_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_tconst, v_dev,
+                                                             ctx->d_u);
+    CK(cudaMemsetAsync(ctx->d_gcoef, 0, sizeof(double) * g.n_species * (g.n_grid - 1) * 4, st));
+    const IterPlan& pl = ctx->plans[0];
+    VjpParams V;
+    EvalParams& P = V.E;
+    P.geo = g;
+    P.sides = ctx->d_sides;
+    P.tasks = ctx->d_tasks;
+    P.tconst = ctx->d_tconst;
+    P.sconst = ctx->d_sconst;
+    P.ts = ctx->d_ts;
+    P.edges = ctx->d_edges;
+    P.segs = pl.d_segs;
+    P.cta_seg = pl.d_cta_seg;
+    P.coef = f32 ? static_cast<const void*>(ctx->d_coef32) : static_cast<const void*>(ctx->d_coef64);
+    P.knots = f32 ? static_cast<const void*>(ctx->d_knots32) : static_cast<const void*>(ctx->d_knots);
+    P.partials = ctx->d_partials;
+    P.itn = 0xFFFFu;                                   // the adjoint's reserved iteration index
+    P.smem_spline_elems = g.n_species * 4 * (g.n_grid - 1) + g.n_grid;
+    const PhiloxKey key = philox_key(g.seed);
+    for (int r = 0; r < 20; ++r) P.rk[r] = key.k[r];
+    V.task_u = ctx->d_u;
+    V.gcoef = ctx->d_gcoef;
+    void* args[] = {&V};
+    CK(cudaLaunchKernel(fn, dim3(ctx->grid), dim3(kThreads), args, ctx->vjp_smem, st));
+    vjp_task_kernel<<<(pl.n_active + 127) / 128, 128, 0, st>>>(g, pl.d_active, pl.d_task_seg, pl.d_segs,
+                                                               ctx->d_partials, pl.n_active, ctx->d_vjp_tot);
+    vjp_finish_kernel<<<1, 32, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_tconst, ctx->d_sconst, ctx->d_ts, v_dev,
+                                        ctx->d_u, ctx->d_vjp_tot, ctx->d_coupling, C_dev, gf_dev, gm_dev,
+                                        gcoupling_dev, ctx->d_gtail, ctx->n_processes);
+    spline_adjoint_kernel<<<g.n_species, 32, ctx->spline_smem, st>>>(g, ctx->d_knots, ctx->d_fgrid, ctx->d_sconst,
+                                                                     ctx->d_ts, ctx->d_gcoef, ctx->d_gtail, gf_dev,
+                                                                     gm_dev);
+    ctx->launches = 9;
+    CK(cudaGetLastError());
+    return BEST_OK;
 }
 
 int32_t best_num_tasks(const best_ctx* ctx) { return ctx ? ctx->geo.n_tasks : 0; }

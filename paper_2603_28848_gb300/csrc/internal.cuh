@@ -133,4 +133,18 @@ struct EvalParams {
     uint32_t rk[20];            // Philox round keys (kernel parameters: read from the constant bank)
 };
 
+// Arguments of the adjoint sample kernel.
+struct VjpParams {
+    EvalParams E;
+    const double* task_u;       // per task: v_{a,i} mult sign K scale / N
+    double* gcoef;              // [species][n-1][4] FP64, accumulated with atomics
+};
+
+// Doubles per partial record: the sample kernel writes 2 + D nb, the adjoint
+// kernel up to 12 values.
+__host__ __device__ inline int64_t record_doubles(int D, int nb) {
+    const int64_t r = 2 + static_cast<int64_t>(D) * nb;
+    return r < 16 ? 16 : r;
+}
+
 }  // namespace best

@@ -149,7 +149,7 @@ __device__ inline double clamp_scale(double scale, double obs_factor) {
 __global__ void prepare_kernel(Geometry g, const SideDesc* __restrict__ sides,
                                const TaskDesc* __restrict__ tasks, const double* __restrict__ knots,
                                const double* __restrict__ fgrid, const TimeState* ts,
-                               const double* __restrict__ prev, TaskConst* tconst, TaskAcc* acc) {
+                               const double* __restrict__ prev, TaskConst* tconst, TaskAcc* acc, int reset_acc) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.n_tasks) return;
     const TaskDesc td = tasks[t];
@@ -173,6 +173,7 @@ __global__ void prepare_kernel(Geometry g, const SideDesc* __restrict__ sides,
     const double est = prev[t];
     c.scale = clamp_scale(est > 0.0 && c.K > 0.0 ? est / c.K : (c.f_obs > 0.0 ? c.f_obs : 1.0), c.obs_factor);
     tconst[t] = c;
+    if (!reset_acc) return;
     TaskAcc z;
     z.sum_inv_var = 0.0; z.sum_mean_inv_var = 0.0; z.sum_exact = 0.0; z.n_exact = 0.0;
     z.mean = 0.0; z.err = 0.0;

@@ -1,0 +1,373 @@
+// Adjoint sample kernel: vector-Jacobian products of the fixed-sample
+// collision integral C~ (one VEGAS iteration per task on the current maps,
+// Philox iteration index kVjpIteration) with respect to the grid values f_j,
+// the masses and the couplings, by recomputing every sample (nothing is
+// stored).  Included by vjp.cu.
+//
+// Per sample, with w_n the normalised weight of the sample kernel,
+//   w_n = c0 * prod_k fac_k * base,  fac_k = ca_k + cb_k f_k,
+//   base = prod r^2 sin(theta) / prod E_k (non-observed legs) * G(dE) * J:
+//   d w_n / d f_k      = cb_k * c0 * base * prod_{l != k} fac_l  (0 where f is clamped)
+//   d w_n / d f_obs    = w_n / c0 * (d obs_factor / d f_obs) / scale
+//   d w_n / d E_k      = w_n * (-1/E_k - dE s_k / sigma^2)      (1/E_k and the Gaussian)
+//   d E_k / d m        = m / E_k
+// f_k from the spline scatters d w_n / d f_k * (1, t, t^2, t^3) into the
+// coefficient gradients of its interval; f_k from an Eq. (13) tail,
+// f = 1/(exp(z) - eta), z = a + b E, contributes through dz: d f / d z =
+// -f (1 + eta f) to (a, b) and, via E_cons, to the mass.
+#pragma once
+
+#include "eval_impl.cuh"
+
+namespace best {
+
+constexpr uint32_t kVjpIteration = 0xFFFF;
+
+
+template <typename R>
+struct Hit {
+    R f;        // value (clamped)
+    R d;        // 1 where f follows the polynomial, 0 where it was clamped
+    int j;      // interval
+    R t;        // q - q_j
+};
+
+template <typename R>
+__device__ __forceinline__ Hit<R> spline_hit(const SplineView<R>& sv, R q, const Geometry& g, R inv_step, R q0,
+                                             R lq0_step, bool fd) {
+    int j;
+    if (g.log_spaced) {
+        j = static_cast<int>(fmaf(__log2f(static_cast<float>(q)), static_cast<float>(inv_step),
+                                  -static_cast<float>(lq0_step)));
+    } else {
+        j = static_cast<int>(static_cast<float>((q - q0) * inv_step));
+    }
+    j = min(max(j, 0), g.n_grid - 2);
+    const R t = q - sv.knot[j];
+    R f;
+    if constexpr (sizeof(R) == 4) {
+        const float4 c = reinterpret_cast<const float4*>(sv.coef)[j];
+        f = fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
+    } else {
+        const double2* cp = reinterpret_cast<const double2*>(sv.coef) + 2 * j;
+        const double2 lo = cp[0], hi = cp[1];
+        f = fma(fma(fma(hi.y, t, hi.x), t, lo.y), t, lo.x);
+    }
+    Hit<R> h;
+    h.j = j;
+    h.t = t;
+    h.d = R(1);
+    if (!(f > R(0))) { f = R(0); h.d = R(0); }
+    if (fd && f > R(1)) { f = R(1); h.d = R(0); }
+    h.f = f;
+    return h;
+}
+
+template <typename R, int NLEG>
+__device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& seg, const SideDesc& sd,
+                                            const TaskDesc& td, const TaskConst& tc, R* s_spline,
+                                            Real2<R>* s_map, double* s_gc, double* s_red) {
+    const EvalParams& P = V.E;
+    constexpr int NI = NLEG - 2;
+    constexpr int D = 3 * NI;
+    constexpr bool F32 = RMath<R>::kF32;
+    using SS = StreamShape<D, F32>;
+    constexpr int G = SS::kGroup;
+    const Geometry& g = P.geo;
+    const int nb = td.nbins;
+    const int tid = threadIdx.x;
+
+    const double* edges = P.edges + static_cast<int64_t>(seg.task) * g.map_stride;
+    for (int k = tid; k < D * nb; k += blockDim.x) {
+        const int d = k / nb;
+        const int b = k - d * nb;
+        const double e0 = edges[d * (nb + 1) + b];
+        const double e1 = edges[d * (nb + 1) + b + 1];
+        double lo, sc;
+        switch (d % 3) {
+            case 0: lo = g.q_min; sc = g.q_max - g.q_min; break;
+            case 1: lo = 0.0; sc = kPi; break;
+            default: lo = -kPi; sc = kTwoPi; break;
+        }
+        Real2<R> v;
+        v.y0 = static_cast<R>(lo + sc * e0);
+        v.dy = static_cast<R>(sc * (e1 - e0));
+        s_map[k] = v;
+    }
+
+    // per-segment constants (as in the sample kernel)
+    const TimeState& ts = *P.ts;
+    const int cons = sd.cons;
+    const bool cons_in = (sd.in_mask >> cons) & 1;
+    const R flip = cons_in ? R(-1) : R(1);
+    const bool is_loss = td.term == 1;
+    const R s_obs = ((sd.in_mask >> sd.obs) & 1) ? R(1) : R(-1);
+    const R pobs_sig = flip * s_obs * static_cast<R>(tc.p_obs);
+    const R sgn_obs_E = s_obs * static_cast<R>(tc.E_obs);
+    R sig[NI], sgnE[NI], m2[NI], ca[NI], cb[NI], mass[NI];
+    int spc[NI], fdj[NI];
+#pragma unroll
+    for (int j = 0; j < NI; ++j) {
+        const int k = sd.integ[j];
+        const bool kin = (sd.in_mask >> k) & 1;
+        const bool own = (sd.own_mask >> k) & 1;
+        const int sp = sd.leg_species[k];
+        const double eta = P.sconst[sp].eta;
+        sig[j] = flip * (kin ? R(1) : R(-1));
+        sgnE[j] = kin ? R(1) : R(-1);
+        const double m = ts.mass[sp];
+        mass[j] = static_cast<R>(m);
+        m2[j] = static_cast<R>(m * m);
+        const bool enh = own != is_loss;
+        ca[j] = enh ? R(1) : R(0);
+        cb[j] = enh ? static_cast<R>(eta) : R(1);
+        spc[j] = sp;
+        fdj[j] = P.sconst[sp].stat == BEST_FD;
+    }
+    const int spcn = sd.leg_species[cons];
+    const double eta_cd = P.sconst[spcn].eta;
+    const R eta_c = static_cast<R>(eta_cd);
+    const bool fd_c = P.sconst[spcn].stat == BEST_FD;
+    const R sgn_cons = cons_in ? R(1) : R(-1);
+    const R mass_c = static_cast<R>(ts.mass[spcn]);
+    const R m2c = mass_c * mass_c;
+    const bool own_c = (sd.own_mask >> cons) & 1;
+    const bool enh_c = own_c != is_loss;
+    const R cac = enh_c ? R(1) : R(0);
+    const R cbc = enh_c ? eta_c : R(1);
+    const R tlo_a = static_cast<R>(P.sconst[spcn].tail_lo_a), tlo_b = static_cast<R>(P.sconst[spcn].tail_lo_b);
+    const R thi_a = static_cast<R>(P.sconst[spcn].tail_hi_a), thi_b = static_cast<R>(P.sconst[spcn].tail_hi_b);
+    const R a = static_cast<R>(ts.a), inv_a = static_cast<R>(1.0 / ts.a);
+    const R c0 = tc.E_obs < g.e_cut ? R(0) : static_cast<R>(tc.obs_factor / tc.scale);
+    const R gauss_k = static_cast<R>(-1.4426950408889634 / (2.0 * sd.sigma * sd.sigma));
+    const R inv_sig2 = static_cast<R>(1.0 / (sd.sigma * sd.sigma));
+    const R e_cut = static_cast<R>(g.e_cut);
+    const R inv_Eobs = static_cast<R>(1.0 / tc.E_obs);
+    const R U = static_cast<R>(V.task_u[seg.task]);
+    const R nbR = static_cast<R>(nb);
+    const R q0 = static_cast<R>(g.q_min), qN = static_cast<R>(g.q_max);
+    const R lq0_step = static_cast<R>(g.log_spaced ? std::log2(g.q_min) / (g.log_step / 0.6931471805599453) : 0.0);
+    const R inv_step = static_cast<R>(1.0 / (g.log_spaced ? g.log_step / 0.6931471805599453 : g.log_step));
+    const int ncoef = 4 * (g.n_grid - 1);
+    const R* knots = s_spline + g.n_species * ncoef;
+    __syncthreads();
+
+    // accumulators: sum w_n, d/d f_obs (w_n / c0), mass via E_obs, E_cons,
+    // each integrated leg, tail (a, b) at the low and high ends
+    Acc<R> acc_w, acc_fobs, acc_mobs, acc_mc, acc_tla, acc_tlb, acc_tha, acc_thb;
+    Acc<R> acc_m[NI];
+    const int64_t N = td.neval;
+    const uint32_t task = static_cast<uint32_t>(seg.task);
+    const int32_t g1 = static_cast<int32_t>(seg.g1);
+    for (int32_t grp = static_cast<int32_t>(seg.g0) + tid; grp < g1; grp += blockDim.x) {
+        uint32_t uw[F32 ? SS::kUniforms : 1];
+        R u[F32 ? 1 : SS::kUniforms];
+        if constexpr (F32) group_words<D>(uw, grp, P.itn, ts.call, task, P.rk);
+        else group_uniforms<D, F32, R>(u, grp, P.itn, ts.call, task, P.rk);
+#pragma unroll
+        for (int sgi = 0; sgi < G; ++sgi) {
+            const bool valid = static_cast<int64_t>(grp) * G + sgi < N;
+            R y[D];
+            R jac = R(1);
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                int b;
+                R fr;
+                if constexpr (F32) {
+                    const uint32_t m = (uw[sgi * D + d] >> 9) * (2u * nb) + static_cast<uint32_t>(nb);
+                    b = static_cast<int>(m >> 24);
+                    fr = static_cast<float>(m & 0xFFFFFFu) * 5.9604644775390625e-08f;
+                } else {
+                    const R t = u[sgi * D + d] * nbR;
+                    b = static_cast<int>(t);
+                    b = b < nb - 1 ? b : nb - 1;
+                    fr = t - static_cast<R>(b);
+                }
+                const Real2<R> e = s_map[d * nb + b];
+                y[d] = fma(e.dy, fr, e.y0);
+                jac *= e.dy;
+            }
+            R px = R(0), py = R(0), pz = pobs_sig;
+            R dE = sgn_obs_E;
+            R meas = jac;
+            R rinv = R(1);
+            bool cut = false;
+            R fac[NI + 1], dfac[NI + 1], tl[NI + 1], rE[NI];
+            int jl[NI + 1];
+#pragma unroll
+            for (int j = 0; j < NI; ++j) {
+                const R r = y[3 * j];
+                R st, ct, sp, cp;
+                RMath<R>::sincos_(y[3 * j + 1], &st, &ct);
+                RMath<R>::sincos_(y[3 * j + 2], &sp, &cp);
+                const R p = r * inv_a;
+                const R ps = p * st;
+                px = fma(-sig[j] * ps, cp, px);
+                py = fma(-sig[j] * ps, sp, py);
+                pz = fma(sig[j] * p, ct, pz);
+                const R E2 = fma(p, p, m2[j]);
+                const R rr = RMath<R>::rsqrt_(E2);
+                const R E = E2 * rr;
+                cut |= E < e_cut;
+                dE = fma(sgnE[j], E, dE);
+                meas *= r * r * st;
+                rinv *= rr;
+                rE[j] = rr;
+                const SplineView<R> sv{s_spline + spc[j] * ncoef, knots};
+                const Hit<R> h = spline_hit<R>(sv, r, g, inv_step, q0, lq0_step, fdj[j]);
+                fac[j] = fma(cb[j], h.f, ca[j]);
+                dfac[j] = cb[j] * h.d;
+                jl[j] = h.j;
+                tl[j] = h.t;
+            }
+            const R pc2 = fma(px, px, fma(py, py, pz * pz));
+            const R Ec2 = pc2 + m2c;
+            const R rEc = RMath<R>::rsqrt_(Ec2 > R(0) ? Ec2 : R(1e-30));
+            const R Ec = Ec2 * rEc;
+            cut |= Ec < e_cut;
+            dE = fma(sgn_cons, Ec, dE);
+            const R qc = pc2 * (pc2 > R(0) ? RMath<R>::rsqrt_(pc2) : R(0)) * a;
+            const bool below = qc < q0, above = qc > qN;
+            const bool inside = !below && !above;
+            R fc, dfdz = R(0);
+            {
+                const SplineView<R> sv{s_spline + spcn * ncoef, knots};
+                const Hit<R> h = spline_hit<R>(sv, inside ? qc : (below ? q0 : qN), g, inv_step, q0, lq0_step, fd_c);
+                jl[NI] = h.j;
+                tl[NI] = h.t;
+                if (inside) {
+                    fc = h.f;
+                    dfac[NI] = cbc * h.d;
+                } else {
+                    const R x = below ? fma(tlo_b, Ec, tlo_a) : fma(thi_b, Ec, thi_a);
+                    R ft;
+                    if constexpr (F32) {
+                        ft = tail_f32(x, eta_c);
+                    } else {
+                        const R den = eta_c == R(1) ? expm1(x) : exp(x) - eta_c;
+                        ft = den > R(0) ? R(1) / den : R(0);
+                    }
+                    dfdz = -ft * fma(eta_c, ft, R(1));
+                    if (fd_c && ft > R(1)) { ft = R(1); dfdz = R(0); }
+                    fc = ft;
+                    dfac[NI] = cbc;
+                }
+            }
+            fac[NI] = fma(cbc, fc, cac);
+            const R gs = RMath<R>::exp2_(gauss_k * dE * dE);
+            R base = meas * rinv * rEc * gs;
+            base = (cut || !valid) ? R(0) : base;
+            // products excluding each factor
+            R pre[NI + 2];
+            pre[0] = R(1);
+#pragma unroll
+            for (int k = 0; k <= NI; ++k) pre[k + 1] = pre[k] * fac[k];
+            const R F = pre[NI + 1];
+            const R wn = c0 * base * F;
+            acc_w.add(wn);
+            acc_fobs.add(base * F);
+            R suf = R(1);
+            R dwdf[NI + 1];
+#pragma unroll
+            for (int k = NI; k >= 0; --k) {
+                dwdf[k] = c0 * base * pre[k] * suf * dfac[k];
+                suf *= fac[k];
+            }
+            const R dEterm = -wn * dE * inv_sig2;
+#pragma unroll
+            for (int j = 0; j < NI; ++j) {
+                const R gE = fma(-wn, rE[j], dEterm * sgnE[j]);
+                acc_m[j].add(gE * mass[j] * rE[j]);
+            }
+            const R gz = dwdf[NI] * dfdz;           // zero inside the grid
+            const R gEc = fma(-wn, rEc, fma(dEterm, sgn_cons, gz * (below ? tlo_b : thi_b)));
+            acc_mc.add(gEc * mass_c * rEc);
+            acc_mobs.add(fma(-wn, inv_Eobs, dEterm * s_obs));
+            if (below) { acc_tla.add(gz); acc_tlb.add(gz * Ec); }
+            if (above) { acc_tha.add(gz); acc_thb.add(gz * Ec); }
+            // spline coefficient gradients of this sample's lookups
+#pragma unroll
+            for (int k = 0; k <= NI; ++k) {
+                if (k == NI && !inside) continue;
+                const R gk = U * dwdf[k];
+                if (gk != R(0)) {
+                    // FP64 shared-memory accumulation of the FP32 contributions
+                    const int sp = k < NI ? spc[k] : spcn;
+                    double* dst = s_gc + sp * ncoef + 4 * jl[k];
+                    const double gd = static_cast<double>(gk), td_ = static_cast<double>(tl[k]);
+                    atomicAdd(dst + 0, gd);
+                    atomicAdd(dst + 1, gd * td_);
+                    atomicAdd(dst + 2, gd * td_ * td_);
+                    atomicAdd(dst + 3, gd * td_ * td_ * td_);
+                }
+            }
+        }
+    }
+
+    // ---- segment record: [w, fobs, mobs, mc, tla, tlb, tha, thb, m_0 .. m_{NI-1}] ----
+    constexpr int NV = 8 + NI;
+    double vals[NV];
+    vals[0] = acc_w.value(); vals[1] = acc_fobs.value(); vals[2] = acc_mobs.value(); vals[3] = acc_mc.value();
+    vals[4] = acc_tla.value(); vals[5] = acc_tlb.value(); vals[6] = acc_tha.value(); vals[7] = acc_thb.value();
+#pragma unroll
+    for (int j = 0; j < NI; ++j) vals[8 + j] = acc_m[j].value();
+    const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double v = vals[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_red[k * 8 + warp] = v;
+    }
+    __syncthreads();
+    double* part = P.partials + seg.part;
+    if (tid < NV) {
+        double v = 0.0;
+        for (int w = 0; w < nw; ++w) v += s_red[tid * 8 + w];
+        part[tid] = v;
+    }
+    __syncthreads();
+}
+
+template <typename R, int NMAX>
+__global__ void __launch_bounds__(kThreads, 1) vjp_kernel(VjpParams V) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const EvalParams& P = V.E;
+    R* s_spline = reinterpret_cast<R*>(smem_raw);
+    const int nsp = P.smem_spline_elems;
+    Real2<R>* s_map = reinterpret_cast<Real2<R>*>(s_spline + ((nsp + 3) & ~3));
+    const int map_elems = kMaxDim * P.geo.nbins_max;
+    const int ngc = 4 * (P.geo.n_grid - 1) * P.geo.n_species;
+    double* s_gc = reinterpret_cast<double*>(s_map + map_elems);     // 16-byte aligned: map_elems even
+    double* s_red = s_gc + ngc;
+    {
+        const R* gc = static_cast<const R*>(P.coef);
+        for (int k = threadIdx.x; k < ngc; k += blockDim.x) {
+            s_spline[k] = gc[k];
+            s_gc[k] = 0.0;
+        }
+        const R* gk = static_cast<const R*>(P.knots);
+        for (int k = threadIdx.x; k < P.geo.n_grid; k += blockDim.x) s_spline[ngc + k] = gk[k];
+    }
+    const int s0 = P.cta_seg[blockIdx.x], s1 = P.cta_seg[blockIdx.x + 1];
+    for (int si = s0; si < s1; ++si) {
+        const Segment seg = P.segs[si];
+        const TaskDesc td = P.tasks[seg.task];
+        const SideDesc& sd = P.sides[td.si];
+        const TaskConst tc = P.tconst[seg.task];
+        __syncthreads();
+        switch (sd.n) {
+            case 3: if constexpr (NMAX >= 3) vjp_segment<R, 3>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red); break;
+            case 4: if constexpr (NMAX >= 4) vjp_segment<R, 4>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red); break;
+            case 5: if constexpr (NMAX >= 5) vjp_segment<R, 5>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red); break;
+            case 6: if constexpr (NMAX >= 6) vjp_segment<R, 6>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red); break;
+            default: break;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < ngc; k += blockDim.x) {
+        const double v = s_gc[k];
+        if (v != 0.0) atomicAdd(V.gcoef + k, v);
+    }
+}
+
+}  // namespace best
