@@ -55,14 +55,54 @@ def mufu_per_sample(n_legs):
     return 6 * (n_legs - 2) + 4
 
 
-NEVAL = None      # per-task samples per iteration; None = the workload's own (1e6)
+NEVAL = None      # per-task samples per iteration; None = the workload's own
+WORKLOAD_KEY = "c2"
+# per workload: (builder, integrator, requested dt, start time, description)
+WORKLOADS = {
+    "c1": ("c1_maxwell_2to2", "euler", 0.1, 0.0,
+           "MB 2->2, m=1, 32 log points [0.01,20], sigma_E=0.01, 1e4 samples x 5 iterations, Euler dt=0.1"),
+    "c2": ("c2_bose_2to2", "heun", 0.5, 0.0,
+           "2 species (m=0, m=0.5) BE 2->2, 128 log points [1e-3,30], sigma_E=0.005, 1e6 samples x 8 "
+           "iterations per task, 512 tasks, Heun steps"),
+    "c3": ("c3_cannibal_2to3", "heun", 0.5, 0.0,
+           "BE 2<->3 m=1 (both pinned sides) + 2->2, 256 log points [0.01,25], sigma_E=0.01, 4e6 x 10, Heun"),
+    "c4": ("c4_multi_species", "heun", 0.5, 1.0,
+           "A (BE, m=1+0.1t) + B (FD, m=0.3): AB->AB, AA->AAA, AAA->BB, FRW a=(t/t0)^1/2, 512 log points "
+           "[0.01,25], budgets 1e5..1e7 per point x 2 iterations, Heun from t=1"),
+    "c5": ("c5_2to4", "heun", 0.5, 0.0,
+           "BE 2->4 m=1 (12-dim), 256 log points [0.01,25], sigma_E=0.01, 2e6 x 2, Heun + adjoint"),
+}
 
 
 def workload():
     import workloads as W
+    name = WORKLOADS[WORKLOAD_KEY][0]
+    fn = getattr(W, name)
     if NEVAL is not None:
-        return W.c2_bose_2to2(neval=NEVAL)
-    return W.c2_bose_2to2()
+        if WORKLOAD_KEY == "c4":
+            return fn(nmin=NEVAL, nmax=NEVAL * 100)
+        if WORKLOAD_KEY == "c3":
+            return fn(neval=NEVAL, with_2to2=True)
+        return fn(neval=NEVAL)
+    if WORKLOAD_KEY == "c3":
+        return fn(with_2to2=True)
+    return fn()
+
+
+def mean_flops_per_sample(prob, col):
+    """Sample-weighted FP32 FLOP count over the processes of a problem."""
+    n = prob.grid.n
+    tot = 0.0
+    cnt = 0.0
+    for p in prob.processes:
+        legs = len(p.species_in) + len(p.species_out)
+        sym = sorted(p.species_in) == sorted(p.species_out)
+        sides = len(set(p.species_in)) + (0 if sym else len(set(p.species_out)))
+        per = p.neval_per_point if p.neval_per_point is not None else [p.neval] * n
+        s = 2 * sides * sum(per)
+        tot += s * flops_per_sample(legs)
+        cnt += s
+    return tot / cnt, max(len(p.species_in) + len(p.species_out) for p in prob.processes)
 
 
 class Clocks:
@@ -136,7 +176,8 @@ def run_native(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     prob, f0 = workload()
-    n_legs = 4
+    wl = WORKLOADS[WORKLOAD_KEY]
+    method, DT, T0 = wl[1], wl[2], wl[3]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MiB > L2
 
     def barrier():
@@ -147,16 +188,19 @@ def run_native(args, rank, world):
     # Heun steps replayed from a CUDA graph (best_evolve) after the launch
     # shape was picked by the autotuner (best_autotune).
     col = Collision(prob, W.PREC_FP32)
+    col_tasks = col.n_tasks
     evals = col.sweep_samples()
     samples_per_launch = col.sweep_samples(0)
+    fps, n_legs = mean_flops_per_sample(prob, col)
+    sweeps_per_step = 2 if method == "heun" else 1
     logf = torch.tensor(np.log(f0), dtype=torch.float64, device="cuda").contiguous()
-    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    t = torch.full((1,), T0, dtype=torch.float64, device="cuda")
     dt = torch.full((1,), DT, dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        ctas_per_sm = col.autotune(torch.exp(logf), 0.0)
+        ctas_per_sm = col.autotune(torch.exp(logf), T0)
         col.profile(True)
-        col.evolve(logf, t, dt, args.warmup, DT, "heun", stream=stream)
+        col.evolve(logf, t, dt, args.warmup, DT, method, stream=stream)
         col.check(stream)
         clocks = Clocks(dev)
         torch.cuda.synchronize()
@@ -167,7 +211,7 @@ def run_native(args, rank, world):
         e0.record(stream)
         launches = 0
         for _ in range(args.steps):
-            col.evolve(logf, t, dt, 1, DT, "heun", stream=stream)
+            col.evolve(logf, t, dt, 1, DT, method, stream=stream)
             launches += col.last_launch_count()
             flush.zero_()                                  # evict L2 between steps
         e1.record(stream)
@@ -182,13 +226,13 @@ def run_native(args, rank, world):
         tt = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         ms = tt.item()
-    sweeps = 2 * args.steps * world
+    sweeps = sweeps_per_step * args.steps * world
     sweeps_per_s = sweeps / (ms / 1e3)
     med32, max32 = rel_err_stats(col)
 
     # ---------------- e2e: host buffers through the public API --------------------------
     h_logf = torch.tensor(np.log(f0), dtype=torch.float64).pin_memory()
-    h_t = torch.zeros(1, dtype=torch.float64).pin_memory()
+    h_t = torch.full((1,), T0, dtype=torch.float64).pin_memory()
     h_out = torch.empty_like(h_logf).pin_memory()
     h_tout = torch.empty_like(h_t).pin_memory()
     with torch.cuda.stream(stream):
@@ -200,7 +244,7 @@ def run_native(args, rank, world):
         for _ in range(args.steps):
             logf.copy_(h_logf, non_blocking=True)
             t.copy_(h_t, non_blocking=True)
-            col.evolve(logf, t, dt, 1, DT, "heun", stream=stream)
+            col.evolve(logf, t, dt, 1, DT, method, stream=stream)
             h_out.copy_(logf, non_blocking=True)
             h_tout.copy_(t, non_blocking=True)
             flush.zero_()
@@ -211,6 +255,23 @@ def run_native(args, rank, world):
         tt = torch.tensor([ms_e2e], device="cuda")
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         ms_e2e = tt.item()
+    vjp = None
+    if WORKLOAD_KEY == "c5" or args.vjp:
+        v = torch.ones_like(logf)
+        fcur = torch.exp(logf)
+        col.vjp(fcur, v, float(t.item()))
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record()
+        for _ in range(3):
+            col.vjp(fcur, v, float(t.item()))
+        b1.record()
+        torch.cuda.synchronize()
+        vms = b0.elapsed_time(b1) / 3
+        vjp = {"ms_per_vjp": vms, "samples": col.sweep_samples(0),
+               "samples_per_s": col.sweep_samples(0) / (vms / 1e3),
+               "what": "dL/df, dL/dm, dL/dcoupling of v.C~ (fixed samples, one iteration per task), FP32"}
     col.close()
 
     # ---------------- FP64 path (same workload, fewer steps) ---------------------------------
@@ -218,10 +279,10 @@ def run_native(args, rank, world):
     if not args.skip_fp64:
         col64 = Collision(prob, W.PREC_FP64)
         logf64 = torch.tensor(np.log(f0), dtype=torch.float64, device="cuda").contiguous()
-        t64 = torch.zeros(1, dtype=torch.float64, device="cuda")
-        dt64 = torch.full((1,), 0.5, dtype=torch.float64, device="cuda")
+        t64 = torch.full((1,), T0, dtype=torch.float64, device="cuda")
+        dt64 = torch.full((1,), DT, dtype=torch.float64, device="cuda")
         f64 = torch.exp(logf64)
-        col64.eval(f64, 0.0)                          # warm-up sweep (maps adapt)
+        col64.eval(f64, T0)                           # warm-up sweep (maps adapt)
         torch.cuda.synchronize()
         col64.profile(True)
         s64 = torch.cuda.current_stream()
@@ -230,14 +291,14 @@ def run_native(args, rank, world):
         a0.record(s64)
         for _ in range(args.fp64_steps):
             dt64.fill_(DT)
-            col64.step_heun(logf64, t64, dt64)
+            (col64.step_heun if method == "heun" else col64.step_euler)(logf64, t64, dt64)
         a1.record(s64)
         torch.cuda.synchronize()
         ms64 = a0.elapsed_time(a1)
         k64_ms, k64_n = col64.profile_read()
         col64.check()
         med64, max64 = rel_err_stats(col64)
-        s64 = 2 * args.fp64_steps / (ms64 / 1e3)
+        s64 = sweeps_per_step * args.fp64_steps / (ms64 / 1e3)
         fp64 = {"sweeps_per_s": s64, "evals_per_s": s64 * evals,
                 "sweeps_per_s_at_1e-4": s64 / (med64 / 1e-4) ** 2,
                 "rel_err_median": med64, "rel_err_max": max64, "steps": args.fp64_steps, "warmup_sweeps": 1,
@@ -246,7 +307,7 @@ def run_native(args, rank, world):
 
     # ---------------- roofline of the dominant kernel ----------------------------------------
     per_launch_ms = kern_ms / max(kern_n, 1)
-    flops = flops_per_sample(n_legs) * samples_per_launch
+    flops = fps * samples_per_launch
     achieved = flops / (per_launch_ms / 1e3) / 1e12
     peaks = measured_peaks()
     peak = FP32_PEAK_TFLOPS_NOMINAL
@@ -255,8 +316,8 @@ def run_native(args, rank, world):
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the sample kernel "
                               "(profiles/eval_kernel_f32_c2_bose_2to2.md); the tables it reads do not "
                               "grow with the sample count",
-            "kernel": "best::eval_kernel<float,4> (persistent sample kernel)",
-            "flops_per_sample": flops_per_sample(n_legs), "mufu_per_sample": mufu_per_sample(n_legs),
+            "kernel": f"best::eval_kernel<float,{max(n_legs, 4)},{ctas_per_sm}> (persistent sample kernel)",
+            "flops_per_sample": fps,
             "samples_per_launch": samples_per_launch, "launch_ms": per_launch_ms,
             "share_of_step": kern_ms / (ms / args.steps) if ms > 0 else None,
             "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz max SM clock (nominal unit "
@@ -267,11 +328,11 @@ def run_native(args, rank, world):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded; BE(T=1) + Gaussian bump, no dataset)",
-        "config": {"workload": f"{WORKLOAD}: 2 species (m=0, m=0.5) BE 2->2, 128 log points [1e-3,30], "
-                               "sigma_E=0.005, 1e6 samples x 8 iterations per task, 512 tasks, Heun steps",
-                   "grid_points": prob.grid.n, "tasks": 512, "neval": prob.processes[0].neval, "nitn": 8,
-                   "step": "one Heun step = 2 sweeps", "l2": "flushed between steps (512 MiB write, in the "
-                   "timed region)", "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "config": {"workload": f"{wl[0]}: {wl[4]}",
+                   "grid_points": prob.grid.n, "tasks": col_tasks, "neval": prob.processes[0].neval,
+                   "nitn": prob.processes[0].nitn,
+                   "step": f"one {method} step = {sweeps_per_step} sweep(s)", "l2": "flushed between steps "
+                   "(512 MiB write, in the timed region)", "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "evals_per_s": sweeps_per_s * evals,
         "evals_per_sweep": evals,
         "sweeps_per_s_at_1e-4": sweeps_per_s / (med32 / 1e-4) ** 2,
@@ -280,6 +341,7 @@ def run_native(args, rank, world):
         "fp32_over_fp64_at_1e-4": (sweeps_per_s / world / (med32 / 1e-4) ** 2) / fp64["sweeps_per_s_at_1e-4"]
         if fp64 else None,
         "roofline": roof,
+        "vjp": vjp,
         "e2e": {"value": sweeps / (ms_e2e / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": logf.numel() * 8 + 8, "d2h_bytes_per_step": logf.numel() * 8 + 8},
         "graph": "Heun steps replayed from a CUDA graph (best_evolve)",
@@ -287,7 +349,7 @@ def run_native(args, rank, world):
         "gpu_launches": launches,
         "clocks": clk,
     }
-    if rank == 0 and not args.skip_cpu:
+    if rank == 0 and not args.skip_cpu and WORKLOAD_KEY == "c2":
         out["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds, evals)
     return out
 
@@ -362,9 +424,12 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--neval", type=int, default=None,
                     help="samples per task per iteration (smaller cases for profiling)")
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--vjp", action="store_true", help="also time the adjoint")
     args = ap.parse_args()
-    global NEVAL
+    global NEVAL, WORKLOAD_KEY
     NEVAL = args.neval
+    WORKLOAD_KEY = args.workload
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
