@@ -222,11 +222,8 @@ def run_native(args, rank, world):
         kern_ms, kern_n = col.profile_read()               # launches of the last timed step
         col.profile(False)
         col.check(stream)
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = tt.item()
-    sweeps = sweeps_per_step * args.steps * world
+    from paper_2603_28848_gb300.dist import aggregate
+    ms, sweeps = aggregate(ms, sweeps_per_step * args.steps, device="cuda")   # max time, summed units
     sweeps_per_s = sweeps / (ms / 1e3)
     med32, max32 = rel_err_stats(col)
 
@@ -251,10 +248,7 @@ def run_native(args, rank, world):
         e3.record(stream)
         torch.cuda.synchronize()
     ms_e2e = e2.elapsed_time(e3)
-    if world > 1:
-        tt = torch.tensor([ms_e2e], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_e2e = tt.item()
+    ms_e2e, _ = aggregate(ms_e2e, 0, device="cuda")
     vjp = None
     if WORKLOAD_KEY == "c5" or args.vjp:
         v = torch.ones_like(logf)

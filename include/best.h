@@ -195,6 +195,21 @@ best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, con
                                double* C_dev, double* gf_dev, double* gm_dev, double* gcoupling_dev,
                                void* stream);
 
+/*
+ * Checkpoint of a context's evolving state (the paper checkpoints its
+ * integrator states with the distributions, Sec. 3F): the VEGAS maps of
+ * every task, the per-task accumulation scales, the evaluation counter and
+ * the time state, behind a header with a hash of the configuration.  With
+ * the same distribution values, time and step, a context restored from a
+ * state continues bit for bit like the one that saved it.  Both calls are
+ * synchronous; buffers are host memory of at least best_state_size bytes.
+ * Loading a state saved from a different configuration returns
+ * BEST_ERR_INVALID.
+ */
+int64_t best_state_size(const best_ctx* ctx);
+best_status best_save_state(best_ctx* ctx, void* host_buf, int64_t size);
+best_status best_load_state(best_ctx* ctx, const void* host_buf, int64_t size);
+
 /* Context geometry. */
 int32_t best_num_tasks(const best_ctx* ctx);
 int32_t best_num_side_integrals(const best_ctx* ctx);

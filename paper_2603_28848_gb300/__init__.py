@@ -178,6 +178,17 @@ class Collision:
                                           _ptr(gl), _stream(stream)), self.ctx)
         return C, gf, gm, gl
 
+    def save_state(self):
+        """Maps, scales, counter and time state as bytes (see checkpoint.py)."""
+        n = self.lib.best_state_size(self.ctx)
+        buf = ctypes.create_string_buffer(n)
+        check(self.lib.best_save_state(self.ctx, buf, n), self.ctx)
+        return buf.raw
+
+    def load_state(self, blob):
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        check(self.lib.best_load_state(self.ctx, buf, len(blob)), self.ctx)
+
     # -- inspection -------------------------------------------------------------
     def check(self, stream=None):
         check(self.lib.best_check(self.ctx, _stream(stream)), self.ctx)

@@ -932,6 +932,79 @@ best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, con
     return BEST_OK;
 }
 
+namespace {
+struct StateHeader {
+    uint64_t magic;         // "BESTSTT1"
+    uint64_t config_hash;   // FNV-1a of the task and side descriptors and the grid
+    int64_t n_tasks;
+    int64_t map_stride;
+};
+constexpr uint64_t kStateMagic = 0x3154545354534542ull;
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t k = 0; k < n; ++k) {
+        h ^= c[k];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+uint64_t config_hash(const best_ctx* ctx) {
+    uint64_t h = 1469598103934665603ull;
+    h = fnv1a(h, ctx->sides.data(), ctx->sides.size() * sizeof(SideDesc));
+    h = fnv1a(h, ctx->tasks.data(), ctx->tasks.size() * sizeof(TaskDesc));
+    const double grid[3] = {ctx->geo.q_min, ctx->geo.q_max, static_cast<double>(ctx->geo.n_grid)};
+    h = fnv1a(h, grid, sizeof(grid));
+    h = fnv1a(h, &ctx->geo.seed, sizeof(ctx->geo.seed));
+    return h;
+}
+}  // namespace
+
+int64_t best_state_size(const best_ctx* ctx) {
+    if (!ctx) return 0;
+    const int64_t T = ctx->geo.n_tasks;
+    return static_cast<int64_t>(sizeof(StateHeader)) + 8 * T * ctx->geo.map_stride + 8 * T +
+           static_cast<int64_t>(sizeof(TimeState));
+}
+
+best_status best_save_state(best_ctx* ctx, void* host_buf, int64_t size) {
+    if (!ctx || !host_buf) return fail(ctx, BEST_ERR_INVALID, "NULL argument");
+    if (size < best_state_size(ctx)) return fail(ctx, BEST_ERR_INVALID, "state buffer too small");
+    CK(cudaDeviceSynchronize());
+    char* p = static_cast<char*>(host_buf);
+    StateHeader hd{kStateMagic, config_hash(ctx), ctx->geo.n_tasks, ctx->geo.map_stride};
+    std::memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    const size_t ne = static_cast<size_t>(ctx->geo.n_tasks) * ctx->geo.map_stride;
+    CK(cudaMemcpy(p, ctx->d_edges, ne * sizeof(double), cudaMemcpyDeviceToHost));
+    p += ne * sizeof(double);
+    CK(cudaMemcpy(p, ctx->d_prev, ctx->geo.n_tasks * sizeof(double), cudaMemcpyDeviceToHost));
+    p += ctx->geo.n_tasks * sizeof(double);
+    CK(cudaMemcpy(p, ctx->d_ts, sizeof(TimeState), cudaMemcpyDeviceToHost));
+    return BEST_OK;
+}
+
+best_status best_load_state(best_ctx* ctx, const void* host_buf, int64_t size) {
+    if (!ctx || !host_buf) return fail(ctx, BEST_ERR_INVALID, "NULL argument");
+    if (size < best_state_size(ctx)) return fail(ctx, BEST_ERR_INVALID, "state buffer too small");
+    const char* p = static_cast<const char*>(host_buf);
+    StateHeader hd;
+    std::memcpy(&hd, p, sizeof(hd));
+    if (hd.magic != kStateMagic) return fail(ctx, BEST_ERR_INVALID, "not a libbest state");
+    if (hd.n_tasks != ctx->geo.n_tasks || hd.map_stride != ctx->geo.map_stride || hd.config_hash != config_hash(ctx))
+        return fail(ctx, BEST_ERR_INVALID, "state was saved from a different configuration");
+    p += sizeof(hd);
+    CK(cudaDeviceSynchronize());
+    const size_t ne = static_cast<size_t>(ctx->geo.n_tasks) * ctx->geo.map_stride;
+    CK(cudaMemcpy(ctx->d_edges, p, ne * sizeof(double), cudaMemcpyHostToDevice));
+    p += ne * sizeof(double);
+    CK(cudaMemcpy(ctx->d_prev, p, ctx->geo.n_tasks * sizeof(double), cudaMemcpyHostToDevice));
+    p += ctx->geo.n_tasks * sizeof(double);
+    CK(cudaMemcpy(ctx->d_ts, p, sizeof(TimeState), cudaMemcpyHostToDevice));
+    return BEST_OK;
+}
+
 int32_t best_num_tasks(const best_ctx* ctx) { return ctx ? ctx->geo.n_tasks : 0; }
 int32_t best_num_side_integrals(const best_ctx* ctx) { return ctx ? ctx->geo.n_side : 0; }
 int64_t best_map_stride(const best_ctx* ctx) { return ctx ? ctx->geo.map_stride : 0; }
