@@ -356,8 +356,12 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
             const R w2 = w * w;
             acc_w.add(w);
             acc_w2.add(w2);
+            // training data: a zero w^2 (far from the energy shell, or
+            // underflow) adds nothing, so such lanes skip the atomics
+            if (w2 != R(0)) {
 #pragma unroll
-            for (int d = 0; d < D; ++d) atomicAdd(&w_hist[d * nb + bin[d]], w2);
+                for (int d = 0; d < D; ++d) atomicAdd(&w_hist[d * nb + bin[d]], w2);
+            }
         }
     }
 
