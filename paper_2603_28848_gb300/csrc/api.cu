@@ -621,7 +621,13 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
             cudaFuncSetAttribute(reinterpret_cast<const void*>(&spline_build_kernel),
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(ctx->spline_smem)) != cudaSuccess)
             return bail(fail(ctx, BEST_ERR_CUDA, "cannot set shared memory of the spline kernel"));
-        ctx->refine_smem = sizeof(double) * (static_cast<size_t>(kMaxDim) * nb_max + 2);
+        ctx->refine_smem = sizeof(double) * (3 * static_cast<size_t>(kMaxDim) * nb_max + 2 * kMaxDim + 2);
+        if (cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(&refine_kernel)) != cudaSuccess)
+            return bail(fail(ctx, BEST_ERR_CUDA, "cannot query the refinement kernel"));
+        if (static_cast<size_t>(fa.maxDynamicSharedSizeBytes) < ctx->refine_smem &&
+            cudaFuncSetAttribute(reinterpret_cast<const void*>(&refine_kernel),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(ctx->refine_smem)) != cudaSuccess)
+            return bail(fail(ctx, BEST_ERR_CUDA, "cannot set shared memory of the refinement kernel"));
     }
 
     // ---- device state ----------------------------------------------------------------------------

@@ -189,8 +189,8 @@ __global__ void prepare_kernel(Geometry g, const SideDesc* __restrict__ sides,
 // ((1-d)/ln(1/d))^alpha, and re-partition into equal shares of the
 // compressed weight.  A normalised share below 1e-30 counts as an empty
 // increment (weight 0, like an exact zero) so that the map does not depend on
-// where underflow of w^2 falls.  Dynamic shared memory: (kMaxDim * nbins_max
-// + 2) doubles.
+// where underflow of w^2 falls.  Dynamic shared memory: (3 kMaxDim nbins_max
+// + 2 kMaxDim + 2) doubles.
 // ---------------------------------------------------------------------------
 __global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
                               const TaskDesc* __restrict__ tasks, const TaskConst* tconst,
@@ -237,50 +237,67 @@ __global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
         if (mean_n != 0.0) tconst_next[t].scale = clamp_scale(fabs(mean_n) * c.scale, c.obs_factor);
     }
     if (underflow) return;
+    // refinement: smoothing and compression in parallel over (dimension,
+    // increment), the cumulative re-partition by one thread per dimension
+    double* sm = hist + 2 + D * nb;            // smoothed, then compressed weights [D][nb]
+    double* tot = sm + D * nb;                 // per-dimension sums [D]
+    double* newe = tot + D;                    // new edges [D][nb + 1]
+    for (int k = threadIdx.x; k < D * nb; k += blockDim.x) {
+        const int d = k / nb, b = k - d * nb;
+        const double* dd = hist + 2 + d * nb;
+        double v;
+        if (nb == 1) v = dd[0];
+        else if (b == 0) v = (7.0 * dd[0] + dd[1]) / 8.0;
+        else if (b == nb - 1) v = (dd[nb - 2] + 7.0 * dd[nb - 1]) / 8.0;
+        else v = (dd[b - 1] + 6.0 * dd[b] + dd[b + 1]) / 8.0;
+        sm[k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < D) {
+        double t = 0.0;
+        for (int b = 0; b < nb; ++b) t += sm[threadIdx.x * nb + b];
+        tot[threadIdx.x] = t;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < D * nb; k += blockDim.x) {
+        const int d = k / nb;
+        const double t = tot[d];
+        double o = 0.0;
+        if (t > 0.0) {
+            const double v = sm[k] / t;
+            if (v < 1e-30) o = 0.0;            // numerically empty increment
+            else if (v >= 1.0) o = 1.0;
+            else o = pow((1.0 - v) / -log(v), td.alpha);
+        }
+        sm[k] = o;
+    }
+    __syncthreads();
     if (threadIdx.x < D) {
         const int d = threadIdx.x;
-        const double* dd = hist + 2 + d * nb;
+        const double* om = sm + d * nb;
         double* e = edges + static_cast<int64_t>(t) * g.map_stride + d * (nb + 1);
-        bool any = false;
-        for (int b = 0; b < nb; ++b) any |= dd[b] > 0.0;
-        if (any) {
-            double sm[256];
-            double om[256];
-            double tot = 0.0;
-            for (int b = 0; b < nb; ++b) {
-                double v;
-                if (nb == 1) v = dd[0];
-                else if (b == 0) v = (7.0 * dd[0] + dd[1]) / 8.0;
-                else if (b == nb - 1) v = (dd[nb - 2] + 7.0 * dd[nb - 1]) / 8.0;
-                else v = (dd[b - 1] + 6.0 * dd[b] + dd[b + 1]) / 8.0;
-                sm[b] = v;
-                tot += v;
-            }
+        if (tot[d] > 0.0) {
             double otot = 0.0;
-            for (int b = 0; b < nb; ++b) {
-                const double v = sm[b] / tot;
-                double o;
-                if (v < 1e-30) o = 0.0;            // numerically empty increment
-                else if (v >= 1.0) o = 1.0;
-                else o = pow((1.0 - v) / -log(v), td.alpha);
-                om[b] = o;
-                otot += o;
-            }
+            for (int b = 0; b < nb; ++b) otot += om[b];
             const double target = otot / nb;
-            double old[257];
-            for (int b = 0; b <= nb; ++b) old[b] = e[b];
+            // new edges depend on the old ones: collect them, then write
             double accw = 0.0;
             int i = 0;
+            double lo_i = e[0], hi_i = e[1];      // old edges of increment i
+            double* ne = newe + d * (nb + 1);
             for (int k = 1; k < nb; ++k) {
                 const double goal = k * target;
                 while (i < nb - 1 && accw + om[i] < goal) {
                     accw += om[i];
                     ++i;
+                    lo_i = e[i];
+                    hi_i = e[i + 1];
                 }
                 double fr = om[i] > 0.0 ? (goal - accw) / om[i] : 0.0;
                 fr = fr < 0.0 ? 0.0 : (fr > 1.0 ? 1.0 : fr);
-                e[k] = old[i] + fr * (old[i + 1] - old[i]);
+                ne[k] = lo_i + fr * (hi_i - lo_i);
             }
+            for (int k = 1; k < nb; ++k) e[k] = ne[k];
             e[0] = 0.0;
             e[nb] = 1.0;
         }
