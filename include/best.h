@@ -196,6 +196,43 @@ best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, con
                                void* stream);
 
 /*
+ * Jacobian-vector product of the same fixed-sample collision integral C~ as
+ * best_collision_vjp (same maps, reserved Philox iteration index and
+ * evaluation counter, so the same samples): writes C~ (C_dev) and
+ * JU = (dC~/df) u (JU_dev), both [n_species*n_grid], for a direction u_dev
+ * in the grid values f (masses and couplings held fixed).  Forward mode: the
+ * tangent of every sample's weight through the spline of u (the spline
+ * coefficients are linear in f) and the Eq. (13) tail fits, accumulated per
+ * task in FP64 in a fixed order, so repeated calls give identical bits.
+ * Device pointers; asynchronous on `stream`; maps and counter untouched.
+ */
+best_status best_collision_jvp(best_ctx* ctx, const double* f_dev, double t, const double* u_dev,
+                               double* C_dev, double* JU_dev, void* stream);
+
+/*
+ * One implicit (backward) Euler step in log space, the implicit counterpart
+ * of Eq. (14): log f(t+dt) = g solves
+ *     R(g) = g - log f(t) - dt C~(e^g) / e^g = 0
+ * with C~ the fixed-sample collision integral at time t + dt (masses and
+ * a(t) there).  Newton's method; each linear system J_R d = -R is solved by
+ * GMRES with at most krylov_dim (1..64) Arnoldi steps, stopped when its
+ * residual is below krylov_rtol * ||R||_2; J_R x = x - dt[(J (f x))/f -
+ * (C~/f) x] costs one best_collision_jvp launch set per product.  Steps are
+ * damped by halving until ||R||_2 decreases.  Stops when ||R||_inf <= tol or
+ * after max_newton iterations.  train != 0 first runs one full VEGAS sweep
+ * (all iterations, Sec. 3B) at f(t), time t + dt, to adapt the maps (and
+ * advances the evaluation counter); train == 0 keeps the current maps.
+ * logf_dev [n_species*n_grid] (device) holds log f(t) on entry and, when
+ * Newton converged, log f(t+dt) on return; otherwise it is unchanged and the
+ * call returns BEST_ERR_NUMERIC.  info (host, may be NULL, 5 doubles):
+ * Newton iterations, Krylov products, final ||R||_inf, converged (1/0),
+ * step halvings.  Synchronous (the Krylov loop reads residual norms).
+ */
+best_status best_step_implicit_euler(best_ctx* ctx, double* logf_dev, double t, double dt, int32_t train,
+                                     double tol, int32_t max_newton, int32_t krylov_dim, double krylov_rtol,
+                                     double* info, void* stream);
+
+/*
  * Checkpoint of a context's evolving state (the paper checkpoints its
  * integrator states with the distributions, Sec. 3F): the VEGAS maps of
  * every task, the per-task accumulation scales, the evaluation counter and

@@ -184,3 +184,16 @@ def vjp(problem, f0, t, v, maps, call, mode="f64"):
     gf, gm, gl = torch.autograd.grad(Lv, [f, m, lam], allow_unused=True)
     z = lambda g, like: g if g is not None else torch.zeros_like(like)
     return C.detach().numpy(), z(gf, f).numpy(), z(gm, m).numpy(), z(gl, lam).numpy()
+
+
+def jvp(problem, f0, t, u, maps, call, mode="f64"):
+    """(C~, J u) with J = dC~/df at fixed masses and couplings: the
+    directional derivative of ``fixed_sample_C`` along u (forward mode, by
+    torch's double-backward construction)."""
+    m = torch.tensor([s.mass0 + s.mass1 * t for s in problem.species], dtype=torch.float64)
+    lam = torch.tensor([p.coupling for p in problem.processes], dtype=torch.float64)
+    f = torch.tensor(np.asarray(f0, dtype=np.float64))
+    ut = torch.tensor(np.asarray(u, dtype=np.float64))
+    C, Ju = torch.autograd.functional.jvp(lambda ff: fixed_sample_C(problem, ff, m, lam, t, maps, call, mode),
+                                          (f,), (ut,))
+    return C.detach().numpy(), Ju.detach().numpy()

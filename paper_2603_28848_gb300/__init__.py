@@ -178,6 +178,35 @@ class Collision:
                                           _ptr(gl), _stream(stream)), self.ctx)
         return C, gf, gm, gl
 
+    def jvp(self, f, u, t=0.0, stream=None):
+        """(C~, J u) for J = dC~/df of the fixed-sample integral (the same
+        samples as vjp)."""
+        import torch
+        n = self.n_species * self.n_grid
+        _require(f, n, "f")
+        _require(u, n, "u")
+        C = torch.empty_like(f)
+        JU = torch.empty_like(f)
+        check(self.lib.best_collision_jvp(self.ctx, _ptr(f), float(t), _ptr(u), _ptr(C), _ptr(JU), _stream(stream)),
+              self.ctx)
+        return C, JU
+
+    def step_implicit_euler(self, logf, t, dt, train=True, tol=None, max_newton=8, krylov_dim=24,
+                            krylov_rtol=1e-6, stream=None):
+        """Backward Euler step of log f in place (Newton-Krylov on the
+        fixed-sample integral at t + dt).  tol defaults to 1e-10 (FP64) or
+        1e-6 (FP32) in ||R||_inf.  Returns a dict of the solver's counts;
+        raises BestError when Newton does not converge (logf unchanged)."""
+        n = self.n_species * self.n_grid
+        _require(logf, n, "logf")
+        if tol is None:
+            tol = 1e-6 if self.precision == 1 else 1e-10          # 1: FP32
+        info = (ctypes.c_double * 5)()
+        check(self.lib.best_step_implicit_euler(self.ctx, _ptr(logf), float(t), float(dt), int(bool(train)),
+                                                float(tol), int(max_newton), int(krylov_dim), float(krylov_rtol),
+                                                info, _stream(stream)), self.ctx)
+        return {"newton": int(info[0]), "krylov": int(info[1]), "residual": info[2], "halvings": int(info[4])}
+
     def save_state(self):
         """Maps, scales, counter and time state as bytes (see checkpoint.py)."""
         n = self.lib.best_state_size(self.ctx)

@@ -49,6 +49,9 @@ SIGNATURES = {
     "best_autotune": ([c_void_p, c_void_p, c_double, POINTER(c_int32), c_void_p], c_int32),
     "best_collision_vjp": ([c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                             c_void_p], c_int32),
+    "best_collision_jvp": ([c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "best_step_implicit_euler": ([c_void_p, c_void_p, c_double, c_double, c_int32, c_double, c_int32, c_int32,
+                                  c_double, c_void_p, c_void_p], c_int32),
     "best_state_size": ([c_void_p], c_int64),
     "best_save_state": ([c_void_p, c_void_p, c_int64], c_int32),
     "best_load_state": ([c_void_p, c_void_p, c_int64], c_int32),

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "internal.cuh"
@@ -31,6 +32,22 @@ __global__ void heun_correct_kernel(Geometry, double*, const double*, const doub
 int eval_variants(bool f32, int nmax, void** fn, int* mb);
 // vjp.cu
 void* vjp_kernel_ptr(bool f32, int nmax);
+void* jvp_kernel_ptr(bool f32, int nmax);
+__global__ void jvp_seed_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskConst*, const SpeciesConst*,
+                                const double*, double*);
+__global__ void jvp_finish_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskConst*, const double*, double*,
+                                  double*);
+__global__ void spline_tangent_kernel(Geometry, const double*, const double*, const double*, const SpeciesConst*,
+                                      const TimeState*, double*, float*, double*);
+__global__ void nk_exp_kernel(int, const double*, double*);
+__global__ void nk_axpy_kernel(int, const double*, const double*, double, double*);
+__global__ void nk_direction_kernel(int, const double*, const double*, double*);
+__global__ void nk_residual_kernel(int, const double*, const double*, const double*, const double*, double, double*,
+                                   double*, double*);
+__global__ void gmres_start_kernel(int, int, const double*, double*, double*);
+__global__ void gmres_arnoldi_kernel(int, int, int, double, const double*, const double*, const double*, double*,
+                                     double*, double*, double*, double*, double*);
+__global__ void gmres_update_kernel(int, int, int, const double*, const double*, const double*, double*);
 __global__ void vjp_seed_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskConst*, const double*, double*);
 __global__ void vjp_task_kernel(Geometry, const int32_t*, const int32_t*, const Segment*, const double*, int, double*);
 __global__ void vjp_finish_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskConst*, const SpeciesConst*,
@@ -121,6 +138,14 @@ struct best_ctx {
     double* d_u = nullptr;          // [task]
     double* d_gtail = nullptr;      // [species][4]
     double* d_coupling = nullptr;   // [process]
+    double* d_dcoef64 = nullptr;    // tangent spline of the JVP direction [species][n-1][4]
+    float* d_dcoef32 = nullptr;
+    double* d_dtail = nullptr;      // [species][4]
+    size_t jvp_smem = 0;
+    bool jvp_ready = false;         // shared-memory attribute of the tangent kernel set
+    // implicit Euler (best_step_implicit_euler): Krylov basis and work vectors
+    double* d_nk = nullptr;
+    int nk_m = 0;
     int n_processes = 0;
     size_t vjp_smem = 0;
     // timing of the sample kernel (best_profile_*)
@@ -178,7 +203,8 @@ void free_all(best_ctx* c) {
     void* bufs[] = {c->d_sides, c->d_tasks, c->d_tconst, c->d_acc, c->d_sconst, c->d_ts, c->d_edges,
                     c->d_knots, c->d_knots32, c->d_coef64, c->d_coef32, c->d_fgrid, c->d_mass0, c->d_mass1,
                     c->d_partials, c->d_k1, c->d_k2, c->d_fstar, c->d_prev, c->d_dtreq,
-                    c->d_gcoef, c->d_vjp_tot, c->d_u, c->d_gtail, c->d_coupling};
+                    c->d_gcoef, c->d_vjp_tot, c->d_u, c->d_gtail, c->d_coupling, c->d_dcoef64,
+                    c->d_dcoef32, c->d_dtail, c->d_nk};
     if (c->graph) cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
     for (void* b : bufs) cudaFree(b);
@@ -684,6 +710,9 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     CKI(dalloc(&ctx->d_u, static_cast<size_t>(T)));
     CKI(dalloc(&ctx->d_gtail, static_cast<size_t>(S) * 4));
     CKI(dalloc(&ctx->d_coupling, static_cast<size_t>(cfg->n_processes)));
+    CKI(dalloc(&ctx->d_dcoef64, static_cast<size_t>(S) * (n - 1) * 4));
+    CKI(dalloc(&ctx->d_dcoef32, static_cast<size_t>(S) * (n - 1) * 4));
+    CKI(dalloc(&ctx->d_dtail, static_cast<size_t>(S) * 4));
     {
         std::vector<double> lam(cfg->n_processes);
         for (int p = 0; p < cfg->n_processes; ++p) lam[p] = cfg->processes[p].coupling;
@@ -695,6 +724,7 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
         const size_t map_elems = static_cast<size_t>(kMaxDim) * nb_max;
         ctx->vjp_smem = rs * ((spl + 3) & ~size_t(3)) + 2 * rs * map_elems + sizeof(double) * ngc +
                         12 * 8 * sizeof(double);
+        ctx->jvp_smem = rs * ((spl + 3) & ~size_t(3)) + 2 * rs * map_elems + 12 * 8 * sizeof(double) + rs * ngc;
     }
     CKI(cudaMemset(ctx->d_prev, 0, sizeof(double) * T));
     CKI(cudaMemcpy(ctx->d_sides, ctx->sides.data(), g.n_side * sizeof(SideDesc), cudaMemcpyHostToDevice));
@@ -923,6 +953,8 @@ best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, con
     for (int r = 0; r < 20; ++r) P.rk[r] = key.k[r];
     V.task_u = ctx->d_u;
     V.gcoef = ctx->d_gcoef;
+    V.dcoef = nullptr;
+    V.dtail = nullptr;
     void* args[] = {&V};
     CK(cudaLaunchKernel(fn, dim3(ctx->grid), dim3(kThreads), args, ctx->vjp_smem, st));
     vjp_task_kernel<<<(pl.n_active + 127) / 128, 128, 0, st>>>(g, pl.d_active, pl.d_task_seg, pl.d_segs,
@@ -966,6 +998,221 @@ uint64_t config_hash(const best_ctx* ctx) {
     return h;
 }
 }  // namespace
+
+// Fixed-sample C~ and its tangent J u (the launches of best_collision_jvp).
+// setup: time state, spline of f and per-task constants, needed whenever f or
+// t changed since the previous call.
+static best_status enqueue_jvp(best_ctx* ctx, const double* f_dev, double t, const double* u_dev, double* C_dev,
+                               double* JU_dev, cudaStream_t st, bool setup) {
+    const Geometry& g = ctx->geo;
+    const bool f32 = ctx->precision == BEST_FP32;
+    void* fn = jvp_kernel_ptr(f32, ctx->nmax_legs);
+    if (!ctx->jvp_ready) {
+        int max_optin = 0, dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (ctx->jvp_smem > static_cast<size_t>(max_optin))
+            return fail(ctx, BEST_ERR_INVALID, "tangent tables need %zu B of shared memory (max %d)", ctx->jvp_smem,
+                        max_optin);
+        cudaFuncAttributes fa{};
+        CK(cudaFuncGetAttributes(&fa, fn));
+        if (static_cast<size_t>(fa.maxDynamicSharedSizeBytes) < ctx->jvp_smem)
+            CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(ctx->jvp_smem)));
+        ctx->jvp_ready = true;
+    }
+    if (setup) {
+        set_time_kernel<<<1, 32, 0, st>>>(g, ctx->d_ts, nullptr, t, 0, ctx->d_mass0, ctx->d_mass1);
+        spline_build_kernel<<<g.n_species, 256, ctx->spline_smem, st>>>(
+            g, f_dev, 0, ctx->d_knots, ctx->d_ts, ctx->d_sconst, ctx->d_fgrid, ctx->d_coef64, ctx->d_coef32);
+        prepare_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_knots,
+                                                                ctx->d_fgrid, ctx->d_ts, ctx->d_prev, ctx->d_tconst,
+                                                                ctx->d_acc, 0);
+        ctx->launches += 3;
+    }
+    jvp_seed_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_tconst,
+                                                             ctx->d_sconst, u_dev, ctx->d_u);
+    spline_tangent_kernel<<<g.n_species, 256, ctx->spline_smem, st>>>(g, u_dev, ctx->d_knots, ctx->d_fgrid,
+                                                                      ctx->d_sconst, ctx->d_ts, ctx->d_dcoef64,
+                                                                      ctx->d_dcoef32, ctx->d_dtail);
+    const IterPlan& pl = ctx->plans[0];
+    VjpParams V{};
+    EvalParams& P = V.E;
+    P.geo = g;
+    P.sides = ctx->d_sides;
+    P.tasks = ctx->d_tasks;
+    P.tconst = ctx->d_tconst;
+    P.sconst = ctx->d_sconst;
+    P.ts = ctx->d_ts;
+    P.edges = ctx->d_edges;
+    P.segs = pl.d_segs;
+    P.cta_seg = pl.d_cta_seg;
+    P.coef = f32 ? static_cast<const void*>(ctx->d_coef32) : static_cast<const void*>(ctx->d_coef64);
+    P.knots = f32 ? static_cast<const void*>(ctx->d_knots32) : static_cast<const void*>(ctx->d_knots);
+    P.partials = ctx->d_partials;
+    P.itn = 0xFFFFu;                                   // same samples as best_collision_vjp
+    P.smem_spline_elems = g.n_species * 4 * (g.n_grid - 1) + g.n_grid;
+    const PhiloxKey key = philox_key(g.seed);
+    for (int r = 0; r < 20; ++r) P.rk[r] = key.k[r];
+    V.task_u = ctx->d_u;
+    V.gcoef = nullptr;
+    V.dcoef = f32 ? static_cast<const void*>(ctx->d_dcoef32) : static_cast<const void*>(ctx->d_dcoef64);
+    V.dtail = ctx->d_dtail;
+    void* args[] = {&V};
+    CK(cudaLaunchKernel(fn, dim3(ctx->grid), dim3(kThreads), args, ctx->jvp_smem, st));
+    vjp_task_kernel<<<(pl.n_active + 127) / 128, 128, 0, st>>>(g, pl.d_active, pl.d_task_seg, pl.d_segs,
+                                                               ctx->d_partials, pl.n_active, ctx->d_vjp_tot);
+    jvp_finish_kernel<<<1, 32, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_tconst, ctx->d_vjp_tot, C_dev, JU_dev);
+    ctx->launches += 5;
+    CK(cudaGetLastError());
+    return BEST_OK;
+}
+
+best_status best_collision_jvp(best_ctx* ctx, const double* f_dev, double t, const double* u_dev, double* C_dev,
+                               double* JU_dev, void* stream) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    if (!f_dev || !u_dev || !C_dev || !JU_dev) return fail(ctx, BEST_ERR_INVALID, "f, u, C and JU must not be NULL");
+    if (!std::isfinite(t)) return fail(ctx, BEST_ERR_INVALID, "t must be finite");
+    ctx->launches = 0;
+    return enqueue_jvp(ctx, f_dev, t, u_dev, C_dev, JU_dev, static_cast<cudaStream_t>(stream), true);
+}
+
+// Newton-Krylov implicit Euler (kernels in newton.cu).
+static best_status nk_buffers(best_ctx* ctx, int m) {
+    const int64_t N = static_cast<int64_t>(ctx->geo.n_species) * ctx->geo.n_grid;
+    if (ctx->nk_m >= m && ctx->d_nk) return BEST_OK;
+    if (ctx->d_nk) cudaFree(ctx->d_nk);
+    ctx->d_nk = nullptr;
+    ctx->nk_m = 0;
+    const size_t total = static_cast<size_t>(N) * (m + 1 + 10) + static_cast<size_t>(m + 1) * m + 3 * m + 2 + 8;
+    CK(cudaMalloc(&ctx->d_nk, total * sizeof(double)));
+    ctx->nk_m = m;
+    return BEST_OK;
+}
+
+static best_status read_stat(best_ctx* ctx, const double* d_stat, double* h_stat, cudaStream_t st) {
+    CK(cudaMemcpyAsync(h_stat, d_stat, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return BEST_OK;
+}
+
+best_status best_step_implicit_euler(best_ctx* ctx, double* logf_dev, double t, double dt, int32_t train,
+                                     double tol, int32_t max_newton, int32_t krylov_dim, double krylov_rtol,
+                                     double* info, void* stream) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    if (!logf_dev) return fail(ctx, BEST_ERR_INVALID, "logf must not be NULL");
+    if (!std::isfinite(t) || !(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, BEST_ERR_INVALID, "need finite t, dt > 0");
+    if (!(tol > 0.0)) return fail(ctx, BEST_ERR_INVALID, "tol must be > 0");
+    if (max_newton < 1) return fail(ctx, BEST_ERR_INVALID, "max_newton must be >= 1");
+    if (krylov_dim < 1 || krylov_dim > 64) return fail(ctx, BEST_ERR_INVALID, "krylov_dim must be in [1, 64]");
+    if (!(krylov_rtol > 0.0 && krylov_rtol < 1.0)) return fail(ctx, BEST_ERR_INVALID, "krylov_rtol must be in (0, 1)");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Geometry& g = ctx->geo;
+    const int N = g.n_species * g.n_grid;
+    const int m = krylov_dim;
+    best_status s = nk_buffers(ctx, m);
+    if (s != BEST_OK) return s;
+    ctx->launches = 0;
+    const int mm = ctx->nk_m;               // layout follows the allocated Krylov dimension
+    double* V = ctx->d_nk;
+    double* gn = V + static_cast<size_t>(N) * (mm + 1);
+    double* ga = gn + N;                    // accepted iterate
+    double* gt = ga + N;                    // trial iterate
+    double* f = gt + N;
+    double* r = f + N;
+    double* Qd = r + N;
+    double* d = Qd + N;
+    double* C = d + N;
+    double* JU = C + N;
+    double* u = JU + N;
+    double* H = u + N;
+    double* cs = H + static_cast<size_t>(mm + 1) * mm;
+    double* sn = cs + mm;
+    double* gvec = sn + mm;
+    double* stat = gvec + mm + 2;
+    double hs[8] = {};
+    const int eb = (N + 255) / 256;
+    const double t1 = t + dt;
+
+    if (train) {
+        set_time_kernel<<<1, 32, 0, st>>>(g, ctx->d_ts, nullptr, t1, 0, ctx->d_mass0, ctx->d_mass1);
+        ctx->launches += 1;
+        s = enqueue_sweep(ctx, logf_dev, 1, ctx->d_k1, nullptr, st);
+        if (s != BEST_OK) return s;
+    }
+    CK(cudaMemcpyAsync(gn, logf_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ga, logf_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(u, 0, N * sizeof(double), st));
+    nk_exp_kernel<<<eb, 256, 0, st>>>(N, ga, f);
+    ctx->launches += 1;
+    s = enqueue_jvp(ctx, f, t1, u, C, JU, st, true);
+    if (s != BEST_OK) return s;
+    nk_residual_kernel<<<1, 1024, 0, st>>>(N, ga, gn, C, f, dt, r, Qd, stat);
+    ctx->launches += 1;
+    s = read_stat(ctx, stat, hs, st);
+    if (s != BEST_OK) return s;
+    if (hs[4] != 0.0) return fail(ctx, BEST_ERR_NUMERIC, "implicit Euler: non-finite residual at the initial iterate");
+    double rn2 = hs[0], rinf = hs[1];
+    int newton = 0, krylov = 0, halvings = 0;
+    while (rinf > tol && newton < max_newton) {
+        gmres_start_kernel<<<1, 1024, 0, st>>>(N, mm, r, V, gvec);
+        ctx->launches += 1;
+        int k = 0;
+        for (int j = 0; j < m; ++j) {
+            nk_direction_kernel<<<eb, 256, 0, st>>>(N, f, V + static_cast<size_t>(j) * N, u);
+            ctx->launches += 1;
+            s = enqueue_jvp(ctx, f, t1, u, C, JU, st, false);
+            if (s != BEST_OK) return s;
+            gmres_arnoldi_kernel<<<1, 1024, 0, st>>>(N, mm, j, dt, f, Qd, JU, V, H, cs, sn, gvec, stat);
+            ctx->launches += 1;
+            ++krylov;
+            s = read_stat(ctx, stat, hs, st);
+            if (s != BEST_OK) return s;
+            k = j + 1;
+            if (hs[2] <= krylov_rtol * rn2 || !(hs[3] > 1e-300 * rn2)) break;
+        }
+        gmres_update_kernel<<<1, 1024, 0, st>>>(N, mm, k, V, H, gvec, d);
+        ctx->launches += 1;
+        // backtracking on ||R||_2 (Armijo with slope -||R||^2 of the exact Newton direction)
+        double lambda = 1.0;
+        for (int ls = 0;; ++ls) {
+            nk_axpy_kernel<<<eb, 256, 0, st>>>(N, ga, d, lambda, gt);
+            nk_exp_kernel<<<eb, 256, 0, st>>>(N, gt, f);
+            CK(cudaMemsetAsync(u, 0, N * sizeof(double), st));
+            ctx->launches += 2;
+            s = enqueue_jvp(ctx, f, t1, u, C, JU, st, true);
+            if (s != BEST_OK) return s;
+            nk_residual_kernel<<<1, 1024, 0, st>>>(N, gt, gn, C, f, dt, r, Qd, stat);
+            ctx->launches += 1;
+            s = read_stat(ctx, stat, hs, st);
+            if (s != BEST_OK) return s;
+            const bool ok = hs[4] == 0.0 && hs[0] <= (1.0 - 1e-4 * lambda) * rn2;
+            if (ok || ls == 10) {
+                if (hs[4] != 0.0) return fail(ctx, BEST_ERR_NUMERIC, "implicit Euler: non-finite residual");
+                std::swap(ga, gt);
+                rn2 = hs[0];
+                rinf = hs[1];
+                break;
+            }
+            lambda *= 0.5;
+            ++halvings;
+        }
+        ++newton;
+    }
+    const bool converged = rinf <= tol;
+    if (info) {
+        info[0] = newton;
+        info[1] = krylov;
+        info[2] = rinf;
+        info[3] = converged ? 1.0 : 0.0;
+        info[4] = halvings;
+    }
+    if (!converged)
+        return fail(ctx, BEST_ERR_NUMERIC, "implicit Euler: Newton stopped at ||R||_inf = %.3e > tol %.3e after %d iterations",
+                    rinf, tol, newton);
+    CK(cudaMemcpyAsync(logf_dev, ga, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return BEST_OK;
+}
 
 int64_t best_state_size(const best_ctx* ctx) {
     if (!ctx) return 0;

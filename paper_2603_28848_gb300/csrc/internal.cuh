@@ -133,11 +133,13 @@ struct EvalParams {
     uint32_t rk[20];            // Philox round keys (kernel parameters: read from the constant bank)
 };
 
-// Arguments of the adjoint sample kernel.
+// Arguments of the adjoint / tangent sample kernel.
 struct VjpParams {
     EvalParams E;
-    const double* task_u;       // per task: v_{a,i} mult sign K scale / N
-    double* gcoef;              // [species][n-1][4] FP64, accumulated with atomics
+    const double* task_u;       // VJP: v_{a,i} mult sign K scale / N;  JVP: dobs u_{a,i} / scale
+    double* gcoef;              // VJP: [species][n-1][4] FP64 coefficient gradients (atomics)
+    const void* dcoef;          // JVP: tangent spline coefficients of u, [species][n-1][4] in R
+    const double* dtail;        // JVP: tail tangents [species][4] = (da, db) low end, (da, db) high end
 };
 
 // Doubles per partial record: the sample kernel writes 2 + D nb, the adjoint

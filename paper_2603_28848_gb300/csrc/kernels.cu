@@ -24,6 +24,46 @@ __global__ void set_time_kernel(Geometry g, TimeState* ts, const double* t_dev, 
     for (int s = 0; s < g.n_species; ++s) ts->mass[s] = mass0[s] + mass1[s] * t;
 }
 
+// Second derivatives M_j of the not-a-knot cubic spline through (q_j, f_j):
+// the tridiagonal system for M_1 .. M_{n-2} with the not-a-knot conditions
+// (third derivative continuous at q_1 and q_{n-2}) eliminated into its first
+// and last rows, solved by the Thomas algorithm; then M_0 and M_{n-1}.
+// cp: scratch of n doubles.  Single thread.
+__device__ void notaknot_moments(int n, const double* __restrict__ knots, const double* f, double* cp, double* M) {
+    const int m = n - 2;    // unknowns M_1 .. M_{n-2}
+    auto h = [&](int i) { return knots[i + 1] - knots[i]; };
+    auto rhs = [&](int i) { return 6.0 * ((f[i + 1] - f[i]) / h(i) - (f[i] - f[i - 1]) / h(i - 1)); };
+    for (int k = 0; k < m; ++k) {
+        const int i = k + 1;
+        double a = h(i - 1), b = 2.0 * (h(i - 1) + h(i)), c = h(i), d = rhs(i);
+        if (k == 0) {
+            const double h0 = h(0), h1 = h(1);
+            b += h0 * (h0 + h1) / h1;
+            c -= h0 * h0 / h1;
+            a = 0.0;
+        }
+        if (k == m - 1) {
+            const double hl = h(n - 2), hp = h(n - 3);
+            a -= hl * hl / hp;
+            b += hl * (hl + hp) / hp;
+            c = 0.0;
+        }
+        if (k > 0) {
+            const double den = b - a * cp[k - 1];
+            cp[k] = c / den;
+            M[k + 1] = (d - a * M[k]) / den;
+        } else {
+            cp[k] = c / b;
+            M[k + 1] = d / b;
+        }
+    }
+    for (int k = m - 2; k >= 0; --k) M[k + 1] -= cp[k] * M[k + 2];
+    const double h0 = h(0), h1 = h(1);
+    M[0] = ((h0 + h1) * M[1] - h0 * M[2]) / h1;
+    const double hl = h(n - 2), hp = h(n - 3);
+    M[n - 1] = ((hl + hp) * M[n - 2] - hl * M[n - 3]) / hp;
+}
+
 // ---------------------------------------------------------------------------
 // Spline of one species per CTA: not-a-knot cubic spline of (q_j, f_j)
 // through the tridiagonal system for the second derivatives M_j, with the
@@ -51,44 +91,7 @@ __global__ void spline_build_kernel(Geometry g, const double* __restrict__ src, 
         fgrid[static_cast<int64_t>(s) * n + j] = v;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        // rows i = 1 .. n-2 : h_{i-1} M_{i-1} + 2 (h_{i-1} + h_i) M_i + h_i M_{i+1} = r_i
-        // M_0 = ((h0 + h1) M_1 - h0 M_2) / h1, M_{n-1} symmetric.
-        const int m = n - 2;    // unknowns M_1 .. M_{n-2}
-        auto h = [&](int i) { return knots[i + 1] - knots[i]; };
-        auto rhs = [&](int i) { return 6.0 * ((f[i + 1] - f[i]) / h(i) - (f[i] - f[i - 1]) / h(i - 1)); };
-        // Thomas algorithm on rows k = 0 .. m-1 (unknown M_{k+1}); cp holds the
-        // normalised upper diagonal, M[k+1] the normalised right-hand side.
-        for (int k = 0; k < m; ++k) {
-            const int i = k + 1;
-            double a = h(i - 1), b = 2.0 * (h(i - 1) + h(i)), c = h(i), d = rhs(i);
-            if (k == 0) {
-                const double h0 = h(0), h1 = h(1);
-                b += h0 * (h0 + h1) / h1;
-                c -= h0 * h0 / h1;
-                a = 0.0;
-            }
-            if (k == m - 1) {
-                const double hl = h(n - 2), hp = h(n - 3);
-                a -= hl * hl / hp;
-                b += hl * (hl + hp) / hp;
-                c = 0.0;
-            }
-            if (k > 0) {
-                const double den = b - a * cp[k - 1];
-                cp[k] = c / den;
-                M[k + 1] = (d - a * M[k]) / den;
-            } else {
-                cp[k] = c / b;
-                M[k + 1] = d / b;
-            }
-        }
-        for (int k = m - 2; k >= 0; --k) M[k + 1] -= cp[k] * M[k + 2];
-        const double h0 = h(0), h1 = h(1);
-        M[0] = ((h0 + h1) * M[1] - h0 * M[2]) / h1;
-        const double hl = h(n - 2), hp = h(n - 3);
-        M[n - 1] = ((hl + hp) * M[n - 2] - hl * M[n - 3]) / hp;
-    }
+    if (threadIdx.x == 0) notaknot_moments(n, knots, f, cp, M);
     __syncthreads();
     for (int j = threadIdx.x; j < n - 1; j += blockDim.x) {
         const double hj = knots[j + 1] - knots[j];
@@ -128,6 +131,68 @@ __global__ void spline_build_kernel(Geometry g, const double* __restrict__ src, 
             const double a0 = ym - b * xm;
             if (end == 0) { sc[s].tail_lo_a = a0; sc[s].tail_lo_b = b; }
             else { sc[s].tail_hi_a = a0; sc[s].tail_hi_b = b; }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tangent of the spline construction in the direction u (one species per
+// CTA): the interval coefficients are linear in f, so the tangent spline is
+// the spline of u (no clamping); the end fits y = log(1/f + eta) = a + b E
+// move by da, db from dy_j = -u_j / (f_j (1 + eta f_j)).  Dynamic shared
+// memory: 3 n doubles.
+// ---------------------------------------------------------------------------
+__global__ void spline_tangent_kernel(Geometry g, const double* __restrict__ u, const double* __restrict__ knots,
+                                      const double* __restrict__ fgrid, const SpeciesConst* __restrict__ sc,
+                                      const TimeState* ts, double* dcoef64, float* dcoef32, double* dtail) {
+    extern __shared__ double sh[];
+    const int n = g.n_grid;
+    const int s = blockIdx.x;
+    double* du = sh;
+    double* cp = sh + n;
+    double* M = sh + 2 * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) du[j] = u[static_cast<int64_t>(s) * n + j];
+    __syncthreads();
+    if (threadIdx.x == 0) notaknot_moments(n, knots, du, cp, M);
+    __syncthreads();
+    for (int j = threadIdx.x; j < n - 1; j += blockDim.x) {
+        const double hj = knots[j + 1] - knots[j];
+        const double c0 = du[j];
+        const double c1 = (du[j + 1] - du[j]) / hj - hj * (2.0 * M[j] + M[j + 1]) / 6.0;
+        const double c2 = 0.5 * M[j];
+        const double c3 = (M[j + 1] - M[j]) / (6.0 * hj);
+        const int64_t o = (static_cast<int64_t>(s) * (n - 1) + j) * 4;
+        dcoef64[o + 0] = c0; dcoef64[o + 1] = c1; dcoef64[o + 2] = c2; dcoef64[o + 3] = c3;
+        dcoef32[o + 0] = static_cast<float>(c0); dcoef32[o + 1] = static_cast<float>(c1);
+        dcoef32[o + 2] = static_cast<float>(c2); dcoef32[o + 3] = static_cast<float>(c3);
+    }
+    if (threadIdx.x == 0) {
+        const double eta = sc[s].eta;
+        const double m = ts->mass[s];
+        const double a = ts->a;
+        const int K = g.tail_points;
+        const double* f = fgrid + static_cast<int64_t>(s) * n;
+        for (int end = 0; end < 2; ++end) {
+            double xm = 0.0, dym = 0.0;
+            for (int q = 0; q < K; ++q) {
+                const int j = end == 0 ? q : n - K + q;
+                const double p = knots[j] / a;
+                xm += sqrt(p * p + m * m);
+                dym += -du[j] / (f[j] * (1.0 + eta * f[j]));
+            }
+            xm /= K;
+            dym /= K;
+            double sxy = 0.0, sxx = 0.0;
+            for (int q = 0; q < K; ++q) {
+                const int j = end == 0 ? q : n - K + q;
+                const double p = knots[j] / a;
+                const double x = sqrt(p * p + m * m) - xm;
+                sxy += x * (-du[j] / (f[j] * (1.0 + eta * f[j])) - dym);
+                sxx += x * x;
+            }
+            const double db = sxy / sxx;
+            dtail[s * 4 + 2 * end] = dym - db * xm;
+            dtail[s * 4 + 2 * end + 1] = db;
         }
     }
 }

@@ -7,23 +7,20 @@
 
 namespace best {
 
-template __global__ void vjp_kernel<float, 4>(VjpParams);
-template __global__ void vjp_kernel<float, 5>(VjpParams);
-template __global__ void vjp_kernel<float, 6>(VjpParams);
-template __global__ void vjp_kernel<double, 4>(VjpParams);
-template __global__ void vjp_kernel<double, 5>(VjpParams);
-template __global__ void vjp_kernel<double, 6>(VjpParams);
-
-void* vjp_kernel_ptr(bool f32, int nmax) {
+template <bool JVP>
+void* kernel_ptr(bool f32, int nmax) {
     if (f32) {
-        if (nmax <= 4) return reinterpret_cast<void*>(&vjp_kernel<float, 4>);
-        if (nmax == 5) return reinterpret_cast<void*>(&vjp_kernel<float, 5>);
-        return reinterpret_cast<void*>(&vjp_kernel<float, 6>);
+        if (nmax <= 4) return reinterpret_cast<void*>(&vjp_kernel<float, 4, JVP>);
+        if (nmax == 5) return reinterpret_cast<void*>(&vjp_kernel<float, 5, JVP>);
+        return reinterpret_cast<void*>(&vjp_kernel<float, 6, JVP>);
     }
-    if (nmax <= 4) return reinterpret_cast<void*>(&vjp_kernel<double, 4>);
-    if (nmax == 5) return reinterpret_cast<void*>(&vjp_kernel<double, 5>);
-    return reinterpret_cast<void*>(&vjp_kernel<double, 6>);
+    if (nmax <= 4) return reinterpret_cast<void*>(&vjp_kernel<double, 4, JVP>);
+    if (nmax == 5) return reinterpret_cast<void*>(&vjp_kernel<double, 5, JVP>);
+    return reinterpret_cast<void*>(&vjp_kernel<double, 6, JVP>);
 }
+
+void* vjp_kernel_ptr(bool f32, int nmax) { return kernel_ptr<false>(f32, nmax); }
+void* jvp_kernel_ptr(bool f32, int nmax) { return kernel_ptr<true>(f32, nmax); }
 
 // Adjoint seed of every task: L = sum_{a,i} v_{a,i} C~_a(p_i) and C~ = sum
 // mult (I_gain - I_loss), I = K scale (sum w_n) / N, so dL/dw_n = v mult sign
@@ -37,6 +34,37 @@ __global__ void vjp_seed_kernel(Geometry g, const SideDesc* __restrict__ sides, 
     const double sign = td.term == 0 ? 1.0 : -1.0;
     u[t] = v[static_cast<int64_t>(sd.species_obs) * g.n_grid + td.point] * sd.mult * sign * tconst[t].K *
            tconst[t].scale / static_cast<double>(td.neval);
+}
+
+// Tangent seed: d w_n / d f_obs u_obs = (w_n / c0) dobs u_{a,i} / scale.
+__global__ void jvp_seed_kernel(Geometry g, const SideDesc* __restrict__ sides, const TaskDesc* __restrict__ tasks,
+                                const TaskConst* __restrict__ tconst, const SpeciesConst* __restrict__ sconst,
+                                const double* __restrict__ uvec, double* u) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.n_tasks) return;
+    const TaskDesc td = tasks[t];
+    const SideDesc& sd = sides[td.si];
+    const double dobs = td.term == 1 ? 1.0 : sconst[sd.species_obs].eta;
+    u[t] = dobs * uvec[static_cast<int64_t>(sd.species_obs) * g.n_grid + td.point] / tconst[t].scale;
+}
+
+// C~ and dC~ = J u from the tasks' tangent records; one thread, tasks in order.
+__global__ void jvp_finish_kernel(Geometry g, const SideDesc* __restrict__ sides, const TaskDesc* __restrict__ tasks,
+                                  const TaskConst* __restrict__ tconst, const double* __restrict__ tot, double* C,
+                                  double* JU) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int n = g.n_grid;
+    for (int k = 0; k < g.n_species * n; ++k) { C[k] = 0.0; JU[k] = 0.0; }
+    for (int t = 0; t < g.n_tasks; ++t) {
+        const TaskDesc td = tasks[t];
+        const SideDesc& sd = sides[td.si];
+        const double* T = tot + static_cast<int64_t>(t) * 16;
+        const int64_t ai = static_cast<int64_t>(sd.species_obs) * n + td.point;
+        const double f = sd.mult * (td.term == 0 ? 1.0 : -1.0) * tconst[t].K * tconst[t].scale /
+                         static_cast<double>(td.neval);
+        C[ai] += f * T[0];
+        JU[ai] += f * T[1];
+    }
 }
 
 // Sum of each task's segment records (fixed order), 16 doubles per task.

@@ -63,10 +63,13 @@ __device__ __forceinline__ Hit<R> spline_hit(const SplineView<R>& sv, R q, const
     return h;
 }
 
-template <typename R, int NLEG>
+// JVP = false: adjoint (VJP) accumulation; true: forward tangent dC~ = J u,
+// with the tangent spline table of u in s_dsp (same layout as s_spline's
+// coefficients) and the tail tangents (da, db per end) in V.dtail.
+template <typename R, int NLEG, bool JVP>
 __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& seg, const SideDesc& sd,
                                             const TaskDesc& td, const TaskConst& tc, R* s_spline,
-                                            Real2<R>* s_map, double* s_gc, double* s_red) {
+                                            Real2<R>* s_map, double* s_gc, double* s_red, const R* s_dsp) {
     const EvalParams& P = V.E;
     constexpr int NI = NLEG - 2;
     constexpr int D = 3 * NI;
@@ -138,12 +141,20 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
     const R tlo_a = static_cast<R>(P.sconst[spcn].tail_lo_a), tlo_b = static_cast<R>(P.sconst[spcn].tail_lo_b);
     const R thi_a = static_cast<R>(P.sconst[spcn].tail_hi_a), thi_b = static_cast<R>(P.sconst[spcn].tail_hi_b);
     const R a = static_cast<R>(ts.a), inv_a = static_cast<R>(1.0 / ts.a);
-    const R c0 = tc.E_obs < g.e_cut ? R(0) : static_cast<R>(tc.obs_factor / tc.scale);
+    const bool obs_cut = tc.E_obs < g.e_cut;       // every sample of the task is cut
+    const R c0 = obs_cut ? R(0) : static_cast<R>(tc.obs_factor / tc.scale);
     const R gauss_k = static_cast<R>(-1.4426950408889634 / (2.0 * sd.sigma * sd.sigma));
     const R inv_sig2 = static_cast<R>(1.0 / (sd.sigma * sd.sigma));
     const R e_cut = static_cast<R>(g.e_cut);
     const R inv_Eobs = static_cast<R>(1.0 / tc.E_obs);
-    const R U = static_cast<R>(V.task_u[seg.task]);
+    const R U = static_cast<R>(V.task_u[seg.task]);     // VJP: adjoint seed; JVP: obs tangent factor
+    R dta_lo = R(0), dtb_lo = R(0), dta_hi = R(0), dtb_hi = R(0);
+    if constexpr (JVP) {
+        dta_lo = static_cast<R>(V.dtail[spcn * 4 + 0]);
+        dtb_lo = static_cast<R>(V.dtail[spcn * 4 + 1]);
+        dta_hi = static_cast<R>(V.dtail[spcn * 4 + 2]);
+        dtb_hi = static_cast<R>(V.dtail[spcn * 4 + 3]);
+    }
     const R nbR = static_cast<R>(nb);
     const R q0 = static_cast<R>(g.q_min), qN = static_cast<R>(g.q_max);
     const R lq0_step = static_cast<R>(g.log_spaced ? std::log2(g.q_min) / (g.log_step / 0.6931471805599453) : 0.0);
@@ -156,6 +167,7 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
     // each integrated leg, tail (a, b) at the low and high ends
     Acc<R> acc_w, acc_fobs, acc_mobs, acc_mc, acc_tla, acc_tlb, acc_tha, acc_thb;
     Acc<R> acc_m[NI];
+    Acc<R> acc_dw;                              // JVP: tangent of w_n
     const int64_t N = td.neval;
     const uint32_t task = static_cast<uint32_t>(seg.task);
     const int32_t g1 = static_cast<int32_t>(seg.g1);
@@ -191,7 +203,7 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
             R dE = sgn_obs_E;
             R meas = jac;
             R rinv = R(1);
-            bool cut = false;
+            bool cut = obs_cut;
             R fac[NI + 1], dfac[NI + 1], tl[NI + 1], rE[NI];
             int jl[NI + 1];
 #pragma unroll
@@ -273,6 +285,24 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
                 dwdf[k] = c0 * base * pre[k] * suf * dfac[k];
                 suf *= fac[k];
             }
+            if constexpr (JVP) {
+                // tangent: d w_n = sum_k dw/df_k df_k + (w_n / c0) U (U = dobs u_obs / scale)
+                R dw = base * F * U;
+#pragma unroll
+                for (int k = 0; k <= NI; ++k) {
+                    R dfk;
+                    if (k == NI && !inside) {
+                        dfk = dfdz * (below ? fma(dtb_lo, Ec, dta_lo) : fma(dtb_hi, Ec, dta_hi));
+                    } else {
+                        const int sp = k < NI ? spc[k] : spcn;
+                        const R* dc = s_dsp + sp * ncoef + 4 * jl[k];
+                        const R t = tl[k];
+                        dfk = fma(fma(fma(dc[3], t, dc[2]), t, dc[1]), t, dc[0]);
+                    }
+                    dw = fma(dwdf[k], dfk, dw);
+                }
+                acc_dw.add(dw);
+            } else {
             const R dEterm = -wn * dE * inv_sig2;
 #pragma unroll
             for (int j = 0; j < NI; ++j) {
@@ -301,16 +331,23 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
                     atomicAdd(dst + 3, gd * td_ * td_ * td_);
                 }
             }
+            }
         }
     }
 
-    // ---- segment record: [w, fobs, mobs, mc, tla, tlb, tha, thb, m_0 .. m_{NI-1}] ----
-    constexpr int NV = 8 + NI;
+    // ---- segment record: VJP [w, fobs, mobs, mc, tla, tlb, tha, thb, m_0 .. m_{NI-1}];
+    //      JVP [w, dw] ----
+    constexpr int NV = JVP ? 2 : 8 + NI;
     double vals[NV];
-    vals[0] = acc_w.value(); vals[1] = acc_fobs.value(); vals[2] = acc_mobs.value(); vals[3] = acc_mc.value();
-    vals[4] = acc_tla.value(); vals[5] = acc_tlb.value(); vals[6] = acc_tha.value(); vals[7] = acc_thb.value();
+    if constexpr (JVP) {
+        vals[0] = acc_w.value();
+        vals[1] = acc_dw.value();
+    } else {
+        vals[0] = acc_w.value(); vals[1] = acc_fobs.value(); vals[2] = acc_mobs.value(); vals[3] = acc_mc.value();
+        vals[4] = acc_tla.value(); vals[5] = acc_tlb.value(); vals[6] = acc_tha.value(); vals[7] = acc_thb.value();
 #pragma unroll
-    for (int j = 0; j < NI; ++j) vals[8 + j] = acc_m[j].value();
+        for (int j = 0; j < NI; ++j) vals[8 + j] = acc_m[j].value();
+    }
     const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
@@ -328,7 +365,7 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
     __syncthreads();
 }
 
-template <typename R, int NMAX>
+template <typename R, int NMAX, bool JVP>
 __global__ void __launch_bounds__(kThreads, 1) vjp_kernel(VjpParams V) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const EvalParams& P = V.E;
@@ -337,13 +374,15 @@ __global__ void __launch_bounds__(kThreads, 1) vjp_kernel(VjpParams V) {
     Real2<R>* s_map = reinterpret_cast<Real2<R>*>(s_spline + ((nsp + 3) & ~3));
     const int map_elems = kMaxDim * P.geo.nbins_max;
     const int ngc = 4 * (P.geo.n_grid - 1) * P.geo.n_species;
-    double* s_gc = reinterpret_cast<double*>(s_map + map_elems);     // 16-byte aligned: map_elems even
-    double* s_red = s_gc + ngc;
+    double* s_gc = reinterpret_cast<double*>(s_map + map_elems);     // VJP: coefficient gradients
+    double* s_red = s_gc + (JVP ? 0 : ngc);
+    R* s_dsp = reinterpret_cast<R*>(s_red + 12 * 8);                  // JVP: tangent coefficients
     {
         const R* gc = static_cast<const R*>(P.coef);
         for (int k = threadIdx.x; k < ngc; k += blockDim.x) {
             s_spline[k] = gc[k];
-            s_gc[k] = 0.0;
+            if constexpr (JVP) s_dsp[k] = static_cast<const R*>(V.dcoef)[k];
+            else s_gc[k] = 0.0;
         }
         const R* gk = static_cast<const R*>(P.knots);
         for (int k = threadIdx.x; k < P.geo.n_grid; k += blockDim.x) s_spline[ngc + k] = gk[k];
@@ -356,17 +395,19 @@ __global__ void __launch_bounds__(kThreads, 1) vjp_kernel(VjpParams V) {
         const TaskConst tc = P.tconst[seg.task];
         __syncthreads();
         switch (sd.n) {
-            case 3: if constexpr (NMAX >= 3) vjp_segment<R, 3>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red); break;
-            case 4: if constexpr (NMAX >= 4) vjp_segment<R, 4>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red); break;
-            case 5: if constexpr (NMAX >= 5) vjp_segment<R, 5>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red); break;
-            case 6: if constexpr (NMAX >= 6) vjp_segment<R, 6>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red); break;
+            case 3: if constexpr (NMAX >= 3) vjp_segment<R, 3, JVP>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp); break;
+            case 4: if constexpr (NMAX >= 4) vjp_segment<R, 4, JVP>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp); break;
+            case 5: if constexpr (NMAX >= 5) vjp_segment<R, 5, JVP>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp); break;
+            case 6: if constexpr (NMAX >= 6) vjp_segment<R, 6, JVP>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp); break;
             default: break;
         }
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < ngc; k += blockDim.x) {
-        const double v = s_gc[k];
-        if (v != 0.0) atomicAdd(V.gcoef + k, v);
+    if constexpr (!JVP) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < ngc; k += blockDim.x) {
+            const double v = s_gc[k];
+            if (v != 0.0) atomicAdd(V.gcoef + k, v);
+        }
     }
 }
 

@@ -69,8 +69,9 @@ def test_gradient_matches_central_differences(kind):
     C, gf, gm, gl = adj.vjp(prob, f0, t, v, maps, 0)
 
     def L(f, m=None, lam=None):
-        mm = torch.tensor(m if m is not None else [s.mass0 + s.mass1 * t for s in prob.species])
-        ll = torch.tensor(lam if lam is not None else [p.coupling for p in prob.processes])
+        mm = torch.tensor(m if m is not None else [s.mass0 + s.mass1 * t for s in prob.species],
+                          dtype=torch.float64)
+        ll = torch.tensor(lam if lam is not None else [p.coupling for p in prob.processes], dtype=torch.float64)
         return float((adj.fixed_sample_C(prob, torch.tensor(f), mm, ll, t, maps, 0) * torch.tensor(v)).sum())
 
     h = 1e-4                      # relative step (smaller steps hit roundoff on tiny grid values)
