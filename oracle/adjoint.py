@@ -19,7 +19,7 @@ import numpy as np
 import torch
 from scipy.interpolate import CubicSpline
 
-from . import philox, vegas
+from . import philox, vegas, width as owidth
 from .collision import TWO_PI, grid_q, scale_factor, task_budget
 from .spline import ETA
 from .tasks import SIDE_IN, side_integrals, task_id
@@ -91,9 +91,10 @@ class TorchDistribution:
         return out
 
 
-def fixed_sample_C(problem, f, masses, couplings, t, maps, call, mode="f64"):
+def fixed_sample_C(problem, f, masses, couplings, t, maps, call, mode="f64", widths=None):
     """C~ (n_species, n_grid) as a torch function of f (S, n), masses (S,)
-    and couplings (P,); maps[task] = edges (D, nb+1) numpy."""
+    and couplings (P,); maps[task] = edges (D, nb+1) numpy; widths[p]: the
+    fractional Gaussian width of process p (default: its initial width)."""
     g = problem.grid
     q = grid_q(g)
     a = scale_factor(problem, t)
@@ -111,14 +112,15 @@ def fixed_sample_C(problem, f, masses, couplings, t, maps, call, mode="f64"):
                 N = task_budget(proc, i)
                 x = philox.uniforms(problem.seed, tid, VJP_ITERATION, call, N, D, mode)
                 y, jac, _ = vegas.apply_map(maps[tid], x)
-                w = _integrand(problem, si, term, i, f, dists, masses, couplings[si.process], a, y, q) * \
+                wf = proc.width if widths is None else widths[si.process]
+                w = _integrand(problem, si, term, i, f, dists, masses, couplings[si.process], a, y, q, wf) * \
                     torch.tensor(jac)
                 sign = 1.0 if term == 0 else -1.0
                 rows[si.species][i] = rows[si.species][i] + si.mult * sign * w.mean()
     return torch.stack([torch.stack(r) for r in rows])
 
 
-def _integrand(problem, si, term, i, f, dists, masses, coupling, a, y, q):
+def _integrand(problem, si, term, i, f, dists, masses, coupling, a, y, q, w_frac=None):
     proc = problem.processes[si.process]
     gr = problem.grid
     n = si.n
@@ -151,7 +153,7 @@ def _integrand(problem, si, term, i, f, dists, masses, coupling, a, y, q):
     for k in range(n):
         cut = cut | (E[k] < problem.e_cut)
     dE = sum(E[k] if si.is_in(k) else -E[k] for k in range(n))
-    sig = proc.sigma_E
+    sig = owidth.sigma(proc, proc.width if w_frac is None else w_frac, sum(E[k] for k in range(n)))
     gauss = torch.exp(-dE * dE / (2.0 * sig * sig)) / (sig * np.sqrt(2.0 * np.pi))
     gain = torch.ones(N, dtype=torch.float64)
     loss = torch.ones(N, dtype=torch.float64)
@@ -174,19 +176,19 @@ def _integrand(problem, si, term, i, f, dists, masses, coupling, a, y, q):
     return torch.where(cut, torch.zeros_like(w), w)
 
 
-def vjp(problem, f0, t, v, maps, call, mode="f64"):
+def vjp(problem, f0, t, v, maps, call, mode="f64", widths=None):
     """(C~, dL/df, dL/dm, dL/dcoupling) for L = sum(v * C~)."""
     f = torch.tensor(np.asarray(f0, dtype=np.float64), requires_grad=True)
     m = torch.tensor([s.mass0 + s.mass1 * t for s in problem.species], dtype=torch.float64, requires_grad=True)
     lam = torch.tensor([p.coupling for p in problem.processes], dtype=torch.float64, requires_grad=True)
-    C = fixed_sample_C(problem, f, m, lam, t, maps, call, mode)
+    C = fixed_sample_C(problem, f, m, lam, t, maps, call, mode, widths)
     Lv = (C * torch.tensor(np.asarray(v, dtype=np.float64))).sum()
     gf, gm, gl = torch.autograd.grad(Lv, [f, m, lam], allow_unused=True)
     z = lambda g, like: g if g is not None else torch.zeros_like(like)
     return C.detach().numpy(), z(gf, f).numpy(), z(gm, m).numpy(), z(gl, lam).numpy()
 
 
-def jvp(problem, f0, t, u, maps, call, mode="f64"):
+def jvp(problem, f0, t, u, maps, call, mode="f64", widths=None):
     """(C~, J u) with J = dC~/df at fixed masses and couplings: the
     directional derivative of ``fixed_sample_C`` along u (forward mode, by
     torch's double-backward construction)."""
@@ -194,6 +196,7 @@ def jvp(problem, f0, t, u, maps, call, mode="f64"):
     lam = torch.tensor([p.coupling for p in problem.processes], dtype=torch.float64)
     f = torch.tensor(np.asarray(f0, dtype=np.float64))
     ut = torch.tensor(np.asarray(u, dtype=np.float64))
-    C, Ju = torch.autograd.functional.jvp(lambda ff: fixed_sample_C(problem, ff, m, lam, t, maps, call, mode),
+    C, Ju = torch.autograd.functional.jvp(lambda ff: fixed_sample_C(problem, ff, m, lam, t, maps, call, mode,
+                                                                    widths),
                                           (f,), (ut,))
     return C.detach().numpy(), Ju.detach().numpy()

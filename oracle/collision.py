@@ -16,7 +16,8 @@ parametrised as in Sec. 2D and App. A:
     sign cases of App. A; its comoving momentum is |p_cons| a;
   * E_k = sqrt(|p_k|^2 + m_k^2); a sample with any E_k < E_cut has weight 0
     (App. A);
-  * energy conservation uses the Gaussian of Eq. (11) with width sigma_E;
+  * energy conservation uses the Gaussian of Eq. (11) with width sigma_E,
+    or the fractional width w (E_in + E_out) / 2 of App. C (``width``);
   * the weight is Eq. (12) / App. A: prod r^2 sin(theta) over
     ((2 pi)^(3(n-1)-4) prod_{all n legs} 2E) times the Gaussian, times |M|^2
     and the gain or loss product;
@@ -34,7 +35,7 @@ from typing import Dict
 import numpy as np
 
 from workloads import PREC_FP32
-from . import philox, vegas
+from . import philox, vegas, width as owidth
 from .spline import ETA, Distribution
 from .tasks import SIDE_IN, side_integrals, task_id
 
@@ -112,8 +113,9 @@ def kinematics(problem, si, i, m, a, y):
     return mom, E, qcom, jac
 
 
-def integrand(problem, si, term, i, f_obs, dists, m, a, y):
-    """Integrand on the unit cube (before the VEGAS Jacobian), shape (N,)."""
+def integrand(problem, si, term, i, f_obs, dists, m, a, y, w_frac=None):
+    """Integrand on the unit cube (before the VEGAS Jacobian), shape (N,);
+    w_frac: the process's fractional width (default: its initial width)."""
     proc = problem.processes[si.process]
     n = si.n
     N = y.shape[0]
@@ -122,7 +124,7 @@ def integrand(problem, si, term, i, f_obs, dists, m, a, y):
     dE = np.zeros(N)
     for k in range(n):
         dE += E[k] if si.is_in(k) else -E[k]
-    sig = proc.sigma_E
+    sig = owidth.sigma(proc, proc.width if w_frac is None else w_frac, np.sum(E, axis=0))
     gauss = np.exp(-dE * dE / (2.0 * sig * sig)) / (sig * np.sqrt(2.0 * np.pi))
     # statistical factor, Eq. (5) with the observed-side products of Sec. 2C
     gain = np.ones(N)
@@ -149,17 +151,21 @@ def integrand(problem, si, term, i, f_obs, dists, m, a, y):
 
 @dataclass
 class State:
-    """Persistent VEGAS maps (one per task, reused across calls, Sec. 3D)
-    and the counter of collision evaluations (part of the sample stream)."""
+    """Persistent VEGAS maps (one per task, reused across calls, Sec. 3D),
+    the counter of collision evaluations (part of the sample stream) and the
+    fractional Gaussian width of each process (App. C) with the relative
+    error that set it."""
     maps: Dict[int, np.ndarray] = field(default_factory=dict)
     call: int = 0
+    widths: Dict[int, float] = field(default_factory=dict)
+    width_rel: Dict[int, float] = field(default_factory=dict)
 
 
 def task_budget(proc, i):
     return proc.neval_per_point[i] if proc.neval_per_point is not None else proc.neval
 
 
-def evaluate_task(problem, si_index, si, i, term, f, t, edges, call, mode="f64", dists=None):
+def evaluate_task(problem, si_index, si, i, term, f, t, edges, call, mode="f64", dists=None, w_frac=None):
     """Run the nitn VEGAS iterations of one task.
 
     Returns (mean, err, edges_after, per-iteration list of (mean, var)).
@@ -182,7 +188,7 @@ def evaluate_task(problem, si_index, si, i, term, f, t, edges, call, mode="f64",
             ns = min(CHUNK, N - s0)
             x = philox.uniforms(problem.seed, tid, it, call, ns, D, mode, first_sample=s0)
             y, jac, bins = vegas.apply_map(edges, x)
-            w = integrand(problem, si, term, i, f_obs, dists, m, a, y) * jac
+            w = integrand(problem, si, term, i, f_obs, dists, m, a, y, w_frac) * jac
             sw += np.sum(w)
             sw2 += np.sum(w * w)
             d += vegas.training_data(bins, w, proc.nbins)
@@ -206,6 +212,8 @@ def collision(problem, f, t, state, mode="f64", points=None):
     detail = {}
     pts = range(n) if points is None else points
     dists = distributions(problem, f, t)
+    widths = {p: state.widths.get(p, proc.width) for p, proc in enumerate(problem.processes)}
+    per_process = {p: ([], []) for p in range(len(problem.processes))}
     for k, si in enumerate(side_integrals(problem)):
         nb = problem.processes[si.process].nbins
         for i in pts:
@@ -216,13 +224,19 @@ def collision(problem, f, t, state, mode="f64", points=None):
                 if edges is None:
                     edges = vegas.uniform_edges(si.dim, nb)
                 mean, err, edges, _ = evaluate_task(problem, k, si, i, term, f, t, edges,
-                                                    state.call, mode, dists)
+                                                    state.call, mode, dists, widths[si.process])
                 state.maps[tid] = edges
                 detail[tid] = (mean, err)
                 res.append((mean, err))
+                per_process[si.process][0].append(mean)
+                per_process[si.process][1].append(err)
             (Ig, eg), (Il, el) = res
             C[si.species, i] += si.mult * (Ig - Il)
             var[si.species, i] += si.mult ** 2 * (eg * eg + el * el)
+    for p, proc in enumerate(problem.processes):
+        rel = owidth.relative_error(*per_process[p])
+        state.widths[p] = owidth.adapt(widths[p], rel, proc)
+        state.width_rel[p] = rel
     state.call += 1
     return C, np.sqrt(var), detail
 

@@ -53,7 +53,10 @@ def two_body_cm(p1, masses, f1, dist2, dist3, dist4, eta, lam=1.0, term="loss",
     legs; ``dist_k(q)`` give f_k, ``eta`` = (eta1..eta4) the (1 + eta f)
     signs; ``r_cut`` = (q_min, q_max) restricts |p3| and |p4| as the Monte
     Carlo restricts its integrated legs.  ``omega`` shifts the energy
-    balance to E3 + E4 = E1 + E2 - omega (used by ``two_body_cm_smeared``).
+    balance to E3 + E4 = E1 + E2 - omega (used by ``two_body_cm_smeared``);
+    a callable omega(E_in) returns (omega, weight) arrays for the initial
+    energy E_in = E1 + E2 of each node, the weight multiplying the integrand
+    (used by ``two_body_cm_fractional``).
     """
     m1, m2, m3, m4 = masses
     e1, e2, e3, e4 = eta
@@ -64,6 +67,9 @@ def two_body_cm(p1, masses, f1, dist2, dist3, dist4, eta, lam=1.0, term="loss",
     P2, C2, CS = np.meshgrid(p2, c2, cs, indexing="ij")
     W = w2[:, None, None] * wc2[None, :, None] * wcs[None, None, :]
     E2 = np.sqrt(P2 ** 2 + m2 * m2)
+    extra = 1.0
+    if callable(omega):
+        omega, extra = omega(E1 + E2)
     Ptot = np.sqrt(np.maximum(p1 * p1 + P2 ** 2 + 2.0 * p1 * P2 * C2, 0.0))
     Etot = E1 + E2 - omega
     s = Etot ** 2 - Ptot ** 2
@@ -93,7 +99,7 @@ def two_body_cm(p1, masses, f1, dist2, dist3, dist4, eta, lam=1.0, term="loss",
     phase = TWO_PI * pstar / (16.0 * np.pi ** 2 * rs)
     # d^3p2 / ((2pi)^3 2E2) with the azimuth of p2 giving 2 pi
     meas = TWO_PI * P2 ** 2 / (TWO_PI ** 3 * 2.0 * E2)
-    val = lam ** 2 * stat * phase * meas / (2.0 * E1)
+    val = lam ** 2 * stat * phase * meas / (2.0 * E1) * extra
     return float(np.sum(np.where(keep, val, 0.0) * W))
 
 
@@ -107,6 +113,24 @@ def two_body_cm_smeared(p1, masses, f1, dist2, dist3, dist4, eta, sigma, lam=1.0
     return float(sum(wk * gk * two_body_cm(p1, masses, f1, dist2, dist3, dist4, eta, lam,
                                            term, r_cut, omega=o, **kw)
                      for o, wk, gk in zip(om, wom, g)))
+
+
+def two_body_cm_fractional(p1, masses, f1, dist2, dist3, dist4, eta, w, lam=1.0,
+                           term="loss", r_cut=None, n_z=32, width=7.0, **kw):
+    """The same term with the fractional width of App. C: the Gaussian in
+    omega = E_in - E_out has sigma = w (E_in + E_out) / 2 = w (2 E_in - omega) / 2.
+    With omega = z sigma this gives omega = z w E_in / (1 + z w / 2) and
+    G d omega = phi(z) dz / (1 + z w / 2), phi the unit normal density;
+    Gauss-Legendre in z over [-width, width]."""
+    z, wz = _gl(-width, width, n_z)
+    total = 0.0
+    for zk, wk in zip(z, wz):
+        den = 1.0 + 0.5 * zk * w
+        phi = np.exp(-0.5 * zk * zk) / np.sqrt(TWO_PI)
+        om = lambda E_in, zk=zk, den=den: (zk * w * E_in / den, 1.0 / den)
+        total += wk * phi * two_body_cm(p1, masses, f1, dist2, dist3, dist4, eta, lam, term, r_cut,
+                                        omega=om, **kw)
+    return float(total)
 
 
 def paper_backward_term(p1, masses, f1, dist2, dist3, dist4, eta, lam=1.0,

@@ -32,6 +32,10 @@ STAT_NAMES = {STAT_MB: "MB", STAT_BE: "BE", STAT_FD: "FD"}
 PREC_FP64 = 0
 PREC_FP32 = 1
 
+WIDTH_ABSOLUTE = 0
+WIDTH_FRACTIONAL = 1
+WIDTH_ADAPTIVE = 2
+
 
 @dataclass(frozen=True)
 class Grid:
@@ -62,6 +66,19 @@ class Process:
     nbins: int = 50
     # Optional per-grid-point budgets (uneven budgets); overrides neval.
     neval_per_point: Optional[Tuple[int, ...]] = None
+    # Width of the Gaussian of Eq. (11): WIDTH_ABSOLUTE uses sigma_E;
+    # WIDTH_FRACTIONAL uses sigma = w (E_in + E_out) / 2 per sample with w =
+    # width; WIDTH_ADAPTIVE also adapts w after every evaluation (App. C):
+    # w / width_factor when the process's relative MC error is below
+    # width_rel_lo, w * width_factor when above width_rel_hi, within
+    # [width_min, width_max].
+    width_mode: int = 0
+    width: float = 0.01
+    width_rel_lo: float = 1e-3
+    width_rel_hi: float = 1e-2
+    width_factor: float = 1.25
+    width_min: float = 1e-4
+    width_max: float = 0.2
 
 
 @dataclass(frozen=True)
