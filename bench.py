@@ -266,6 +266,31 @@ def run_native(args, rank, world):
         vjp = {"ms_per_vjp": vms, "samples": col.sweep_samples(0),
                "samples_per_s": col.sweep_samples(0) / (vms / 1e3),
                "what": "dL/df, dL/dm, dL/dcoupling of v.C~ (fixed samples, one iteration per task), FP32"}
+    implicit = None
+    if WORKLOAD_KEY == "c5" or args.implicit:
+        fcur = torch.exp(logf)
+        tt = float(t.item())
+        u = fcur.clone()
+        C, _ = col.jvp(fcur, u, tt)
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record()
+        for _ in range(3):
+            col.jvp(fcur, u, tt)
+        b1.record()
+        torch.cuda.synchronize()
+        jms = b0.elapsed_time(b1) / 3
+        rate = float((C / fcur).abs().max().item())
+        dt_imp = 10.0 * prob.eps_dt / rate           # ten times the explicit bound of Eq. (16)
+        lg = logf.clone()
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        info = col.step_implicit_euler(lg, tt, dt_imp, train=False, max_newton=12, krylov_dim=32,
+                                       raise_on_failure=False)
+        ims = (time.perf_counter() - c0) * 1e3
+        implicit = {"ms_per_jvp": jms, "ms_per_step": ims, "dt": dt_imp, "dt_over_explicit_bound": 10.0, **info,
+                    "what": "backward Euler of log f, Newton-GMRES on the fixed-sample C~ (maps kept), FP32"}
     col.close()
 
     # ---------------- FP64 path (same workload, fewer steps) ---------------------------------
@@ -336,6 +361,7 @@ def run_native(args, rank, world):
         if fp64 else None,
         "roofline": roof,
         "vjp": vjp,
+        "implicit_euler": implicit,
         "e2e": {"value": sweeps / (ms_e2e / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": logf.numel() * 8 + 8, "d2h_bytes_per_step": logf.numel() * 8 + 8},
         "graph": "Heun steps replayed from a CUDA graph (best_evolve)",
@@ -420,6 +446,7 @@ def main():
                     help="samples per task per iteration (smaller cases for profiling)")
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--vjp", action="store_true", help="also time the adjoint")
+    ap.add_argument("--implicit", action="store_true", help="also time the tangent and one implicit Euler step")
     args = ap.parse_args()
     global NEVAL, WORKLOAD_KEY
     NEVAL = args.neval

@@ -74,7 +74,13 @@ typedef struct {
  * non-NULL neval_per_point (host array of grid.n entries, copied during
  * best_collision_init) overrides it per grid point.  nitn VEGAS iterations
  * per evaluation, damping alpha, nbins increments per dimension (2..256).
- * sigma_E is the width of the Gaussian of Eq. (11). */
+ * The Gaussian of Eq. (11) has width sigma_E (width_mode 0), or the
+ * fractional width of App. C, sigma = w (E_in + E_out) / 2 per sample, with
+ * w = width fixed (width_mode 1) or adapted after every evaluation
+ * (width_mode 2): with r = sqrt(sum err_t^2) / sum |I_t| over the process's
+ * tasks, w /= width_factor when r < width_rel_lo, w *= width_factor when
+ * r > width_rel_hi, then clamped to [width_min, width_max]; the new w is
+ * used from the next evaluation on. */
 typedef struct {
     int32_t n_in, n_out;
     int32_t species[BEST_MAX_LEGS];
@@ -85,6 +91,10 @@ typedef struct {
     int32_t nitn;
     int32_t nbins;
     double alpha;
+    int32_t width_mode;    /* 0: sigma_E; 1: fractional w; 2: fractional, adapted */
+    int32_t pad_;
+    double width;          /* initial w (modes 1, 2) */
+    double width_rel_lo, width_rel_hi, width_factor, width_min, width_max;   /* mode 2 */
 } best_process;
 
 typedef struct {
@@ -246,6 +256,17 @@ best_status best_step_implicit_euler(best_ctx* ctx, double* logf_dev, double t, 
 int64_t best_state_size(const best_ctx* ctx);
 best_status best_save_state(best_ctx* ctx, void* host_buf, int64_t size);
 best_status best_load_state(best_ctx* ctx, const void* host_buf, int64_t size);
+
+/*
+ * Fractional Gaussian widths (App. C), one per process, as used by the next
+ * evaluation: w[p] (0 for width_mode 0) and rel[p], the relative error r of
+ * the last evaluation that updated it (0 before any).  Either pointer may be
+ * NULL; host arrays of n_processes.  best_set_widths overrides w for the
+ * processes with width_mode != 0 (each value must be > 0; synchronous).
+ * The widths are part of the state saved by best_save_state.
+ */
+best_status best_get_widths(best_ctx* ctx, double* w, double* rel);
+best_status best_set_widths(best_ctx* ctx, const double* w);
 
 /* Context geometry. */
 int32_t best_num_tasks(const best_ctx* ctx);

@@ -50,6 +50,13 @@ def config_from_problem(problem, precision):
         pr[k].nitn = int(p.nitn)
         pr[k].nbins = int(p.nbins)
         pr[k].alpha = float(p.alpha)
+        pr[k].width_mode = int(getattr(p, "width_mode", 0))
+        pr[k].width = float(getattr(p, "width", 0.01))
+        pr[k].width_rel_lo = float(getattr(p, "width_rel_lo", 1e-3))
+        pr[k].width_rel_hi = float(getattr(p, "width_rel_hi", 1e-2))
+        pr[k].width_factor = float(getattr(p, "width_factor", 1.25))
+        pr[k].width_min = float(getattr(p, "width_min", 1e-4))
+        pr[k].width_max = float(getattr(p, "width_max", 0.2))
     cfg = _lib.best_config()
     cfg.grid.n = int(g.n)
     cfg.grid.log_spaced = 1 if g.log_spaced else 0
@@ -192,20 +199,39 @@ class Collision:
         return C, JU
 
     def step_implicit_euler(self, logf, t, dt, train=True, tol=None, max_newton=8, krylov_dim=24,
-                            krylov_rtol=1e-6, stream=None):
+                            krylov_rtol=1e-6, stream=None, raise_on_failure=True):
         """Backward Euler step of log f in place (Newton-Krylov on the
         fixed-sample integral at t + dt).  tol defaults to 1e-10 (FP64) or
         1e-6 (FP32) in ||R||_inf.  Returns a dict of the solver's counts;
-        raises BestError when Newton does not converge (logf unchanged)."""
+        when Newton does not converge, logf is unchanged and BestError is
+        raised (or, with raise_on_failure=False, the dict has converged=False)."""
         n = self.n_species * self.n_grid
         _require(logf, n, "logf")
         if tol is None:
             tol = 1e-6 if self.precision == 1 else 1e-10          # 1: FP32
         info = (ctypes.c_double * 5)()
-        check(self.lib.best_step_implicit_euler(self.ctx, _ptr(logf), float(t), float(dt), int(bool(train)),
-                                                float(tol), int(max_newton), int(krylov_dim), float(krylov_rtol),
-                                                info, _stream(stream)), self.ctx)
-        return {"newton": int(info[0]), "krylov": int(info[1]), "residual": info[2], "halvings": int(info[4])}
+        st = self.lib.best_step_implicit_euler(self.ctx, _ptr(logf), float(t), float(dt), int(bool(train)),
+                                               float(tol), int(max_newton), int(krylov_dim), float(krylov_rtol),
+                                               info, _stream(stream))
+        out = {"newton": int(info[0]), "krylov": int(info[1]), "residual": info[2], "converged": info[3] == 1.0,
+               "halvings": int(info[4])}
+        if st != 0 and (raise_on_failure or out["converged"] or info[0] == 0):
+            check(st, self.ctx)
+        return out
+
+    def widths(self):
+        """(w, rel): the fractional Gaussian width of every process as the
+        next evaluation uses it, and the relative error that last set it."""
+        P = len(self.problem.processes)
+        w = (ctypes.c_double * P)()
+        r = (ctypes.c_double * P)()
+        check(self.lib.best_get_widths(self.ctx, w, r), self.ctx)
+        return np.array(w[:]), np.array(r[:])
+
+    def set_widths(self, w):
+        P = len(self.problem.processes)
+        arr = (ctypes.c_double * P)(*[float(x) for x in w])
+        check(self.lib.best_set_widths(self.ctx, arr), self.ctx)
 
     def save_state(self):
         """Maps, scales, counter and time state as bytes (see checkpoint.py)."""

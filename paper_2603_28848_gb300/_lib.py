@@ -24,7 +24,9 @@ class best_process(ctypes.Structure):
     _fields_ = [("n_in", c_int32), ("n_out", c_int32), ("species", c_int32 * MAX_LEGS),
                 ("coupling", c_double), ("sigma_E", c_double), ("neval", c_int64),
                 ("neval_per_point", POINTER(c_int64)), ("nitn", c_int32), ("nbins", c_int32),
-                ("alpha", c_double)]
+                ("alpha", c_double), ("width_mode", c_int32), ("pad_", c_int32), ("width", c_double),
+                ("width_rel_lo", c_double), ("width_rel_hi", c_double), ("width_factor", c_double),
+                ("width_min", c_double), ("width_max", c_double)]
 
 
 class best_config(ctypes.Structure):
@@ -52,6 +54,8 @@ SIGNATURES = {
     "best_collision_jvp": ([c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "best_step_implicit_euler": ([c_void_p, c_void_p, c_double, c_double, c_int32, c_double, c_int32, c_int32,
                                   c_double, c_void_p, c_void_p], c_int32),
+    "best_get_widths": ([c_void_p, c_void_p, c_void_p], c_int32),
+    "best_set_widths": ([c_void_p, c_void_p], c_int32),
     "best_state_size": ([c_void_p], c_int64),
     "best_save_state": ([c_void_p, c_void_p, c_int64], c_int32),
     "best_load_state": ([c_void_p, c_void_p, c_int64], c_int32),

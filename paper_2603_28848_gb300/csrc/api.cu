@@ -20,7 +20,9 @@ __global__ void set_time_kernel(Geometry, TimeState*, const double*, double, int
 __global__ void spline_build_kernel(Geometry, const double*, int, const double*, TimeState*, SpeciesConst*,
                                     double*, double*, float*);
 __global__ void prepare_kernel(Geometry, const SideDesc*, const TaskDesc*, const double*, const double*,
-                               const TimeState*, const double*, TaskConst*, TaskAcc*, int);
+                               const TimeState*, const double*, TaskConst*, TaskAcc*, int, const double*);
+__global__ void width_control_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskAcc*, const WidthCtl*,
+                                     double*, double*);
 __global__ void refine_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskConst*, const int32_t*,
                               const int32_t*, const Segment*, const double*, double*, TaskAcc*, TaskConst*);
 __global__ void assemble_kernel(Geometry, const SideDesc*, TaskAcc*, TimeState*, double*, double*, double*);
@@ -143,6 +145,12 @@ struct best_ctx {
     double* d_dtail = nullptr;      // [species][4]
     size_t jvp_smem = 0;
     bool jvp_ready = false;         // shared-memory attribute of the tangent kernel set
+    // fractional Gaussian widths (App. C), one per process
+    double* d_width = nullptr;
+    double* d_width_rel = nullptr;
+    WidthCtl* d_wctl = nullptr;
+    std::vector<int> width_mode;
+    bool any_adaptive = false;
     // implicit Euler (best_step_implicit_euler): Krylov basis and work vectors
     double* d_nk = nullptr;
     int nk_m = 0;
@@ -204,7 +212,7 @@ void free_all(best_ctx* c) {
                     c->d_knots, c->d_knots32, c->d_coef64, c->d_coef32, c->d_fgrid, c->d_mass0, c->d_mass1,
                     c->d_partials, c->d_k1, c->d_k2, c->d_fstar, c->d_prev, c->d_dtreq,
                     c->d_gcoef, c->d_vjp_tot, c->d_u, c->d_gtail, c->d_coupling, c->d_dcoef64,
-                    c->d_dcoef32, c->d_dtail, c->d_nk};
+                    c->d_dcoef32, c->d_dtail, c->d_nk, c->d_width, c->d_width_rel, c->d_wctl};
     if (c->graph) cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
     for (void* b : bufs) cudaFree(b);
@@ -243,6 +251,17 @@ best_status validate(const best_config* cfg) {
             if (pr.species[k] < 0 || pr.species[k] >= cfg->n_species)
                 return fail(ctx, BEST_ERR_INVALID, "process %d: leg %d has a bad species", p, k);
         if (!(pr.sigma_E > 0.0)) return fail(ctx, BEST_ERR_INVALID, "process %d: sigma_E must be > 0", p);
+        if (pr.width_mode < 0 || pr.width_mode > 2)
+            return fail(ctx, BEST_ERR_INVALID, "process %d: width_mode must be 0, 1 or 2", p);
+        if (pr.width_mode != 0 && !(pr.width > 0.0 && std::isfinite(pr.width)))
+            return fail(ctx, BEST_ERR_INVALID, "process %d: width must be > 0", p);
+        if (pr.width_mode == 2 &&
+            !(pr.width_min > 0.0 && pr.width_min <= pr.width && pr.width <= pr.width_max &&
+              std::isfinite(pr.width_max) && pr.width_factor > 1.0 && std::isfinite(pr.width_factor) &&
+              pr.width_rel_lo >= 0.0 && pr.width_rel_lo < pr.width_rel_hi))
+            return fail(ctx, BEST_ERR_INVALID,
+                        "process %d: adaptive width needs 0 < width_min <= width <= width_max, width_factor > 1, "
+                        "0 <= width_rel_lo < width_rel_hi", p);
         if (pr.nitn < 1 || pr.nitn > 1000) return fail(ctx, BEST_ERR_INVALID, "process %d: nitn in [1,1000]", p);
         if (pr.nbins < 2 || pr.nbins > 256) return fail(ctx, BEST_ERR_INVALID, "process %d: nbins in [2,256]", p);
         if (!(pr.alpha >= 0.0)) return fail(ctx, BEST_ERR_INVALID, "process %d: alpha must be >= 0", p);
@@ -387,7 +406,7 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
         g, src, src_mode, ctx->d_knots, ctx->d_ts, ctx->d_sconst, ctx->d_fgrid, ctx->d_coef64, ctx->d_coef32);
     prepare_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_knots,
                                                             ctx->d_fgrid, ctx->d_ts, ctx->d_prev, ctx->d_tconst,
-                                                            ctx->d_acc, 1);
+                                                            ctx->d_acc, 1, ctx->d_width);
     ctx->launches += 2;
     const bool f32 = ctx->precision == BEST_FP32;
     for (int it = 0; it < ctx->max_nitn; ++it) {
@@ -438,6 +457,11 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
     assemble_kernel<<<(total + 255) / 256, 256, 0, st>>>(g, ctx->d_sides, ctx->d_acc, ctx->d_ts, C, err,
                                                          ctx->d_prev);
     ctx->launches += 1;
+    if (ctx->any_adaptive) {
+        width_control_kernel<<<ctx->n_processes, 256, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_acc,
+                                                               ctx->d_wctl, ctx->d_width, ctx->d_width_rel);
+        ctx->launches += 1;
+    }
     CK(cudaGetLastError());
     return BEST_OK;
 }
@@ -502,6 +526,8 @@ bool describe_task(const best_config* cfg, int32_t task, SideDesc* out_sd, TaskD
                     const int st_obs = cfg->species[a].stat;
                     sd.eta_obs = st_obs == BEST_BE ? 1.0 : (st_obs == BEST_FD ? -1.0 : 0.0);
                     sd.sigma = pr.sigma_E;
+                    sd.width_mode = pr.width_mode;
+                    sd.width0 = pr.width;
                     TaskDesc td{};
                     td.si = 0;
                     td.point = (task / 2) % n_grid;
@@ -595,6 +621,8 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
                 const int st_obs = cfg->species[a].stat;
                 sd.eta_obs = st_obs == BEST_BE ? 1.0 : (st_obs == BEST_FD ? -1.0 : 0.0);
                 sd.sigma = pr.sigma_E;
+                sd.width_mode = pr.width_mode;
+                sd.width0 = pr.width;
                 ctx->sides.push_back(sd);
             }
         }
@@ -713,6 +741,26 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     CKI(dalloc(&ctx->d_dcoef64, static_cast<size_t>(S) * (n - 1) * 4));
     CKI(dalloc(&ctx->d_dcoef32, static_cast<size_t>(S) * (n - 1) * 4));
     CKI(dalloc(&ctx->d_dtail, static_cast<size_t>(S) * 4));
+    {
+        const int P = cfg->n_processes;
+        CKI(dalloc(&ctx->d_width, static_cast<size_t>(P)));
+        CKI(dalloc(&ctx->d_width_rel, static_cast<size_t>(P)));
+        CKI(dalloc(&ctx->d_wctl, static_cast<size_t>(P)));
+        std::vector<double> w0(P), zero(P, 0.0);
+        std::vector<WidthCtl> wc(P);
+        ctx->width_mode.assign(P, 0);
+        for (int p = 0; p < P; ++p) {
+            const best_process& pr = cfg->processes[p];
+            w0[p] = pr.width_mode == 0 ? 0.0 : pr.width;
+            wc[p] = WidthCtl{pr.width_mode, 0, pr.width_rel_lo, pr.width_rel_hi, pr.width_factor, pr.width_min,
+                             pr.width_max};
+            ctx->width_mode[p] = pr.width_mode;
+            if (pr.width_mode == 2) ctx->any_adaptive = true;
+        }
+        CKI(cudaMemcpy(ctx->d_width, w0.data(), P * sizeof(double), cudaMemcpyHostToDevice));
+        CKI(cudaMemcpy(ctx->d_width_rel, zero.data(), P * sizeof(double), cudaMemcpyHostToDevice));
+        CKI(cudaMemcpy(ctx->d_wctl, wc.data(), P * sizeof(WidthCtl), cudaMemcpyHostToDevice));
+    }
     {
         std::vector<double> lam(cfg->n_processes);
         for (int p = 0; p < cfg->n_processes; ++p) lam[p] = cfg->processes[p].coupling;
@@ -928,7 +976,8 @@ best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, con
     spline_build_kernel<<<g.n_species, 256, ctx->spline_smem, st>>>(
         g, f_dev, 0, ctx->d_knots, ctx->d_ts, ctx->d_sconst, ctx->d_fgrid, ctx->d_coef64, ctx->d_coef32);
     prepare_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_knots, ctx->d_fgrid,
-                                                            ctx->d_ts, ctx->d_prev, ctx->d_tconst, ctx->d_acc, 0);
+                                                            ctx->d_ts, ctx->d_prev, ctx->d_tconst, ctx->d_acc, 0,
+                                                            ctx->d_width);
     vjp_seed_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_tconst, v_dev,
                                                              ctx->d_u);
     CK(cudaMemsetAsync(ctx->d_gcoef, 0, sizeof(double) * g.n_species * (g.n_grid - 1) * 4, st));
@@ -1026,7 +1075,7 @@ static best_status enqueue_jvp(best_ctx* ctx, const double* f_dev, double t, con
             g, f_dev, 0, ctx->d_knots, ctx->d_ts, ctx->d_sconst, ctx->d_fgrid, ctx->d_coef64, ctx->d_coef32);
         prepare_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_knots,
                                                                 ctx->d_fgrid, ctx->d_ts, ctx->d_prev, ctx->d_tconst,
-                                                                ctx->d_acc, 0);
+                                                                ctx->d_acc, 0, ctx->d_width);
         ctx->launches += 3;
     }
     jvp_seed_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_tconst,
@@ -1218,7 +1267,7 @@ int64_t best_state_size(const best_ctx* ctx) {
     if (!ctx) return 0;
     const int64_t T = ctx->geo.n_tasks;
     return static_cast<int64_t>(sizeof(StateHeader)) + 8 * T * ctx->geo.map_stride + 8 * T +
-           static_cast<int64_t>(sizeof(TimeState));
+           static_cast<int64_t>(sizeof(TimeState)) + 16 * static_cast<int64_t>(ctx->n_processes);
 }
 
 best_status best_save_state(best_ctx* ctx, void* host_buf, int64_t size) {
@@ -1235,6 +1284,10 @@ best_status best_save_state(best_ctx* ctx, void* host_buf, int64_t size) {
     CK(cudaMemcpy(p, ctx->d_prev, ctx->geo.n_tasks * sizeof(double), cudaMemcpyDeviceToHost));
     p += ctx->geo.n_tasks * sizeof(double);
     CK(cudaMemcpy(p, ctx->d_ts, sizeof(TimeState), cudaMemcpyDeviceToHost));
+    p += sizeof(TimeState);
+    CK(cudaMemcpy(p, ctx->d_width, ctx->n_processes * sizeof(double), cudaMemcpyDeviceToHost));
+    p += ctx->n_processes * sizeof(double);
+    CK(cudaMemcpy(p, ctx->d_width_rel, ctx->n_processes * sizeof(double), cudaMemcpyDeviceToHost));
     return BEST_OK;
 }
 
@@ -1255,6 +1308,34 @@ best_status best_load_state(best_ctx* ctx, const void* host_buf, int64_t size) {
     CK(cudaMemcpy(ctx->d_prev, p, ctx->geo.n_tasks * sizeof(double), cudaMemcpyHostToDevice));
     p += ctx->geo.n_tasks * sizeof(double);
     CK(cudaMemcpy(ctx->d_ts, p, sizeof(TimeState), cudaMemcpyHostToDevice));
+    p += sizeof(TimeState);
+    CK(cudaMemcpy(ctx->d_width, p, ctx->n_processes * sizeof(double), cudaMemcpyHostToDevice));
+    p += ctx->n_processes * sizeof(double);
+    CK(cudaMemcpy(ctx->d_width_rel, p, ctx->n_processes * sizeof(double), cudaMemcpyHostToDevice));
+    return BEST_OK;
+}
+
+best_status best_get_widths(best_ctx* ctx, double* w, double* rel) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    CK(cudaDeviceSynchronize());
+    if (w) CK(cudaMemcpy(w, ctx->d_width, ctx->n_processes * sizeof(double), cudaMemcpyDeviceToHost));
+    if (rel) CK(cudaMemcpy(rel, ctx->d_width_rel, ctx->n_processes * sizeof(double), cudaMemcpyDeviceToHost));
+    return BEST_OK;
+}
+
+best_status best_set_widths(best_ctx* ctx, const double* w) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    if (!w) return fail(ctx, BEST_ERR_INVALID, "w is NULL");
+    std::vector<double> cur(ctx->n_processes);
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(cur.data(), ctx->d_width, cur.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int p = 0; p < ctx->n_processes; ++p) {
+        if (ctx->width_mode[p] == 0) continue;
+        if (!(w[p] > 0.0) || !std::isfinite(w[p]))
+            return fail(ctx, BEST_ERR_INVALID, "process %d: width must be > 0", p);
+        cur[p] = w[p];
+    }
+    CK(cudaMemcpy(ctx->d_width, cur.data(), cur.size() * sizeof(double), cudaMemcpyHostToDevice));
     return BEST_OK;
 }
 

@@ -95,7 +95,9 @@ struct SegConst {
     int sp_cons;
     R inv_a, a;
     R c0;                   // obs factor / scale
-    R gauss_k;              // -log2(e) / (2 sigma^2)
+    R gauss_k;              // -log2(e) / (2 sigma^2); fractional width: -2 log2(e) / w^2
+    R e_obs;                // E_obs (fractional width: sigma_ref / sigma = 2 E_obs / (E_in + E_out))
+    bool frac;              // fractional width of App. C
     R e_cut;
     R eta_c;                // eta of the conserved leg (tail formula)
     R tlo_a, tlo_b, thi_a, thi_b;   // Eq. (13) end fits of the conserved leg's species
@@ -231,7 +233,10 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
     C.inv_a = static_cast<R>(1.0 / ts.a);
     // the observed leg's own cut (App. A) removes the whole task
     C.c0 = tc.E_obs < g.e_cut ? R(0) : static_cast<R>(tc.obs_factor / tc.scale);
-    C.gauss_k = static_cast<R>(-1.4426950408889634 / (2.0 * sd.sigma * sd.sigma));
+    C.frac = tc.wfrac > 0.0;
+    C.gauss_k = static_cast<R>(C.frac ? -2.0 * 1.4426950408889634 / (tc.wfrac * tc.wfrac)
+                                      : -1.4426950408889634 / (2.0 * sd.sigma * sd.sigma));
+    C.e_obs = static_cast<R>(tc.E_obs);
     C.e_cut = static_cast<R>(g.e_cut);
     const R nbR = static_cast<R>(nb);
     const R q0 = static_cast<R>(g.q_min);
@@ -288,6 +293,7 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
             // integrated legs
             R px = R(0), py = R(0), pz = C.pobs_sig;
             R dE = C.sgn_obs_E;
+            R Esum = C.e_obs;                   // E_in + E_out (used when C.frac)
             R meas = jac;
             R stat = C.c0;
             R rinvE_prod = R(1);
@@ -309,6 +315,7 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
                 const R E = E2 * rE;
                 cut |= E < C.e_cut;
                 dE = fma(C.sgnE[j], E, dE);
+                Esum += E;
                 meas *= r * r * st;
                 rinvE_prod *= rE;
                 const SplineView<R> sv{s_spline + C.spc[j] * ncoef, knots};
@@ -350,7 +357,17 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
                 fc = C.fd_c ? (fc < R(1) ? fc : R(1)) : fc;
             }
             stat *= fma(C.cbc, fc, C.cac);
-            const R gauss = RMath<R>::exp2_(C.gauss_k * dE * dE);
+            R gauss;
+            if (C.frac) {
+                // sigma = w S / 2 with S = E_in + E_out: exponent
+                // -2 dE^2 / (w S)^2, normalisation sigma_ref / sigma = 2 E_obs / S
+                Esum += Ec;
+                const R iS = RMath<R>::rcp_(Esum);
+                const R x = dE * iS;
+                gauss = RMath<R>::exp2_(C.gauss_k * x * x) * (R(2) * C.e_obs * iS);
+            } else {
+                gauss = RMath<R>::exp2_(C.gauss_k * dE * dE);
+            }
             R w = stat * meas * rinvE_prod * rEc * gauss;
             w = (cut || !valid) ? R(0) : w;
             const R w2 = w * w;

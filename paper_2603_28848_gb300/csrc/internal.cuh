@@ -32,6 +32,9 @@ struct SideDesc {
     double coupling2;       // |M|^2
     double sigma;           // sigma_E
     double eta_obs;         // eta of the observed species
+    int32_t width_mode;     // 0: sigma_E; 1: fractional w; 2: fractional, adapted (App. C)
+    int32_t pad_;
+    double width0;          // initial fractional width
 };
 
 // One task: side integral x grid point x {gain, loss}.
@@ -54,6 +57,14 @@ struct TaskConst {
     double f_obs;           // f_a(q_i), the grid value of the observed leg
     double E_obs;           // energy of the observed leg
     double p_obs;           // physical momentum of the observed leg
+    double wfrac;           // fractional width w of App. C this sweep (0: absolute sigma_E)
+};
+
+// Width controller of one process (App. C).
+struct WidthCtl {
+    int32_t mode;           // width_mode of the process
+    int32_t pad_;
+    double rel_lo, rel_hi, factor, w_min, w_max;
 };
 
 // Per-task VEGAS iteration combination accumulators (FP64).

@@ -214,7 +214,8 @@ __device__ inline double clamp_scale(double scale, double obs_factor) {
 __global__ void prepare_kernel(Geometry g, const SideDesc* __restrict__ sides,
                                const TaskDesc* __restrict__ tasks, const double* __restrict__ knots,
                                const double* __restrict__ fgrid, const TimeState* ts,
-                               const double* __restrict__ prev, TaskConst* tconst, TaskAcc* acc, int reset_acc) {
+                               const double* __restrict__ prev, TaskConst* tconst, TaskAcc* acc, int reset_acc,
+                               const double* __restrict__ width) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.n_tasks) return;
     const TaskDesc td = tasks[t];
@@ -232,8 +233,12 @@ __global__ void prepare_kernel(Geometry g, const SideDesc* __restrict__ sides,
     c.p_obs = p;
     c.E_obs = E;
     c.f_obs = fgrid[static_cast<int64_t>(sd.species_obs) * g.n_grid + td.point];
+    // fractional width (App. C): the per-sample factor sigma_ref / sigma with
+    // sigma_ref = w E_obs is applied in the sample kernel
+    c.wfrac = sd.width_mode == 0 ? 0.0 : (width ? width[sd.process] : sd.width0);
+    const double sigma_ref = sd.width_mode == 0 ? sd.sigma : c.wfrac * E;
     c.K = sd.coupling2 * nbD * a3 /
-          (two_pi_pow * ldexp(1.0, n) * E * sd.sigma * sqrt(kTwoPi));
+          (two_pi_pow * ldexp(1.0, n) * E * sigma_ref * sqrt(kTwoPi));
     c.obs_factor = td.term == 1 ? c.f_obs : 1.0 + sd.eta_obs * c.f_obs;
     const double est = prev[t];
     c.scale = clamp_scale(est > 0.0 && c.K > 0.0 ? est / c.K : (c.f_obs > 0.0 ? c.f_obs : 1.0), c.obs_factor);
@@ -415,6 +420,45 @@ __global__ void assemble_kernel(Geometry g, const SideDesc* __restrict__ sides, 
         if (err) err[k] = sqrt(v);
     }
     if (k == 0) ts->call += 1u;
+}
+
+// ---------------------------------------------------------------------------
+// Adaptive fractional width (App. C), one CTA per process after a sweep:
+// r = sqrt(sum err_t^2) / sum |I_t| over the process's tasks (FP64, fixed
+// summation order), then w /= factor below rel_lo, w *= factor above rel_hi,
+// clamped to [w_min, w_max]; processes with a fixed width are left alone.
+// ---------------------------------------------------------------------------
+__global__ void width_control_kernel(Geometry g, const SideDesc* __restrict__ sides,
+                                     const TaskDesc* __restrict__ tasks, const TaskAcc* __restrict__ acc,
+                                     const WidthCtl* __restrict__ ctl, double* width, double* width_rel) {
+    __shared__ double r2[256], ra[256];
+    const int p = blockIdx.x;
+    const WidthCtl c = ctl[p];
+    if (c.mode != 2) return;
+    double e2 = 0.0, am = 0.0;
+    for (int t = threadIdx.x; t < g.n_tasks; t += blockDim.x) {
+        if (sides[tasks[t].si].process != p) continue;
+        const TaskAcc& A = acc[t];
+        e2 = fma(A.err, A.err, e2);
+        am += fabs(A.mean);
+    }
+    r2[threadIdx.x] = e2;
+    ra[threadIdx.x] = am;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            r2[threadIdx.x] += r2[threadIdx.x + h];
+            ra[threadIdx.x] += ra[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0 || !(ra[0] > 0.0)) return;
+    const double rel = sqrt(r2[0]) / ra[0];
+    double w = width[p];
+    if (rel < c.rel_lo) w /= c.factor;
+    else if (rel > c.rel_hi) w *= c.factor;
+    width[p] = fmin(fmax(w, c.w_min), c.w_max);
+    width_rel[p] = rel;
 }
 
 // ---------------------------------------------------------------------------

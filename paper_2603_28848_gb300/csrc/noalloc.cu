@@ -19,7 +19,7 @@ namespace best {
 __global__ void spline_build_kernel(Geometry, const double*, int, const double*, TimeState*, SpeciesConst*,
                                     double*, double*, float*);
 __global__ void prepare_kernel(Geometry, const SideDesc*, const TaskDesc*, const double*, const double*,
-                               const TimeState*, const double*, TaskConst*, TaskAcc*, int);
+                               const TimeState*, const double*, TaskConst*, TaskAcc*, int, const double*);
 void* eval_kernel_ptr_f32(int nmax);
 void* eval_kernel_ptr_f64(int nmax);
 best_status check_config(const best_config* cfg);
@@ -247,7 +247,7 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     noalloc_setup_kernel<<<1, 512, 0, st>>>(A, base);
     const size_t spline_smem = 3 * sizeof(double) * n;
     spline_build_kernel<<<S, 256, spline_smem, st>>>(g, f_dev, 0, knots, ts, sc, fgrid, coef64, coef32);
-    prepare_kernel<<<1, 32, 0, st>>>(g, dsd, dtd, knots, fgrid, ts, prev, dtc, dacc, 1);
+    prepare_kernel<<<1, 32, 0, st>>>(g, dsd, dtd, knots, fgrid, ts, prev, dtc, dacc, 1, nullptr);
 
     // The sample kernel indexes its descriptor arrays and the map by the task
     // id that also enters the Philox counter; the single task's entries sit

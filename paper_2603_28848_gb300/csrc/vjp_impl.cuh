@@ -143,8 +143,14 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
     const R a = static_cast<R>(ts.a), inv_a = static_cast<R>(1.0 / ts.a);
     const bool obs_cut = tc.E_obs < g.e_cut;       // every sample of the task is cut
     const R c0 = obs_cut ? R(0) : static_cast<R>(tc.obs_factor / tc.scale);
-    const R gauss_k = static_cast<R>(-1.4426950408889634 / (2.0 * sd.sigma * sd.sigma));
-    const R inv_sig2 = static_cast<R>(1.0 / (sd.sigma * sd.sigma));
+    // Gaussian of Eq. (11); fractional width (App. C): sigma = w S / 2 per
+    // sample, S = E_in + E_out, with sigma_ref = w E_obs inside K
+    const bool frac = tc.wfrac > 0.0;
+    const R gauss_k = static_cast<R>(frac ? -2.0 * 1.4426950408889634 / (tc.wfrac * tc.wfrac)
+                                          : -1.4426950408889634 / (2.0 * sd.sigma * sd.sigma));
+    const R inv_sig2_abs = static_cast<R>(1.0 / (sd.sigma * sd.sigma));
+    const R four_over_w2 = static_cast<R>(frac ? 4.0 / (tc.wfrac * tc.wfrac) : 0.0);
+    const R e_obs = static_cast<R>(tc.E_obs);
     const R e_cut = static_cast<R>(g.e_cut);
     const R inv_Eobs = static_cast<R>(1.0 / tc.E_obs);
     const R U = static_cast<R>(V.task_u[seg.task]);     // VJP: adjoint seed; JVP: obs tangent factor
@@ -201,6 +207,7 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
             }
             R px = R(0), py = R(0), pz = pobs_sig;
             R dE = sgn_obs_E;
+            R Esum = e_obs;
             R meas = jac;
             R rinv = R(1);
             bool cut = obs_cut;
@@ -222,6 +229,7 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
                 const R E = E2 * rr;
                 cut |= E < e_cut;
                 dE = fma(sgnE[j], E, dE);
+                Esum += E;
                 meas *= r * r * st;
                 rinv *= rr;
                 rE[j] = rr;
@@ -266,7 +274,22 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
                 }
             }
             fac[NI] = fma(cbc, fc, cac);
-            const R gs = RMath<R>::exp2_(gauss_k * dE * dE);
+            // Gaussian and, for the adjoint, 1/sigma^2 and the derivative of
+            // log(1/sigma) with exp(-dE^2 / 2 sigma^2) through sigma(E_k)
+            R gs, inv_sig2, sig_term;
+            if (frac) {
+                Esum += Ec;
+                const R iS = RMath<R>::rcp_(Esum);
+                const R x = dE * iS;
+                gs = RMath<R>::exp2_(gauss_k * x * x) * (R(2) * e_obs * iS);
+                inv_sig2 = four_over_w2 * iS * iS;
+                // d log g / d E_k from sigma: (dE^2 / sigma^2 - 1) / S for every leg
+                sig_term = fma(dE * dE, inv_sig2, R(-1)) * iS;
+            } else {
+                gs = RMath<R>::exp2_(gauss_k * dE * dE);
+                inv_sig2 = inv_sig2_abs;
+                sig_term = R(0);
+            }
             R base = meas * rinv * rEc * gs;
             base = (cut || !valid) ? R(0) : base;
             // products excluding each factor
@@ -304,15 +327,16 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
                 acc_dw.add(dw);
             } else {
             const R dEterm = -wn * dE * inv_sig2;
+            const R wsig = wn * sig_term;           // fractional width: same for every leg
 #pragma unroll
             for (int j = 0; j < NI; ++j) {
-                const R gE = fma(-wn, rE[j], dEterm * sgnE[j]);
+                const R gE = fma(-wn, rE[j], fma(dEterm, sgnE[j], wsig));
                 acc_m[j].add(gE * mass[j] * rE[j]);
             }
             const R gz = dwdf[NI] * dfdz;           // zero inside the grid
-            const R gEc = fma(-wn, rEc, fma(dEterm, sgn_cons, gz * (below ? tlo_b : thi_b)));
+            const R gEc = fma(-wn, rEc, fma(dEterm, sgn_cons, fma(gz, below ? tlo_b : thi_b, wsig)));
             acc_mc.add(gEc * mass_c * rEc);
-            acc_mobs.add(fma(-wn, inv_Eobs, dEterm * s_obs));
+            acc_mobs.add(fma(-wn, inv_Eobs, fma(dEterm, s_obs, wsig)));
             if (below) { acc_tla.add(gz); acc_tlb.add(gz * Ec); }
             if (above) { acc_tha.add(gz); acc_thb.add(gz * Ec); }
             // spline coefficient gradients of this sample's lookups
