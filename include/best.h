@@ -258,6 +258,19 @@ best_status best_save_state(best_ctx* ctx, void* host_buf, int64_t size);
 best_status best_load_state(best_ctx* ctx, const void* host_buf, int64_t size);
 
 /*
+ * Number and energy densities of every species at time t, the conservation
+ * diagnostics of a thermalisation run (Sec. 5C): n_s = Int q^2 f dq /
+ * (2 pi^2 a^3) and rho_s = Int q^2 E(q/a) f dq / (2 pi^2 a^3) over the grid
+ * range on the not-a-knot spline of f (unclamped, no tails), 4-point
+ * Gauss-Legendre per interval, FP64.  f_dev [n_species*n_grid], n_dev and
+ * rho_dev [n_species]: device pointers; asynchronous on `stream`.  Rebuilds
+ * the context's spline tables and time state (the next evaluation or step
+ * rebuilds them again).
+ */
+best_status best_moments(best_ctx* ctx, const double* f_dev, double t, double* n_dev, double* rho_dev,
+                         void* stream);
+
+/*
  * Fractional Gaussian widths (App. C), one per process, as used by the next
  * evaluation: w[p] (0 for width_mode 0) and rel[p], the relative error r of
  * the last evaluation that updated it (0 before any).  Either pointer may be

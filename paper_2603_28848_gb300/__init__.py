@@ -219,6 +219,15 @@ class Collision:
             check(st, self.ctx)
         return out
 
+    def moments(self, f, t=0.0, stream=None):
+        """(n, rho): number and energy density of every species (device tensors)."""
+        import torch
+        _require(f, self.n_species * self.n_grid, "f")
+        n = torch.empty(self.n_species, dtype=torch.float64, device=f.device)
+        rho = torch.empty_like(n)
+        check(self.lib.best_moments(self.ctx, _ptr(f), float(t), _ptr(n), _ptr(rho), _stream(stream)), self.ctx)
+        return n, rho
+
     def widths(self):
         """(w, rel): the fractional Gaussian width of every process as the
         next evaluation uses it, and the relative error that last set it."""

@@ -54,6 +54,7 @@ SIGNATURES = {
     "best_collision_jvp": ([c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "best_step_implicit_euler": ([c_void_p, c_void_p, c_double, c_double, c_int32, c_double, c_int32, c_int32,
                                   c_double, c_void_p, c_void_p], c_int32),
+    "best_moments": ([c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p], c_int32),
     "best_get_widths": ([c_void_p, c_void_p, c_void_p], c_int32),
     "best_set_widths": ([c_void_p, c_void_p], c_int32),
     "best_state_size": ([c_void_p], c_int64),

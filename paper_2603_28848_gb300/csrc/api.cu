@@ -21,6 +21,7 @@ __global__ void spline_build_kernel(Geometry, const double*, int, const double*,
                                     double*, double*, float*);
 __global__ void prepare_kernel(Geometry, const SideDesc*, const TaskDesc*, const double*, const double*,
                                const TimeState*, const double*, TaskConst*, TaskAcc*, int, const double*);
+__global__ void moments_kernel(Geometry, const double*, const double*, const TimeState*, double*, double*);
 __global__ void width_control_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskAcc*, const WidthCtl*,
                                      double*, double*);
 __global__ void refine_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskConst*, const int32_t*,
@@ -1312,6 +1313,22 @@ best_status best_load_state(best_ctx* ctx, const void* host_buf, int64_t size) {
     CK(cudaMemcpy(ctx->d_width, p, ctx->n_processes * sizeof(double), cudaMemcpyHostToDevice));
     p += ctx->n_processes * sizeof(double);
     CK(cudaMemcpy(ctx->d_width_rel, p, ctx->n_processes * sizeof(double), cudaMemcpyHostToDevice));
+    return BEST_OK;
+}
+
+best_status best_moments(best_ctx* ctx, const double* f_dev, double t, double* n_dev, double* rho_dev,
+                         void* stream) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    if (!f_dev || !n_dev || !rho_dev) return fail(ctx, BEST_ERR_INVALID, "f, n and rho must not be NULL");
+    if (!std::isfinite(t)) return fail(ctx, BEST_ERR_INVALID, "t must be finite");
+    const Geometry& g = ctx->geo;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    set_time_kernel<<<1, 32, 0, st>>>(g, ctx->d_ts, nullptr, t, 0, ctx->d_mass0, ctx->d_mass1);
+    spline_build_kernel<<<g.n_species, 256, ctx->spline_smem, st>>>(
+        g, f_dev, 0, ctx->d_knots, ctx->d_ts, ctx->d_sconst, ctx->d_fgrid, ctx->d_coef64, ctx->d_coef32);
+    moments_kernel<<<g.n_species, 256, 0, st>>>(g, ctx->d_knots, ctx->d_coef64, ctx->d_ts, n_dev, rho_dev);
+    ctx->launches = 3;
+    CK(cudaGetLastError());
     return BEST_OK;
 }
 

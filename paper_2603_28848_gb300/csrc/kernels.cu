@@ -423,6 +423,51 @@ __global__ void assemble_kernel(Geometry g, const SideDesc* __restrict__ sides, 
 }
 
 // ---------------------------------------------------------------------------
+// Number and energy densities, one CTA (256 threads) per species:
+//   n = Int q^2 f dq / (2 pi^2 a^3),  rho = Int q^2 E(q/a) f dq / (2 pi^2 a^3)
+// over [q_min, q_max] on the FP64 not-a-knot spline (unclamped), 4-point
+// Gauss-Legendre per grid interval, fixed-order tree reduction.
+// ---------------------------------------------------------------------------
+__global__ void moments_kernel(Geometry g, const double* __restrict__ knots, const double* __restrict__ coef64,
+                               const TimeState* ts, double* n_out, double* rho_out) {
+    __shared__ double sn[256], sr[256];
+    const int s = blockIdx.x;
+    const double a = ts->a, m = ts->mass[s];
+    const double xg[4] = {-0.8611363115940526, -0.3399810435848563, 0.3399810435848563, 0.8611363115940526};
+    const double wg[4] = {0.3478548451374538, 0.6521451548625461, 0.6521451548625461, 0.3478548451374538};
+    double an = 0.0, ar = 0.0;
+    for (int j = threadIdx.x; j < g.n_grid - 1; j += blockDim.x) {
+        const double* c = coef64 + (static_cast<int64_t>(s) * (g.n_grid - 1) + j) * 4;
+        const double lo = knots[j], hi = knots[j + 1];
+        const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+        for (int k = 0; k < 4; ++k) {
+            const double q = fma(half, xg[k], mid);
+            const double tt = q - lo;
+            const double f = fma(fma(fma(c[3], tt, c[2]), tt, c[1]), tt, c[0]);
+            const double p = q / a;
+            const double wq = half * wg[k] * q * q * f;
+            an += wq;
+            ar += wq * sqrt(fma(p, p, m * m));
+        }
+    }
+    sn[threadIdx.x] = an;
+    sr[threadIdx.x] = ar;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            sn[threadIdx.x] += sn[threadIdx.x + h];
+            sr[threadIdx.x] += sr[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double pref = 1.0 / (2.0 * kPi * kPi * a * a * a);
+        n_out[s] = pref * sn[0];
+        rho_out[s] = pref * sr[0];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Adaptive fractional width (App. C), one CTA per process after a sweep:
 // r = sqrt(sum err_t^2) / sum |I_t| over the process's tasks (FP64, fixed
 // summation order), then w /= factor below rel_lo, w *= factor above rel_hi,
