@@ -35,7 +35,7 @@ from typing import Dict
 import numpy as np
 
 from workloads import PREC_FP32
-from . import philox, vegas, width as owidth
+from . import philox, stratified, vegas, width as owidth
 from .spline import ETA, Distribution
 from .tasks import SIDE_IN, side_integrals, task_id
 
@@ -159,16 +159,24 @@ class State:
     call: int = 0
     widths: Dict[int, float] = field(default_factory=dict)
     width_rel: Dict[int, float] = field(default_factory=dict)
+    strata: Dict[int, np.ndarray] = field(default_factory=dict)
 
 
 def task_budget(proc, i):
-    return proc.neval_per_point[i] if proc.neval_per_point is not None else proc.neval
+    """Samples per iteration of a task (stratified: whole items of 8)."""
+    N = proc.neval_per_point[i] if proc.neval_per_point is not None else proc.neval
+    if getattr(proc, "strat", 0):
+        N = stratified.CHUNK_ITEMS * (N // stratified.CHUNK_ITEMS)
+    return N
 
 
-def evaluate_task(problem, si_index, si, i, term, f, t, edges, call, mode="f64", dists=None, w_frac=None):
+def evaluate_task(problem, si_index, si, i, term, f, t, edges, call, mode="f64", dists=None, w_frac=None,
+                  strata=None):
     """Run the nitn VEGAS iterations of one task.
 
-    Returns (mean, err, edges_after, per-iteration list of (mean, var)).
+    Returns (mean, err, edges_after, per-iteration list of (mean, var),
+    strata_after); strata is the stratified allocation (items per hypercube)
+    or None without stratification.
     """
     proc = problem.processes[si.process]
     if dists is None:
@@ -179,23 +187,45 @@ def evaluate_task(problem, si_index, si, i, term, f, t, edges, call, mode="f64",
     D = si.dim
     N = task_budget(proc, i)
     tid = task_id(si_index, i, term, problem.grid.n)
+    strat = bool(getattr(proc, "strat", 0))
+    if strat:
+        M, H, J = stratified.shape(N, D, proc.strat_max_hcubes)
+        alloc = strata if strata is not None else stratified.uniform_allocation(J, H)
     iters = []
     for it in range(proc.nitn):
         sw = 0.0
         sw2 = 0.0
         d = np.zeros((D, proc.nbins))
+        if strat:
+            item_h = np.repeat(np.arange(H), alloc)
+            S1 = np.zeros(H)
+            S2 = np.zeros(H)
         for s0 in range(0, N, CHUNK):
             ns = min(CHUNK, N - s0)
             x = philox.uniforms(problem.seed, tid, it, call, ns, D, mode, first_sample=s0)
+            if strat:
+                h = item_h[np.arange(s0, s0 + ns) // stratified.CHUNK_ITEMS]
+                x = (stratified.digits(h, M, D) + x) / M
             y, jac, bins = vegas.apply_map(edges, x)
             w = integrand(problem, si, term, i, f_obs, dists, m, a, y, w_frac) * jac
-            sw += np.sum(w)
-            sw2 += np.sum(w * w)
-            d += vegas.training_data(bins, w, proc.nbins)
-        iters.append(vegas.iteration_estimate(sw, sw2, N))
+            if strat:
+                np.add.at(S1, h, w)
+                np.add.at(S2, h, w * w)
+                w2m = w * w / alloc[h]
+                d += np.stack([np.bincount(bins[:, k], weights=w2m, minlength=proc.nbins) for k in range(D)])
+            else:
+                sw += np.sum(w)
+                sw2 += np.sum(w * w)
+                d += vegas.training_data(bins, w, proc.nbins)
+        if strat:
+            mean_it, var_it, s2 = stratified.estimate(S1, S2, alloc)
+            iters.append((mean_it, var_it))
+            alloc = stratified.allocate(s2, J, proc.strat_beta)
+        else:
+            iters.append(vegas.iteration_estimate(sw, sw2, N))
         edges = vegas.refine(edges, d, proc.alpha)
     mean, err = vegas.combine([v[0] for v in iters], [v[1] for v in iters])
-    return mean, err, edges, iters
+    return mean, err, edges, iters, (alloc if strat else None)
 
 
 def collision(problem, f, t, state, mode="f64", points=None):
@@ -223,9 +253,11 @@ def collision(problem, f, t, state, mode="f64", points=None):
                 edges = state.maps.get(tid)
                 if edges is None:
                     edges = vegas.uniform_edges(si.dim, nb)
-                mean, err, edges, _ = evaluate_task(problem, k, si, i, term, f, t, edges,
-                                                    state.call, mode, dists, widths[si.process])
+                mean, err, edges, _, alloc = evaluate_task(problem, k, si, i, term, f, t, edges, state.call,
+                                                           mode, dists, widths[si.process], state.strata.get(tid))
                 state.maps[tid] = edges
+                if alloc is not None:
+                    state.strata[tid] = alloc
                 detail[tid] = (mean, err)
                 res.append((mean, err))
                 per_process[si.process][0].append(mean)

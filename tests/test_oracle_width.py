@@ -42,7 +42,7 @@ def test_mc_matches_fractional_smeared_reduction(case):
     dists = col.distributions(prob, f, 0.0)
     si = side_integrals(prob)[0]
     for i in pts:
-        mean, err, _, _ = col.evaluate_task(prob, 0, si, i, term, f, 0.0, vegas.uniform_edges(6, 50), 0, "f64",
+        mean, err, *_ = col.evaluate_task(prob, 0, si, i, term, f, 0.0, vegas.uniform_edges(6, 50), 0, "f64",
                                             dists)
         d = dists[0]
         red = ref.two_body_cm_fractional(q[i], (m, m, m, m), f[0, i], d, d, d, (eta,) * 4, w,
@@ -73,7 +73,7 @@ def test_narrow_fractional_width_approaches_exact_delta():
     f = (0.5 * np.exp(-q / 1.5))[None, :]
     si = side_integrals(prob)[0]
     i = 9
-    mean, err, _, _ = col.evaluate_task(prob, 0, si, i, 1, f, 0.0, vegas.uniform_edges(6, 50), 0)
+    mean, err, *_ = col.evaluate_task(prob, 0, si, i, 1, f, 0.0, vegas.uniform_edges(6, 50), 0)
     cf = ref.loss_massless_mb(q[i], 0.5, 1.5)
     assert abs(mean - cf) < 3.5 * err + 2e-3 * cf
 

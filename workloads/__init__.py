@@ -79,6 +79,12 @@ class Process:
     width_factor: float = 1.25
     width_min: float = 1e-4
     width_max: float = 0.2
+    # Adaptive stratified sampling (VEGAS+): strat = 1 splits the map's unit
+    # cube into at most strat_max_hcubes hypercubes whose sample counts adapt
+    # as sigma_h^strat_beta; tasks then draw 8 floor(N / 8) samples.
+    strat: int = 0
+    strat_beta: float = 0.75
+    strat_max_hcubes: int = 65536
 
 
 @dataclass(frozen=True)
