@@ -67,6 +67,17 @@ typedef struct {
     double mass0, mass1;
 } best_species;
 
+/* Adaptive stratified sampling (strat = 1; the vegas library's default
+ * since 2021, Lepage, J. Comput. Phys. 439 (2021) 110386): a task draws
+ * 8 floor(N/8) samples in items of 8; the map's unit cube is cut into M^D
+ * hypercubes, M the largest integer with 4 M^D <= items and
+ * M^D <= strat_max_hcubes; each hypercube gets m_h >= 1 items (uniform at
+ * first), samples uniform inside it; the estimate is the volume-weighted sum
+ * of the hypercube means; after each iteration
+ * m_h = 1 + floor((J - H) d_h / sum d) with d_h = s_h^strat_beta (s_h the
+ * sample standard deviation in h), leftovers one each to the first
+ * hypercubes.  The allocation persists like the maps and is checkpointed.
+ * The fixed-sample integral of best_collision_vjp / _jvp does not stratify. */
 /* A process n_in -> n_out (Sec. 3A, App. D) with constant |M|^2 = coupling^2.
  * species[0 .. n_in-1] are the initial legs, species[n_in .. n_in+n_out-1]
  * the final legs.  neval is the number of samples per VEGAS iteration per
@@ -95,6 +106,9 @@ typedef struct {
     int32_t pad_;
     double width;          /* initial w (modes 1, 2) */
     double width_rel_lo, width_rel_hi, width_factor, width_min, width_max;   /* mode 2 */
+    int32_t strat;         /* 1: adaptive stratified sampling (see below) */
+    int32_t strat_max_hcubes;   /* 1 .. 2^20 */
+    double strat_beta;     /* >= 0 */
 } best_process;
 
 typedef struct {
@@ -269,6 +283,14 @@ best_status best_load_state(best_ctx* ctx, const void* host_buf, int64_t size);
  */
 best_status best_moments(best_ctx* ctx, const double* f_dev, double t, double* n_dev, double* rho_dev,
                          void* stream);
+
+/*
+ * Stratification of task t (host outputs, each may be NULL): strata per
+ * dimension *M, hypercubes *H (0: the task is not stratified) and, when m is
+ * not NULL and *H > 0, the items per hypercube m[0 .. H) that the next
+ * iteration uses (synchronous).
+ */
+best_status best_get_strata(best_ctx* ctx, int32_t task, int32_t* M, int32_t* H, int32_t* m);
 
 /*
  * Fractional Gaussian widths (App. C), one per process, as used by the next

@@ -31,7 +31,8 @@ internals are not restated here, only the published method):
     d_b = sum over samples in increment b of w^2 / m_h;
   * the next allocation: d_h = (s_h^2)^(beta/2) (beta = 0.75 damps it);
     m_h = 1 + floor((J - H) d_h / sum d), the J - sum m_h items left over go
-    one each to h = 0, 1, ...; if every d_h is 0 the allocation is uniform;
+    one each to h = 0, 1, ...; if every d_h is 0 (or rounding made
+    sum m_h exceed J) the allocation is uniform;
   * map refinement and reallocation both use the same iteration's samples;
     the allocation persists across evaluations like the map.
 """
@@ -89,5 +90,7 @@ def allocate(s2, J, beta):
         return uniform_allocation(J, H)
     m = 1 + np.floor((J - H) * d / tot).astype(np.int64)
     rest = J - int(np.sum(m))
+    if rest < 0:                       # rounding overshoot: start afresh
+        return uniform_allocation(J, H)
     m[:rest] += 1
     return m

@@ -57,6 +57,9 @@ def config_from_problem(problem, precision):
         pr[k].width_factor = float(getattr(p, "width_factor", 1.25))
         pr[k].width_min = float(getattr(p, "width_min", 1e-4))
         pr[k].width_max = float(getattr(p, "width_max", 0.2))
+        pr[k].strat = int(getattr(p, "strat", 0))
+        pr[k].strat_max_hcubes = int(getattr(p, "strat_max_hcubes", 65536))
+        pr[k].strat_beta = float(getattr(p, "strat_beta", 0.75))
     cfg = _lib.best_config()
     cfg.grid.n = int(g.n)
     cfg.grid.log_spaced = 1 if g.log_spaced else 0
@@ -227,6 +230,19 @@ class Collision:
         rho = torch.empty_like(n)
         check(self.lib.best_moments(self.ctx, _ptr(f), float(t), _ptr(n), _ptr(rho), _stream(stream)), self.ctx)
         return n, rho
+
+    def strata(self, task):
+        """(M, H, m): strata per dimension, hypercubes and items per
+        hypercube of a stratified task (H = 0 and m = None otherwise)."""
+        M = ctypes.c_int32(0)
+        H = ctypes.c_int32(0)
+        check(self.lib.best_get_strata(self.ctx, int(task), ctypes.byref(M), ctypes.byref(H), None), self.ctx)
+        if H.value == 0:
+            return M.value, 0, None
+        m = np.zeros(H.value, dtype=np.int32)
+        check(self.lib.best_get_strata(self.ctx, int(task), None, None, m.ctypes.data_as(ctypes.c_void_p)),
+              self.ctx)
+        return M.value, H.value, m
 
     def widths(self):
         """(w, rel): the fractional Gaussian width of every process as the

@@ -26,7 +26,8 @@ class best_process(ctypes.Structure):
                 ("neval_per_point", POINTER(c_int64)), ("nitn", c_int32), ("nbins", c_int32),
                 ("alpha", c_double), ("width_mode", c_int32), ("pad_", c_int32), ("width", c_double),
                 ("width_rel_lo", c_double), ("width_rel_hi", c_double), ("width_factor", c_double),
-                ("width_min", c_double), ("width_max", c_double)]
+                ("width_min", c_double), ("width_max", c_double), ("strat", c_int32),
+                ("strat_max_hcubes", c_int32), ("strat_beta", c_double)]
 
 
 class best_config(ctypes.Structure):
@@ -55,6 +56,7 @@ SIGNATURES = {
     "best_step_implicit_euler": ([c_void_p, c_void_p, c_double, c_double, c_int32, c_double, c_int32, c_int32,
                                   c_double, c_void_p, c_void_p], c_int32),
     "best_moments": ([c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p], c_int32),
+    "best_get_strata": ([c_void_p, c_int32, POINTER(c_int32), POINTER(c_int32), c_void_p], c_int32),
     "best_get_widths": ([c_void_p, c_void_p, c_void_p], c_int32),
     "best_set_widths": ([c_void_p, c_void_p], c_int32),
     "best_state_size": ([c_void_p], c_int64),

@@ -25,14 +25,18 @@ __global__ void moments_kernel(Geometry, const double*, const double*, const Tim
 __global__ void width_control_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskAcc*, const WidthCtl*,
                                      double*, double*);
 __global__ void refine_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskConst*, const int32_t*,
-                              const int32_t*, const Segment*, const double*, double*, TaskAcc*, TaskConst*);
+                              const int32_t*, const Segment*, const double*, double*, TaskAcc*, TaskConst*,
+                              const double*);
+__global__ void strat_init_kernel(const TaskDesc*, int32_t*, uint32_t*, int);
+__global__ void strat_refine_kernel(const TaskDesc*, const int32_t*, const double*, int32_t*, double*, uint32_t*,
+                                    double*);
 __global__ void assemble_kernel(Geometry, const SideDesc*, TaskAcc*, TimeState*, double*, double*, double*);
 __global__ void step_first_kernel(Geometry, double*, const double*, const double*, double*, double*, TimeState*,
                                   double*, int);
 __global__ void heun_correct_kernel(Geometry, double*, const double*, const double*, const double*, double*,
                                     double*, TimeState*);
 // variants.cu
-int eval_variants(bool f32, int nmax, void** fn, int* mb);
+int eval_variants(bool f32, int nmax, void** fn, int* mb, bool strat);
 // vjp.cu
 void* vjp_kernel_ptr(bool f32, int nmax);
 void* jvp_kernel_ptr(bool f32, int nmax);
@@ -152,6 +156,14 @@ struct best_ctx {
     WidthCtl* d_wctl = nullptr;
     std::vector<int> width_mode;
     bool any_adaptive = false;
+    // adaptive stratified sampling (VEGAS+)
+    bool any_strat = false;
+    int64_t strat_total_h = 0, strat_total_items = 0;
+    int32_t* d_strat_m = nullptr;   // items per hypercube, all stratified tasks
+    double* d_strat_d = nullptr;    // allocation weights (scratch)
+    uint32_t* d_item_h = nullptr;   // hypercube of every item
+    double* d_item_rec = nullptr;   // (sum w, sum w^2) per item
+    double* d_strat_est = nullptr;  // [task][4] iteration estimate, variance, underflow flag
     // implicit Euler (best_step_implicit_euler): Krylov basis and work vectors
     double* d_nk = nullptr;
     int nk_m = 0;
@@ -213,7 +225,8 @@ void free_all(best_ctx* c) {
                     c->d_knots, c->d_knots32, c->d_coef64, c->d_coef32, c->d_fgrid, c->d_mass0, c->d_mass1,
                     c->d_partials, c->d_k1, c->d_k2, c->d_fstar, c->d_prev, c->d_dtreq,
                     c->d_gcoef, c->d_vjp_tot, c->d_u, c->d_gtail, c->d_coupling, c->d_dcoef64,
-                    c->d_dcoef32, c->d_dtail, c->d_nk, c->d_width, c->d_width_rel, c->d_wctl};
+                    c->d_dcoef32, c->d_dtail, c->d_nk, c->d_width, c->d_width_rel, c->d_wctl,
+                    c->d_strat_m, c->d_strat_d, c->d_item_h, c->d_item_rec, c->d_strat_est};
     if (c->graph) cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
     for (void* b : bufs) cudaFree(b);
@@ -263,6 +276,11 @@ best_status validate(const best_config* cfg) {
             return fail(ctx, BEST_ERR_INVALID,
                         "process %d: adaptive width needs 0 < width_min <= width <= width_max, width_factor > 1, "
                         "0 <= width_rel_lo < width_rel_hi", p);
+        if (pr.strat != 0 && pr.strat != 1) return fail(ctx, BEST_ERR_INVALID, "process %d: strat must be 0 or 1", p);
+        if (pr.strat && (!(pr.strat_beta >= 0.0) || !std::isfinite(pr.strat_beta) || pr.strat_max_hcubes < 1 ||
+                         pr.strat_max_hcubes > (1 << 20)))
+            return fail(ctx, BEST_ERR_INVALID, "process %d: stratification needs strat_beta >= 0 and "
+                        "1 <= strat_max_hcubes <= 2^20", p);
         if (pr.nitn < 1 || pr.nitn > 1000) return fail(ctx, BEST_ERR_INVALID, "process %d: nitn in [1,1000]", p);
         if (pr.nbins < 2 || pr.nbins > 256) return fail(ctx, BEST_ERR_INVALID, "process %d: nbins in [2,256]", p);
         if (!(pr.alpha >= 0.0)) return fail(ctx, BEST_ERR_INVALID, "process %d: alpha must be >= 0", p);
@@ -271,6 +289,8 @@ best_status validate(const best_config* cfg) {
             // the Philox block index of a task's last sample must fit the 32-bit counter word
             if (N < 2 || N > (int64_t(1) << 31) || N * 3 * (n - 2) > (int64_t(1) << 33))
                 return fail(ctx, BEST_ERR_INVALID, "process %d: need 2 <= neval, neval * dim <= 2^33", p);
+            if (pr.strat && N < 2 * kItem)
+                return fail(ctx, BEST_ERR_INVALID, "process %d: stratified sampling needs neval >= %d", p, 2 * kItem);
         }
     }
     return BEST_OK;
@@ -293,12 +313,15 @@ best_status build_plan(best_ctx* ctx, int it, IterPlan& plan) {
     for (size_t t = 0; t < ctx->tasks.size(); ++t)
         if (ctx->tasks[t].nitn > it) active.push_back(static_cast<int32_t>(t));
     const int A = static_cast<int>(active.size());
-    std::vector<int64_t> groups(A), cost(A), cum(A + 1, 0);
+    // work units: sample groups, or for stratified tasks items of kItem
+    // samples (kItem / G groups), so that a segment holds whole items
+    std::vector<int64_t> groups(A), unit(A), cost(A), cum(A + 1, 0);
     for (int a = 0; a < A; ++a) {
         const TaskDesc& td = ctx->tasks[active[a]];
         const int G = group_size(td.dim, f32);
-        groups[a] = (td.neval + G - 1) / G;
-        cost[a] = static_cast<int64_t>(G) * (td.dim + 6);
+        unit[a] = td.strat_H > 0 ? kItem / G : 1;
+        groups[a] = (td.neval + G - 1) / G / unit[a];
+        cost[a] = static_cast<int64_t>(G) * unit[a] * (td.dim + 6);
         cum[a + 1] = cum[a] + groups[a] * cost[a];
     }
     const int64_t W = cum[A];
@@ -318,8 +341,8 @@ best_status build_plan(best_ctx* ctx, int it, IterPlan& plan) {
             if (g1 <= g0) continue;
             Segment s{};
             s.task = active[a];
-            s.g0 = g0;
-            s.g1 = g1;
+            s.g0 = g0 * unit[a];
+            s.g1 = g1 * unit[a];
             segs.push_back(s);
             seg_active.push_back(a);
         }
@@ -426,6 +449,9 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
         P.coef = f32 ? static_cast<const void*>(ctx->d_coef32) : static_cast<const void*>(ctx->d_coef64);
         P.knots = f32 ? static_cast<const void*>(ctx->d_knots32) : static_cast<const void*>(ctx->d_knots);
         P.partials = ctx->d_partials;
+        P.item_h = ctx->d_item_h;
+        P.strat_m = ctx->d_strat_m;
+        P.item_rec = ctx->d_item_rec;
         P.itn = static_cast<uint32_t>(it);
         P.smem_spline_elems = g.n_species * 4 * (g.n_grid - 1) + g.n_grid;
         const PhiloxKey key = philox_key(g.seed);
@@ -449,9 +475,15 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
             CK(cudaEventRecordWithFlags(ctx->ev[ctx->ev_used + 1], st, rec_flags));
             ctx->ev_used += 2;
         }
+        if (ctx->any_strat) {
+            strat_refine_kernel<<<pl.n_active, 256, 0, st>>>(ctx->d_tasks, pl.d_active, ctx->d_item_rec,
+                                                             ctx->d_strat_m, ctx->d_strat_d, ctx->d_item_h,
+                                                             ctx->d_strat_est);
+            ctx->launches += 1;
+        }
         refine_kernel<<<pl.n_active, 128, ctx->refine_smem, st>>>(
             g, ctx->d_sides, ctx->d_tasks, ctx->d_tconst, pl.d_active, pl.d_task_seg, pl.d_segs,
-            ctx->d_partials, ctx->d_edges, ctx->d_acc, ctx->d_tconst);
+            ctx->d_partials, ctx->d_edges, ctx->d_acc, ctx->d_tconst, ctx->d_strat_est);
         ctx->launches += 2;
     }
     const int total = g.n_species * g.n_grid;
@@ -645,6 +677,23 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
                 td.dim = 3 * (sd.n - 2);
                 td.nbins = pr.nbins;
                 td.alpha = pr.alpha;
+                if (pr.strat) {
+                    // items of kItem samples; M the largest with 4 M^D <= J and M^D <= max hypercubes
+                    const int64_t J = td.neval / kItem;
+                    int64_t M = 1;
+                    auto pw = [](int64_t b, int e) { int64_t r = 1; for (int k = 0; k < e; ++k) r *= b; return r; };
+                    while (4 * pw(M + 1, td.dim) <= J && pw(M + 1, td.dim) <= pr.strat_max_hcubes) ++M;
+                    td.neval = kItem * J;
+                    td.strat_M = static_cast<int32_t>(M);
+                    td.strat_H = static_cast<int32_t>(pw(M, td.dim));
+                    td.strat_J = J;
+                    td.strat_off_h = ctx->strat_total_h;
+                    td.strat_off_item = ctx->strat_total_items;
+                    td.strat_beta = pr.strat_beta;
+                    ctx->strat_total_h += td.strat_H;
+                    ctx->strat_total_items += J;
+                    ctx->any_strat = true;
+                }
                 ctx->tasks.push_back(td);
             }
     }
@@ -655,7 +704,7 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return bail(fail(ctx, BEST_ERR_CUDA, "no CUDA device"));
-    ctx->n_variants = eval_variants(f32, ctx->nmax_legs, ctx->variant_fn, ctx->variant_mb);
+    ctx->n_variants = eval_variants(f32, ctx->nmax_legs, ctx->variant_fn, ctx->variant_mb, ctx->any_strat);
     {
         const size_t rs = f32 ? 4 : 8;
         const size_t spl = static_cast<size_t>(g.n_species) * 4 * (g.n_grid - 1) + g.n_grid;
@@ -785,6 +834,16 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     CKI(cudaMemcpy(ctx->d_knots32, knots32.data(), n * sizeof(float), cudaMemcpyHostToDevice));
     CKI(cudaMemcpy(ctx->d_mass0, m0.data(), S * sizeof(double), cudaMemcpyHostToDevice));
     CKI(cudaMemcpy(ctx->d_mass1, m1.data(), S * sizeof(double), cudaMemcpyHostToDevice));
+    CKI(dalloc(&ctx->d_strat_est, static_cast<size_t>(T) * 4));
+    CKI(cudaMemset(ctx->d_strat_est, 0, sizeof(double) * 4 * T));
+    if (ctx->any_strat) {
+        CKI(dalloc(&ctx->d_strat_m, static_cast<size_t>(ctx->strat_total_h)));
+        CKI(dalloc(&ctx->d_strat_d, static_cast<size_t>(ctx->strat_total_h)));
+        CKI(dalloc(&ctx->d_item_h, static_cast<size_t>(ctx->strat_total_items)));
+        CKI(dalloc(&ctx->d_item_rec, static_cast<size_t>(ctx->strat_total_items) * 2));
+        strat_init_kernel<<<T, 256>>>(ctx->d_tasks, ctx->d_strat_m, ctx->d_item_h, 1);
+        CKI(cudaGetLastError());
+    }
     {
         best_status sv = set_variant(ctx, 0);
         if (sv != BEST_OK) return bail(sv);
@@ -983,7 +1042,7 @@ best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, con
                                                              ctx->d_u);
     CK(cudaMemsetAsync(ctx->d_gcoef, 0, sizeof(double) * g.n_species * (g.n_grid - 1) * 4, st));
     const IterPlan& pl = ctx->plans[0];
-    VjpParams V;
+    VjpParams V{};
     EvalParams& P = V.E;
     P.geo = g;
     P.sides = ctx->d_sides;
@@ -1268,7 +1327,8 @@ int64_t best_state_size(const best_ctx* ctx) {
     if (!ctx) return 0;
     const int64_t T = ctx->geo.n_tasks;
     return static_cast<int64_t>(sizeof(StateHeader)) + 8 * T * ctx->geo.map_stride + 8 * T +
-           static_cast<int64_t>(sizeof(TimeState)) + 16 * static_cast<int64_t>(ctx->n_processes);
+           static_cast<int64_t>(sizeof(TimeState)) + 16 * static_cast<int64_t>(ctx->n_processes) +
+           4 * ctx->strat_total_h;
 }
 
 best_status best_save_state(best_ctx* ctx, void* host_buf, int64_t size) {
@@ -1289,6 +1349,9 @@ best_status best_save_state(best_ctx* ctx, void* host_buf, int64_t size) {
     CK(cudaMemcpy(p, ctx->d_width, ctx->n_processes * sizeof(double), cudaMemcpyDeviceToHost));
     p += ctx->n_processes * sizeof(double);
     CK(cudaMemcpy(p, ctx->d_width_rel, ctx->n_processes * sizeof(double), cudaMemcpyDeviceToHost));
+    p += ctx->n_processes * sizeof(double);
+    if (ctx->strat_total_h > 0)
+        CK(cudaMemcpy(p, ctx->d_strat_m, ctx->strat_total_h * sizeof(int32_t), cudaMemcpyDeviceToHost));
     return BEST_OK;
 }
 
@@ -1313,6 +1376,14 @@ best_status best_load_state(best_ctx* ctx, const void* host_buf, int64_t size) {
     CK(cudaMemcpy(ctx->d_width, p, ctx->n_processes * sizeof(double), cudaMemcpyHostToDevice));
     p += ctx->n_processes * sizeof(double);
     CK(cudaMemcpy(ctx->d_width_rel, p, ctx->n_processes * sizeof(double), cudaMemcpyHostToDevice));
+    p += ctx->n_processes * sizeof(double);
+    if (ctx->strat_total_h > 0) {
+        // the allocation, then the items rebuilt from it
+        CK(cudaMemcpy(ctx->d_strat_m, p, ctx->strat_total_h * sizeof(int32_t), cudaMemcpyHostToDevice));
+        strat_init_kernel<<<ctx->geo.n_tasks, 256>>>(ctx->d_tasks, ctx->d_strat_m, ctx->d_item_h, 0);
+        CK(cudaGetLastError());
+        CK(cudaDeviceSynchronize());
+    }
     return BEST_OK;
 }
 
@@ -1329,6 +1400,19 @@ best_status best_moments(best_ctx* ctx, const double* f_dev, double t, double* n
     moments_kernel<<<g.n_species, 256, 0, st>>>(g, ctx->d_knots, ctx->d_coef64, ctx->d_ts, n_dev, rho_dev);
     ctx->launches = 3;
     CK(cudaGetLastError());
+    return BEST_OK;
+}
+
+best_status best_get_strata(best_ctx* ctx, int32_t task, int32_t* M, int32_t* H, int32_t* m) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    if (task < 0 || task >= ctx->geo.n_tasks) return fail(ctx, BEST_ERR_INVALID, "task out of range");
+    const TaskDesc& td = ctx->tasks[task];
+    if (M) *M = td.strat_M;
+    if (H) *H = td.strat_H;
+    if (m && td.strat_H > 0) {
+        CK(cudaDeviceSynchronize());
+        CK(cudaMemcpy(m, ctx->d_strat_m + td.strat_off_h, td.strat_H * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    }
     return BEST_OK;
 }
 

@@ -142,7 +142,100 @@ __device__ __forceinline__ float tail_f32(float x, float eta) {
     return den > 0.0f ? __fdividef(1.0f, den) : 0.0f;      // MUFU reciprocal (2 ulp)
 }
 
+// Weight of one sample at the mapped point y (r, theta, phi - pi per
+// integrated leg) with map Jacobian jac: momenta, conserved leg, energies,
+// statistical factor, Gaussian and Eq. (12); 0 for a cut sample.
 template <typename R, int NLEG>
+__device__ __forceinline__ R weight_at(const SegConst<R, NLEG>& C, const R* y, R jac, const R* s_spline,
+                                       const R* knots, const Geometry& g, R inv_step, R q0, R lq0_step, R qN,
+                                       int ncoef) {
+    constexpr int NI = NLEG - 2;
+    constexpr bool F32 = RMath<R>::kF32;
+    // integrated legs
+    R px = R(0), py = R(0), pz = C.pobs_sig;
+    R dE = C.sgn_obs_E;
+    R Esum = C.e_obs;                   // E_in + E_out (used when C.frac)
+    R meas = jac;
+    R stat = C.c0;
+    R rinvE_prod = R(1);
+    bool cut = false;
+#pragma unroll
+    for (int j = 0; j < NI; ++j) {
+        const R r = y[3 * j];
+        R st, ct, sp, cp;
+        RMath<R>::sincos_(y[3 * j + 1], &st, &ct);
+        RMath<R>::sincos_(y[3 * j + 2], &sp, &cp);   // angle phi - pi
+        const R p = r * C.inv_a;
+        const R ps = p * st;
+        const R sg = C.sig[j];
+        px = fma(-sg * ps, cp, px);                    // cos(phi) = -cos(phi - pi)
+        py = fma(-sg * ps, sp, py);
+        pz = fma(sg * p, ct, pz);
+        const R E2 = fma(p, p, C.m2[j]);
+        const R rE = RMath<R>::rsqrt_(E2);
+        const R E = E2 * rE;
+        cut |= E < C.e_cut;
+        dE = fma(C.sgnE[j], E, dE);
+        Esum += E;
+        meas *= r * r * st;
+        rinvE_prod *= rE;
+        const SplineView<R> sv{s_spline + C.spc[j] * ncoef, knots};
+        R f = spline_eval<R>(sv, r, g, inv_step, q0, lq0_step);
+        f = C.fd[j] ? (f < R(1) ? f : R(1)) : f;
+        stat *= fma(C.cb[j], f, C.ca[j]);
+    }
+    // conserved leg (Eq. (10), App. A)
+    const R pc2 = fma(px, px, fma(py, py, pz * pz));
+    const R Ec2 = pc2 + C.m2c;
+    const R rEc = RMath<R>::rsqrt_(Ec2 > R(0) ? Ec2 : R(1e-30));
+    const R Ec = Ec2 * rEc;
+    cut |= Ec < C.e_cut;
+    dE = fma(C.sgn_cons, Ec, dE);
+    R fc;
+    {
+        const R qc = pc2 * (pc2 > R(0) ? RMath<R>::rsqrt_(pc2) : R(0)) * C.a;
+        const bool below = qc < q0, above = qc > qN;
+        if constexpr (F32) {
+            // spline and tail for every lane, then a select: the warp
+            // never diverges on the conserved leg
+            const SplineView<R> sv{s_spline + C.sp_cons * ncoef, knots};
+            fc = spline_eval<R>(sv, fminf(fmaxf(qc, q0), qN), g, inv_step, q0, lq0_step);
+            {
+                const float x = below ? fmaf(C.tlo_b, Ec, C.tlo_a) : fmaf(C.thi_b, Ec, C.thi_a);
+                const float ft = tail_f32(x, C.eta_c);
+                fc = (below || above) ? ft : fc;
+            }
+        } else {
+            if (!below && !above) {
+                const SplineView<R> sv{s_spline + C.sp_cons * ncoef, knots};
+                fc = spline_eval<R>(sv, qc, g, inv_step, q0, lq0_step);
+            } else {
+                const R x = below ? C.tlo_a + C.tlo_b * Ec : C.thi_a + C.thi_b * Ec;
+                const R den = C.eta_c == R(1) ? RMath<R>::expm1_(x) : RMath<R>::exp_(x) - C.eta_c;
+                fc = den > R(0) ? R(1) / den : R(0);
+            }
+        }
+        fc = C.fd_c ? (fc < R(1) ? fc : R(1)) : fc;
+    }
+    stat *= fma(C.cbc, fc, C.cac);
+    R gauss;
+    if (C.frac) {
+        // sigma = w S / 2 with S = E_in + E_out: exponent
+        // -2 dE^2 / (w S)^2, normalisation sigma_ref / sigma = 2 E_obs / S
+        Esum += Ec;
+        const R iS = RMath<R>::rcp_(Esum);
+        const R x = dE * iS;
+        gauss = RMath<R>::exp2_(C.gauss_k * x * x) * (R(2) * C.e_obs * iS);
+    } else {
+        gauss = RMath<R>::exp2_(C.gauss_k * dE * dE);
+    }
+    const R w = stat * meas * rinvE_prod * rEc * gauss;
+    return cut ? R(0) : w;
+}
+
+// STRAT: the instantiation also handles stratified tasks (kept apart so that
+// the plain kernel's register allocation is not affected).
+template <typename R, int NLEG, bool STRAT>
 __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& seg,
                                             const SideDesc& sd, const TaskDesc& td,
                                             const TaskConst& tc, R* s_spline,
@@ -254,6 +347,7 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
     const int64_t N = td.neval;
     const uint32_t task = static_cast<uint32_t>(seg.task);
     const int32_t g1 = static_cast<int32_t>(seg.g1);
+    if (!STRAT || td.strat_H == 0)
     for (int32_t grp = static_cast<int32_t>(seg.g0) + tid; grp < g1; grp += blockDim.x) {
         // FP32: raw words; FP64: 52-bit uniforms
         uint32_t uw[F32 ? SS::kUniforms : 1];
@@ -290,86 +384,8 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
                 jac *= e.dy;
                 bin[d] = b;
             }
-            // integrated legs
-            R px = R(0), py = R(0), pz = C.pobs_sig;
-            R dE = C.sgn_obs_E;
-            R Esum = C.e_obs;                   // E_in + E_out (used when C.frac)
-            R meas = jac;
-            R stat = C.c0;
-            R rinvE_prod = R(1);
-            bool cut = false;
-#pragma unroll
-            for (int j = 0; j < NI; ++j) {
-                const R r = y[3 * j];
-                R st, ct, sp, cp;
-                RMath<R>::sincos_(y[3 * j + 1], &st, &ct);
-                RMath<R>::sincos_(y[3 * j + 2], &sp, &cp);   // angle phi - pi
-                const R p = r * C.inv_a;
-                const R ps = p * st;
-                const R sg = C.sig[j];
-                px = fma(-sg * ps, cp, px);                    // cos(phi) = -cos(phi - pi)
-                py = fma(-sg * ps, sp, py);
-                pz = fma(sg * p, ct, pz);
-                const R E2 = fma(p, p, C.m2[j]);
-                const R rE = RMath<R>::rsqrt_(E2);
-                const R E = E2 * rE;
-                cut |= E < C.e_cut;
-                dE = fma(C.sgnE[j], E, dE);
-                Esum += E;
-                meas *= r * r * st;
-                rinvE_prod *= rE;
-                const SplineView<R> sv{s_spline + C.spc[j] * ncoef, knots};
-                R f = spline_eval<R>(sv, r, g, inv_step, q0, lq0_step);
-                f = C.fd[j] ? (f < R(1) ? f : R(1)) : f;
-                stat *= fma(C.cb[j], f, C.ca[j]);
-            }
-            // conserved leg (Eq. (10), App. A)
-            const R pc2 = fma(px, px, fma(py, py, pz * pz));
-            const R Ec2 = pc2 + C.m2c;
-            const R rEc = RMath<R>::rsqrt_(Ec2 > R(0) ? Ec2 : R(1e-30));
-            const R Ec = Ec2 * rEc;
-            cut |= Ec < C.e_cut;
-            dE = fma(C.sgn_cons, Ec, dE);
-            R fc;
-            {
-                const R qc = pc2 * (pc2 > R(0) ? RMath<R>::rsqrt_(pc2) : R(0)) * C.a;
-                const bool below = qc < q0, above = qc > qN;
-                if constexpr (F32) {
-                    // spline and tail for every lane, then a select: the warp
-                    // never diverges on the conserved leg
-                    const SplineView<R> sv{s_spline + C.sp_cons * ncoef, knots};
-                    fc = spline_eval<R>(sv, fminf(fmaxf(qc, q0), qN), g, inv_step, q0, lq0_step);
-                    {
-                        const float x = below ? fmaf(C.tlo_b, Ec, C.tlo_a) : fmaf(C.thi_b, Ec, C.thi_a);
-                        const float ft = tail_f32(x, C.eta_c);
-                        fc = (below || above) ? ft : fc;
-                    }
-                } else {
-                    if (!below && !above) {
-                        const SplineView<R> sv{s_spline + C.sp_cons * ncoef, knots};
-                        fc = spline_eval<R>(sv, qc, g, inv_step, q0, lq0_step);
-                    } else {
-                        const R x = below ? C.tlo_a + C.tlo_b * Ec : C.thi_a + C.thi_b * Ec;
-                        const R den = C.eta_c == R(1) ? RMath<R>::expm1_(x) : RMath<R>::exp_(x) - C.eta_c;
-                        fc = den > R(0) ? R(1) / den : R(0);
-                    }
-                }
-                fc = C.fd_c ? (fc < R(1) ? fc : R(1)) : fc;
-            }
-            stat *= fma(C.cbc, fc, C.cac);
-            R gauss;
-            if (C.frac) {
-                // sigma = w S / 2 with S = E_in + E_out: exponent
-                // -2 dE^2 / (w S)^2, normalisation sigma_ref / sigma = 2 E_obs / S
-                Esum += Ec;
-                const R iS = RMath<R>::rcp_(Esum);
-                const R x = dE * iS;
-                gauss = RMath<R>::exp2_(C.gauss_k * x * x) * (R(2) * C.e_obs * iS);
-            } else {
-                gauss = RMath<R>::exp2_(C.gauss_k * dE * dE);
-            }
-            R w = stat * meas * rinvE_prod * rEc * gauss;
-            w = (cut || !valid) ? R(0) : w;
+            R w = weight_at<R, NLEG>(C, y, jac, s_spline, knots, g, inv_step, q0, lq0_step, qN, ncoef);
+            w = valid ? w : R(0);
             const R w2 = w * w;
             acc_w.add(w);
             acc_w2.add(w2);
@@ -379,6 +395,81 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
 #pragma unroll
                 for (int d = 0; d < D; ++d) atomicAdd(&w_hist[d * nb + bin[d]], w2);
             }
+        }
+    }
+    else if constexpr (STRAT) {
+        // Adaptive stratified sampling: one thread per item of kItem samples,
+        // all in hypercube h = item_h[item] with strata (i_0 .. i_{D-1});
+        // x_d = (i_d + u_d) / M.  The item's (sum w, sum w^2) go to its own
+        // record (summed per hypercube in a fixed order afterwards); the
+        // training data weigh w^2 by 1 / m_h.
+        constexpr int GPI = kItem / G;                  // groups per item
+        const int M = td.strat_M;
+        const R invM = R(1) / static_cast<R>(M);
+        const uint32_t* ih = P.item_h + td.strat_off_item;
+        const int32_t* sm = P.strat_m + td.strat_off_h;
+        double2* rec = reinterpret_cast<double2*>(P.item_rec) + td.strat_off_item;
+        const int32_t it1 = g1 / GPI;
+        for (int32_t item = static_cast<int32_t>(seg.g0) / GPI + tid; item < it1; item += blockDim.x) {
+            const uint32_t h = ih[item];
+            const R inv_m = R(1) / static_cast<R>(sm[h]);
+            R xi[D];                                     // i_d as R
+            {
+                uint32_t r = h;
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    const uint32_t q = r / static_cast<uint32_t>(M);
+                    xi[d] = static_cast<R>(r - q * static_cast<uint32_t>(M));
+                    r = q;
+                }
+            }
+            R s1 = R(0), s2 = R(0);
+#pragma unroll 1
+            for (int gi = 0; gi < GPI; ++gi) {
+                const int32_t grp = item * GPI + gi;
+                uint32_t uw[F32 ? SS::kUniforms : 1];
+                R u[F32 ? 1 : SS::kUniforms];
+                if constexpr (F32) group_words<D>(uw, grp, P.itn, ts.call, task, P.rk);
+                else group_uniforms<D, F32, R>(u, grp, P.itn, ts.call, task, P.rk);
+#pragma unroll
+                for (int sgi = 0; sgi < G; ++sgi) {
+                    R y[D];
+                    int bin[D];
+                    R jac = R(1);
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        R x;
+                        if constexpr (F32) {
+                            const float uf = static_cast<float>(((uw[sgi * D + d] >> 9) << 1) | 1u) *
+                                             5.9604644775390625e-08f;          // (2k + 1) 2^-24
+                            x = fmaf(uf, invM, xi[d] * invM);
+                        } else {
+                            x = (xi[d] + u[sgi * D + d]) / static_cast<R>(M);
+                        }
+                        const R t = x * nbR;
+                        int b = static_cast<int>(t);
+                        b = b < nb - 1 ? b : nb - 1;
+                        const R fr = t - static_cast<R>(b);
+                        const Real2<R> e = s_map[d * nb + b];
+                        y[d] = fma(e.dy, fr, e.y0);
+                        jac *= e.dy;
+                        bin[d] = b;
+                    }
+                    const R w = weight_at<R, NLEG>(C, y, jac, s_spline, knots, g, inv_step, q0, lq0_step, qN,
+                                                   ncoef);
+                    const R w2 = w * w;
+                    s1 += w;
+                    s2 += w2;
+                    acc_w.add(w);
+                    acc_w2.add(w2);
+                    if (w2 != R(0)) {
+                        const R w2m = w2 * inv_m;
+#pragma unroll
+                        for (int d = 0; d < D; ++d) atomicAdd(&w_hist[d * nb + bin[d]], w2m);
+                    }
+                }
+            }
+            rec[item] = make_double2(static_cast<double>(s1), static_cast<double>(s2));
         }
     }
 
@@ -415,7 +506,7 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
 
 // MB: CTAs per SM the kernel is register-limited to (__launch_bounds__);
 // several values are instantiated and the autotuner picks one at run time.
-template <typename R, int NMAX, int MB>
+template <typename R, int NMAX, int MB, bool STRAT = false>
 __global__ void __launch_bounds__(kThreads, MB)
 eval_kernel(EvalParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -442,10 +533,10 @@ eval_kernel(EvalParams P) {
         const TaskConst tc = P.tconst[seg.task];
         __syncthreads();
         switch (sd.n) {
-            case 3: if constexpr (NMAX >= 3) run_segment<R, 3>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red); break;
-            case 4: if constexpr (NMAX >= 4) run_segment<R, 4>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red); break;
-            case 5: if constexpr (NMAX >= 5) run_segment<R, 5>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red); break;
-            case 6: if constexpr (NMAX >= 6) run_segment<R, 6>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red); break;
+            case 3: if constexpr (NMAX >= 3) run_segment<R, 3, STRAT>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red); break;
+            case 4: if constexpr (NMAX >= 4) run_segment<R, 4, STRAT>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red); break;
+            case 5: if constexpr (NMAX >= 5) run_segment<R, 5, STRAT>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red); break;
+            case 6: if constexpr (NMAX >= 6) run_segment<R, 6, STRAT>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red); break;
             default: break;
         }
     }

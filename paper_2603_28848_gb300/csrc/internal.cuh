@@ -11,6 +11,7 @@ namespace best {
 constexpr int kMaxLegs = BEST_MAX_LEGS;
 constexpr int kMaxDim = 3 * (BEST_MAX_LEGS - 2);
 constexpr int kThreads = 256;          // threads per CTA of the sample kernel
+constexpr int kItem = 8;               // samples per item of stratified sampling (a multiple of every group size)
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTwoPi = 6.28318530717958647692;
 
@@ -47,6 +48,13 @@ struct TaskDesc {
     int32_t dim;
     int32_t nbins;
     double alpha;
+    // adaptive stratified sampling (VEGAS+); strat_H == 0: off
+    int32_t strat_M;        // strata per dimension
+    int32_t strat_H;        // hypercubes M^D
+    int64_t strat_J;        // items of kItem samples (neval = kItem * strat_J)
+    int64_t strat_off_h;    // offset of the task's hypercube arrays
+    int64_t strat_off_item; // offset of the task's item arrays
+    double strat_beta;      // damping exponent of the allocation
 };
 
 // Per-task values recomputed at the start of every sweep (FP64).
@@ -139,6 +147,9 @@ struct EvalParams {
     const void* coef;           // [species][n-1][4] in R
     const void* knots;          // [n] in R
     double* partials;
+    const uint32_t* item_h;     // stratified: hypercube of every item
+    const int32_t* strat_m;     // stratified: items per hypercube
+    double* item_rec;           // stratified: (sum w, sum w^2) per item
     uint32_t itn;
     int32_t smem_spline_elems;  // R elements of spline coefficients + knots
     uint32_t rk[20];            // Philox round keys (kernel parameters: read from the constant bank)

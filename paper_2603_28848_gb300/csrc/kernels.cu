@@ -251,6 +251,165 @@ __global__ void prepare_kernel(Geometry g, const SideDesc* __restrict__ sides,
 }
 
 // ---------------------------------------------------------------------------
+// Adaptive stratified sampling (VEGAS+): per-task hypercube allocation m_h
+// (items of kItem samples, at least one per hypercube) and the hypercube of
+// every item, items in hypercube order.  One CTA of 256 threads per task.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Exclusive prefix of v over the CTA (v of thread k at position k), with the
+// CTA total in *total; s: 256 int64 of shared memory.
+__device__ int64_t cta_exclusive_scan(int64_t v, int64_t* s, int64_t* total) {
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < static_cast<int>(blockDim.x); o <<= 1) {
+        const int64_t a = static_cast<int>(threadIdx.x) >= o ? s[threadIdx.x - o] : 0;
+        __syncthreads();
+        s[threadIdx.x] += a;
+        __syncthreads();
+    }
+    const int64_t incl = s[threadIdx.x];
+    *total = s[blockDim.x - 1];
+    __syncthreads();
+    return incl - v;
+}
+
+__device__ void strat_write_items(const int32_t* m, int H, int64_t J, uint32_t* item_h, int64_t* s) {
+    int64_t base = 0;
+    for (int c0 = 0; c0 < H; c0 += blockDim.x) {
+        const int h = c0 + static_cast<int>(threadIdx.x);
+        const int64_t v = h < H ? m[h] : 0;
+        int64_t tot;
+        const int64_t ex = base + cta_exclusive_scan(v, s, &tot);
+        for (int64_t k = 0; k < v && ex + k < J; ++k) item_h[ex + k] = static_cast<uint32_t>(h);
+        base += tot;
+    }
+}
+
+__device__ void uniform_allocation(int32_t* m, int H, int64_t J) {
+    for (int h = threadIdx.x; h < H; h += blockDim.x)
+        m[h] = static_cast<int32_t>(J / H + (h < J % H ? 1 : 0));
+}
+
+}  // namespace
+
+// uniform != 0: first (uniform) allocation; otherwise only the items are
+// rebuilt from the stored allocation (after a state load).
+__global__ void strat_init_kernel(const TaskDesc* __restrict__ tasks, int32_t* strat_m, uint32_t* item_h,
+                                  int uniform) {
+    __shared__ int64_t s[256];
+    const TaskDesc td = tasks[blockIdx.x];
+    if (td.strat_H == 0) return;
+    int32_t* m = strat_m + td.strat_off_h;
+    if (uniform) {
+        uniform_allocation(m, td.strat_H, td.strat_J);
+        __syncthreads();
+    }
+    strat_write_items(m, td.strat_H, td.strat_J, item_h + td.strat_off_item, s);
+}
+
+// After the sample kernel of an iteration, one CTA per active task: per
+// hypercube S1 = sum w, S2 = sum w^2 from its items (in item order), the
+// iteration estimate I = (1/H) sum_h S1_h / n_h and variance
+// (1/H^2) sum_h s_h^2 / n_h (n_h = kItem m_h), written to est[4 t ..] with an
+// underflow flag (S2 < S1^2 / n violated: FP32 squares underflowed); then the
+// next allocation m_h = 1 + floor((J - H) d_h / sum d), d_h = (s_h^2)^(beta/2),
+// the remaining items one each to h = 0, 1, ... (uniform if every d_h = 0),
+// and the items rebuilt.  An underflowed iteration keeps its allocation.
+__global__ void strat_refine_kernel(const TaskDesc* __restrict__ tasks, const int32_t* __restrict__ active,
+                                    const double* __restrict__ item_rec, int32_t* strat_m, double* strat_d,
+                                    uint32_t* item_h, double* est) {
+    __shared__ int64_t s[256];
+    __shared__ double r0[256], r1[256], r2[256];
+    __shared__ int64_t si[256];
+    const int t = active[blockIdx.x];
+    const TaskDesc td = tasks[t];
+    if (td.strat_H == 0) return;
+    const int H = td.strat_H;
+    const int64_t J = td.strat_J;
+    int32_t* m = strat_m + td.strat_off_h;
+    double* dd = strat_d + td.strat_off_h;
+    const double2* rec = reinterpret_cast<const double2*>(item_rec) + td.strat_off_item;
+    double a_mean = 0.0, a_var = 0.0, a_d = 0.0;
+    int64_t bad = 0;
+    int64_t base = 0;
+    for (int c0 = 0; c0 < H; c0 += blockDim.x) {
+        const int h = c0 + static_cast<int>(threadIdx.x);
+        const int64_t v = h < H ? m[h] : 0;
+        int64_t tot;
+        const int64_t ex = base + cta_exclusive_scan(v, s, &tot);
+        if (h < H) {
+            double S1 = 0.0, S2 = 0.0;
+            for (int64_t k = 0; k < v; ++k) {
+                const double2 r = rec[ex + k];
+                S1 += r.x;
+                S2 += r.y;
+            }
+            const double n = static_cast<double>(kItem) * static_cast<double>(v);
+            const double q = S1 * S1 / n;
+            double s2 = (S2 - q) / (n - 1.0);
+            s2 = s2 > 0.0 ? s2 : 0.0;
+            if (S2 < (1.0 - 1e-6) * q) bad = 1;
+            a_mean += S1 / n;
+            a_var += s2 / n;
+            const double d = pow(s2, 0.5 * td.strat_beta);
+            dd[h] = d;
+            a_d += d;
+        }
+        base += tot;
+    }
+    r0[threadIdx.x] = a_mean;
+    r1[threadIdx.x] = a_var;
+    r2[threadIdx.x] = a_d;
+    si[threadIdx.x] = bad;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (static_cast<int>(threadIdx.x) < o) {
+            r0[threadIdx.x] += r0[threadIdx.x + o];
+            r1[threadIdx.x] += r1[threadIdx.x + o];
+            r2[threadIdx.x] += r2[threadIdx.x + o];
+            si[threadIdx.x] |= si[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    const double sum_d = r2[0];
+    const bool underflow = si[0] != 0;
+    if (threadIdx.x == 0) {
+        est[4 * t] = r0[0] / H;
+        est[4 * t + 1] = r1[0] / (static_cast<double>(H) * H);
+        est[4 * t + 2] = underflow ? 1.0 : 0.0;
+    }
+    if (underflow) return;
+    __syncthreads();
+    if (sum_d > 0.0) {
+        int64_t cnt = 0;
+        for (int h = threadIdx.x; h < H; h += blockDim.x) {
+            const int32_t v = 1 + static_cast<int32_t>(floor(static_cast<double>(J - H) * dd[h] / sum_d));
+            m[h] = v;
+            cnt += v;
+        }
+        si[threadIdx.x] = cnt;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (static_cast<int>(threadIdx.x) < o) si[threadIdx.x] += si[threadIdx.x + o];
+            __syncthreads();
+        }
+        const int64_t rest = J - si[0];
+        __syncthreads();
+        if (rest >= 0) {
+            for (int h = threadIdx.x; h < H; h += blockDim.x)
+                if (h < rest) m[h] += 1;
+        } else {
+            uniform_allocation(m, H, J);      // rounding overshoot (never seen): start afresh
+        }
+    } else {
+        uniform_allocation(m, H, J);
+    }
+    __syncthreads();
+    strat_write_items(m, H, J, item_h + td.strat_off_item, s);
+}
+
+// ---------------------------------------------------------------------------
 // End of one VEGAS iteration, one CTA per active task: sum the task's
 // segment records in a fixed order (deterministic), form the iteration
 // estimate and its variance, add them to the combination accumulators, and
@@ -266,7 +425,8 @@ __global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
                               const TaskDesc* __restrict__ tasks, const TaskConst* tconst,
                               const int32_t* __restrict__ active, const int32_t* __restrict__ task_seg,
                               const Segment* __restrict__ segs, const double* __restrict__ partials,
-                              double* edges, TaskAcc* acc, TaskConst* tconst_next) {
+                              double* edges, TaskAcc* acc, TaskConst* tconst_next,
+                              const double* __restrict__ strat_est) {
     extern __shared__ double hist[];
     const int t = active[blockIdx.x];
     const TaskDesc td = tasks[t];
@@ -285,12 +445,21 @@ __global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
     // iteration is discarded (no estimate, no refinement) and only the scale
     // is corrected for the next iteration.
     const double N = static_cast<double>(td.neval);
-    const double mean_n = hist[0] / N;
-    const bool underflow = hist[1] / N < (1.0 - 1e-6) * mean_n * mean_n;
+    double mean_n, var_n;
+    bool underflow;
+    if (td.strat_H > 0) {
+        // stratified: estimate, variance and underflow flag from strat_refine_kernel
+        mean_n = strat_est[4 * t];
+        var_n = strat_est[4 * t + 1];
+        underflow = strat_est[4 * t + 2] != 0.0;
+    } else {
+        mean_n = hist[0] / N;
+        underflow = hist[1] / N < (1.0 - 1e-6) * mean_n * mean_n;
+        var_n = N > 1.0 ? (hist[1] / N - mean_n * mean_n) / (N - 1.0) : 0.0;
+        var_n = var_n > 0.0 ? var_n : 0.0;
+    }
     if (threadIdx.x == 0) {
         const TaskConst c = tconst[t];
-        double var_n = N > 1.0 ? (hist[1] / N - mean_n * mean_n) / (N - 1.0) : 0.0;
-        var_n = var_n > 0.0 ? var_n : 0.0;
         const double sc = c.K * c.scale;
         const double mean = mean_n * sc;
         const double var = var_n * sc * sc;

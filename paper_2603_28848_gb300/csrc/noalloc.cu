@@ -154,6 +154,8 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     TaskDesc td;
     if (task < 0 || !describe_task(cfg, task, &sd, &td)) return report(BEST_ERR_INVALID, "noalloc: task out of range");
     if (td.nbins > kMaxBins) return report(BEST_ERR_INVALID, "noalloc: nbins exceeds 64");
+    if (cfg->processes[sd.process].strat)
+        return report(BEST_ERR_INVALID, "noalloc: stratified sampling is not supported here");
     const bool f32 = cfg->precision == BEST_FP32;
 
     // Set-up once per device: the device address of the scratch array.
@@ -267,6 +269,9 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     P.coef = f32 ? static_cast<const void*>(coef32) : static_cast<const void*>(coef64);
     P.knots = f32 ? static_cast<const void*>(knots32) : static_cast<const void*>(knots);
     P.partials = reinterpret_cast<double*>(base + kOffPart);
+    P.item_h = nullptr;                 // no stratified sampling here (rejected above)
+    P.strat_m = nullptr;
+    P.item_rec = nullptr;
     P.itn = iteration;
     P.smem_spline_elems = static_cast<int32_t>(spl);
     const PhiloxKey key = philox_key(g.seed);
