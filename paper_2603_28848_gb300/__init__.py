@@ -58,7 +58,7 @@ def config_from_problem(problem, precision):
         pr[k].width_min = float(getattr(p, "width_min", 1e-4))
         pr[k].width_max = float(getattr(p, "width_max", 0.2))
         pr[k].strat = int(getattr(p, "strat", 0))
-        pr[k].strat_max_hcubes = int(getattr(p, "strat_max_hcubes", 65536))
+        pr[k].strat_max_hcubes = int(getattr(p, "strat_max_hcubes", 64))
         pr[k].strat_beta = float(getattr(p, "strat_beta", 0.75))
     cfg = _lib.best_config()
     cfg.grid.n = int(g.n)

@@ -28,8 +28,8 @@ __global__ void refine_kernel(Geometry, const SideDesc*, const TaskDesc*, const 
                               const int32_t*, const Segment*, const double*, double*, TaskAcc*, TaskConst*,
                               const double*);
 __global__ void strat_init_kernel(const TaskDesc*, int32_t*, uint32_t*, int);
-__global__ void strat_refine_kernel(const TaskDesc*, const int32_t*, const double*, int32_t*, double*, uint32_t*,
-                                    double*);
+__global__ void strat_refine_kernel(const TaskDesc*, const int32_t*, const double*, int32_t*, double*, double*,
+                                    uint32_t*, double*);
 __global__ void assemble_kernel(Geometry, const SideDesc*, TaskAcc*, TimeState*, double*, double*, double*);
 __global__ void step_first_kernel(Geometry, double*, const double*, const double*, double*, double*, TimeState*,
                                   double*, int);
@@ -160,7 +160,8 @@ struct best_ctx {
     bool any_strat = false;
     int64_t strat_total_h = 0, strat_total_items = 0;
     int32_t* d_strat_m = nullptr;   // items per hypercube, all stratified tasks
-    double* d_strat_d = nullptr;    // allocation weights (scratch)
+    double* d_strat_d = nullptr;    // per-hypercube sum w, then allocation weights (scratch)
+    double* d_strat_s2 = nullptr;   // per-hypercube sum w^2 (scratch)
     uint32_t* d_item_h = nullptr;   // hypercube of every item
     double* d_item_rec = nullptr;   // (sum w, sum w^2) per item
     double* d_strat_est = nullptr;  // [task][4] iteration estimate, variance, underflow flag
@@ -226,7 +227,7 @@ void free_all(best_ctx* c) {
                     c->d_partials, c->d_k1, c->d_k2, c->d_fstar, c->d_prev, c->d_dtreq,
                     c->d_gcoef, c->d_vjp_tot, c->d_u, c->d_gtail, c->d_coupling, c->d_dcoef64,
                     c->d_dcoef32, c->d_dtail, c->d_nk, c->d_width, c->d_width_rel, c->d_wctl,
-                    c->d_strat_m, c->d_strat_d, c->d_item_h, c->d_item_rec, c->d_strat_est};
+                    c->d_strat_m, c->d_strat_d, c->d_strat_s2, c->d_item_h, c->d_item_rec, c->d_strat_est};
     if (c->graph) cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
     for (void* b : bufs) cudaFree(b);
@@ -477,8 +478,8 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
         }
         if (ctx->any_strat) {
             strat_refine_kernel<<<pl.n_active, 256, 0, st>>>(ctx->d_tasks, pl.d_active, ctx->d_item_rec,
-                                                             ctx->d_strat_m, ctx->d_strat_d, ctx->d_item_h,
-                                                             ctx->d_strat_est);
+                                                             ctx->d_strat_m, ctx->d_strat_d, ctx->d_strat_s2,
+                                                             ctx->d_item_h, ctx->d_strat_est);
             ctx->launches += 1;
         }
         refine_kernel<<<pl.n_active, 128, ctx->refine_smem, st>>>(
@@ -839,6 +840,7 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     if (ctx->any_strat) {
         CKI(dalloc(&ctx->d_strat_m, static_cast<size_t>(ctx->strat_total_h)));
         CKI(dalloc(&ctx->d_strat_d, static_cast<size_t>(ctx->strat_total_h)));
+        CKI(dalloc(&ctx->d_strat_s2, static_cast<size_t>(ctx->strat_total_h)));
         CKI(dalloc(&ctx->d_item_h, static_cast<size_t>(ctx->strat_total_items)));
         CKI(dalloc(&ctx->d_item_rec, static_cast<size_t>(ctx->strat_total_items) * 2));
         strat_init_kernel<<<T, 256>>>(ctx->d_tasks, ctx->d_strat_m, ctx->d_item_h, 1);

@@ -275,6 +275,17 @@ __device__ int64_t cta_exclusive_scan(int64_t v, int64_t* s, int64_t* total) {
 }
 
 __device__ void strat_write_items(const int32_t* m, int H, int64_t J, uint32_t* item_h, int64_t* s) {
+    if (H < static_cast<int>(blockDim.x)) {
+        // few (large) hypercubes: every thread fills each hypercube's range
+        int64_t base = 0;
+        for (int h = 0; h < H; ++h) {
+            const int64_t v = m[h];
+            for (int64_t k = threadIdx.x; k < v && base + k < J; k += blockDim.x)
+                item_h[base + k] = static_cast<uint32_t>(h);
+            base += v;
+        }
+        return;
+    }
     int64_t base = 0;
     for (int c0 = 0; c0 < H; c0 += blockDim.x) {
         const int h = c0 + static_cast<int>(threadIdx.x);
@@ -309,71 +320,120 @@ __global__ void strat_init_kernel(const TaskDesc* __restrict__ tasks, int32_t* s
 }
 
 // After the sample kernel of an iteration, one CTA per active task: per
-// hypercube S1 = sum w, S2 = sum w^2 from its items (in item order), the
+// hypercube S1 = sum w, S2 = sum w^2 from its items (fixed order), the
 // iteration estimate I = (1/H) sum_h S1_h / n_h and variance
 // (1/H^2) sum_h s_h^2 / n_h (n_h = kItem m_h), written to est[4 t ..] with an
-// underflow flag (S2 < S1^2 / n violated: FP32 squares underflowed); then the
+// underflow flag (S2 < S1^2 / n violated, i.e. FP32 squares underflowed, in
+// hypercubes holding more than 1e-6 of sum_h |S1_h| / n_h); then the
 // next allocation m_h = 1 + floor((J - H) d_h / sum d), d_h = (s_h^2)^(beta/2),
 // the remaining items one each to h = 0, 1, ... (uniform if every d_h = 0),
 // and the items rebuilt.  An underflowed iteration keeps its allocation.
 __global__ void strat_refine_kernel(const TaskDesc* __restrict__ tasks, const int32_t* __restrict__ active,
                                     const double* __restrict__ item_rec, int32_t* strat_m, double* strat_d,
-                                    uint32_t* item_h, double* est) {
+                                    double* strat_s2, uint32_t* item_h, double* est) {
     __shared__ int64_t s[256];
-    __shared__ double r0[256], r1[256], r2[256];
+    __shared__ double r0[256], r1[256], r2[256], r3[256], r4[256];
     __shared__ int64_t si[256];
+    __shared__ int32_t b_h[2][256];          // boundary runs of each thread's item chunk: first, last
+    __shared__ double b_1[2][256], b_2[2][256];
     const int t = active[blockIdx.x];
     const TaskDesc td = tasks[t];
     if (td.strat_H == 0) return;
     const int H = td.strat_H;
     const int64_t J = td.strat_J;
     int32_t* m = strat_m + td.strat_off_h;
-    double* dd = strat_d + td.strat_off_h;
+    double* S1h = strat_d + td.strat_off_h;      // sum w per hypercube, then d_h
+    double* S2h = strat_s2 + td.strat_off_h;
+    const uint32_t* ih = item_h + td.strat_off_item;
     const double2* rec = reinterpret_cast<const double2*>(item_rec) + td.strat_off_item;
-    double a_mean = 0.0, a_var = 0.0, a_d = 0.0;
-    int64_t bad = 0;
-    int64_t base = 0;
-    for (int c0 = 0; c0 < H; c0 += blockDim.x) {
-        const int h = c0 + static_cast<int>(threadIdx.x);
-        const int64_t v = h < H ? m[h] : 0;
-        int64_t tot;
-        const int64_t ex = base + cta_exclusive_scan(v, s, &tot);
-        if (h < H) {
-            double S1 = 0.0, S2 = 0.0;
-            for (int64_t k = 0; k < v; ++k) {
-                const double2 r = rec[ex + k];
-                S1 += r.x;
-                S2 += r.y;
+    // per-hypercube sums: each thread scans a contiguous chunk of items
+    // (items of a hypercube are contiguous); runs inside a chunk are whole
+    // hypercubes and are stored directly, the chunk's first and last runs
+    // are added afterwards by one thread in chunk order (deterministic)
+    for (int h = threadIdx.x; h < H; h += blockDim.x) {
+        S1h[h] = 0.0;
+        S2h[h] = 0.0;
+    }
+    __syncthreads();
+    {
+        const int64_t ch = (J + blockDim.x - 1) / blockDim.x;
+        const int64_t i0 = static_cast<int64_t>(threadIdx.x) * ch;
+        const int64_t i1 = i0 + ch < J ? i0 + ch : J;
+        int32_t cur = -1;
+        double s1 = 0.0, s2 = 0.0;
+        b_h[0][threadIdx.x] = -1;
+        b_h[1][threadIdx.x] = -1;
+        for (int64_t i = i0; i < i1; ++i) {
+            const int32_t h = static_cast<int32_t>(ih[i]);
+            if (h != cur) {
+                if (cur >= 0) {
+                    if (b_h[0][threadIdx.x] < 0) {
+                        b_h[0][threadIdx.x] = cur; b_1[0][threadIdx.x] = s1; b_2[0][threadIdx.x] = s2;
+                    } else {
+                        S1h[cur] = s1;
+                        S2h[cur] = s2;
+                    }
+                }
+                cur = h;
+                s1 = 0.0;
+                s2 = 0.0;
             }
-            const double n = static_cast<double>(kItem) * static_cast<double>(v);
-            const double q = S1 * S1 / n;
-            double s2 = (S2 - q) / (n - 1.0);
-            s2 = s2 > 0.0 ? s2 : 0.0;
-            if (S2 < (1.0 - 1e-6) * q) bad = 1;
-            a_mean += S1 / n;
-            a_var += s2 / n;
-            const double d = pow(s2, 0.5 * td.strat_beta);
-            dd[h] = d;
-            a_d += d;
+            const double2 r = rec[i];
+            s1 += r.x;
+            s2 += r.y;
         }
-        base += tot;
+        if (cur >= 0) {
+            const int k = b_h[0][threadIdx.x] < 0 ? 0 : 1;
+            b_h[k][threadIdx.x] = cur; b_1[k][threadIdx.x] = s1; b_2[k][threadIdx.x] = s2;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < static_cast<int>(blockDim.x); ++c)
+            for (int k = 0; k < 2; ++k) {
+                const int32_t h = b_h[k][c];
+                if (h >= 0) {
+                    S1h[h] += b_1[k][c];
+                    S2h[h] += b_2[k][c];
+                }
+            }
+    }
+    __syncthreads();
+    double a_mean = 0.0, a_var = 0.0, a_d = 0.0, a_abs = 0.0, a_bad = 0.0;
+    for (int h = threadIdx.x; h < H; h += blockDim.x) {
+        const double S1 = S1h[h], S2 = S2h[h];
+        const double n = static_cast<double>(kItem) * static_cast<double>(m[h]);
+        const double q = S1 * S1 / n;
+        double s2v = (S2 - q) / (n - 1.0);
+        s2v = s2v > 0.0 ? s2v : 0.0;
+        if (S2 < (1.0 - 1e-6) * q) a_bad += fabs(S1) / n;
+        a_abs += fabs(S1) / n;
+        a_mean += S1 / n;
+        a_var += s2v / n;
+        const double d = pow(s2v, 0.5 * td.strat_beta);
+        S1h[h] = d;
+        a_d += d;
     }
     r0[threadIdx.x] = a_mean;
     r1[threadIdx.x] = a_var;
     r2[threadIdx.x] = a_d;
-    si[threadIdx.x] = bad;
+    r3[threadIdx.x] = a_abs;
+    r4[threadIdx.x] = a_bad;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (static_cast<int>(threadIdx.x) < o) {
             r0[threadIdx.x] += r0[threadIdx.x + o];
             r1[threadIdx.x] += r1[threadIdx.x + o];
             r2[threadIdx.x] += r2[threadIdx.x + o];
-            si[threadIdx.x] |= si[threadIdx.x + o];
+            r3[threadIdx.x] += r3[threadIdx.x + o];
+            r4[threadIdx.x] += r4[threadIdx.x + o];
         }
         __syncthreads();
     }
     const double sum_d = r2[0];
-    const bool underflow = si[0] != 0;
+    // underflowed hypercubes (FP32 squares of weights near the end of the
+    // range) matter only when they carry a noticeable part of the estimate
+    const bool underflow = r4[0] > 1e-6 * r3[0];
     if (threadIdx.x == 0) {
         est[4 * t] = r0[0] / H;
         est[4 * t + 1] = r1[0] / (static_cast<double>(H) * H);
@@ -384,7 +444,7 @@ __global__ void strat_refine_kernel(const TaskDesc* __restrict__ tasks, const in
     if (sum_d > 0.0) {
         int64_t cnt = 0;
         for (int h = threadIdx.x; h < H; h += blockDim.x) {
-            const int32_t v = 1 + static_cast<int32_t>(floor(static_cast<double>(J - H) * dd[h] / sum_d));
+            const int32_t v = 1 + static_cast<int32_t>(floor(static_cast<double>(J - H) * S1h[h] / sum_d));
             m[h] = v;
             cnt += v;
         }

@@ -84,7 +84,7 @@ class Process:
     # as sigma_h^strat_beta; tasks then draw 8 floor(N / 8) samples.
     strat: int = 0
     strat_beta: float = 0.75
-    strat_max_hcubes: int = 65536
+    strat_max_hcubes: int = 64
 
 
 @dataclass(frozen=True)
