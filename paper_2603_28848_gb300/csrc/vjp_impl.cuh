@@ -390,7 +390,7 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
 }
 
 template <typename R, int NMAX, bool JVP>
-__global__ void __launch_bounds__(kThreads, 1) vjp_kernel(VjpParams V) {
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) vjp_kernel(VjpParams V) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const EvalParams& P = V.E;
     R* s_spline = reinterpret_cast<R*>(smem_raw);
