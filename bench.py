@@ -34,7 +34,7 @@ UNIT = "sweeps/s"
 WORKLOAD = "c2_bose_2to2"
 DT = 0.5          # requested Heun step (bounded by Eq. (16) inside each step)
 # DRAM bytes per sample-kernel launch from the last ncu capture of this kernel version
-TRAFFIC_BYTES_PER_LAUNCH = 1.493248e6
+TRAFFIC_BYTES_PER_LAUNCH = 1.511424e6
 FP32_PEAK_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
