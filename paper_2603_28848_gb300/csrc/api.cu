@@ -822,7 +822,7 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
         const size_t ngc = static_cast<size_t>(S) * 4 * (n - 1);
         const size_t map_elems = static_cast<size_t>(kMaxDim) * nb_max;
         ctx->vjp_smem = rs * ((spl + 3) & ~size_t(3)) + 2 * rs * map_elems + sizeof(double) * ngc +
-                        12 * 8 * sizeof(double);
+                        12 * 8 * sizeof(double) + (f32 ? sizeof(float) * ngc : 0);
         ctx->jvp_smem = rs * ((spl + 3) & ~size_t(3)) + 2 * rs * map_elems + 12 * 8 * sizeof(double) + rs * ngc;
     }
     CKI(cudaMemset(ctx->d_prev, 0, sizeof(double) * T));

@@ -69,7 +69,7 @@ __device__ __forceinline__ Hit<R> spline_hit(const SplineView<R>& sv, R q, const
 template <typename R, int NLEG, bool JVP>
 __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& seg, const SideDesc& sd,
                                             const TaskDesc& td, const TaskConst& tc, R* s_spline,
-                                            Real2<R>* s_map, double* s_gc, double* s_red, const R* s_dsp) {
+                                            Real2<R>* s_map, double* s_gc, double* s_red, R* s_dsp) {
     const EvalParams& P = V.E;
     constexpr int NI = NLEG - 2;
     constexpr int D = 3 * NI;
@@ -345,14 +345,26 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
                 if (k == NI && !inside) continue;
                 const R gk = U * dwdf[k];
                 if (gk != R(0)) {
-                    // FP64 shared-memory accumulation of the FP32 contributions
                     const int sp = k < NI ? spc[k] : spcn;
-                    double* dst = s_gc + sp * ncoef + 4 * jl[k];
-                    const double gd = static_cast<double>(gk), td_ = static_cast<double>(tl[k]);
-                    atomicAdd(dst + 0, gd);
-                    atomicAdd(dst + 1, gd * td_);
-                    atomicAdd(dst + 2, gd * td_ * td_);
-                    atomicAdd(dst + 3, gd * td_ * td_ * td_);
+                    if constexpr (F32) {
+                        // FP32 shared-memory sums of this segment (one task: the
+                        // contributions share a sign), moved into the FP64 array
+                        // at the end of the segment
+                        float* dst = s_dsp + sp * ncoef + 4 * jl[k];
+                        const float t = tl[k];
+                        const float g1 = gk * t, g2 = g1 * t;
+                        atomicAdd(dst + 0, gk);
+                        atomicAdd(dst + 1, g1);
+                        atomicAdd(dst + 2, g2);
+                        atomicAdd(dst + 3, g2 * t);
+                    } else {
+                        double* dst = s_gc + sp * ncoef + 4 * jl[k];
+                        const double td_ = tl[k];
+                        atomicAdd(dst + 0, gk);
+                        atomicAdd(dst + 1, gk * td_);
+                        atomicAdd(dst + 2, gk * td_ * td_);
+                        atomicAdd(dst + 3, gk * td_ * td_ * td_);
+                    }
                 }
             }
             }
@@ -386,6 +398,17 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
         for (int w = 0; w < nw; ++w) v += s_red[tid * 8 + w];
         part[tid] = v;
     }
+    if constexpr (!JVP && F32) {
+        // the segment's FP32 coefficient-gradient sums into the FP64 array
+        const int ngc = g.n_species * ncoef;
+        for (int k = tid; k < ngc; k += blockDim.x) {
+            const float v = s_dsp[k];
+            if (v != 0.0f) {
+                s_gc[k] += static_cast<double>(v);
+                s_dsp[k] = 0.0f;
+            }
+        }
+    }
     __syncthreads();
 }
 
@@ -400,13 +423,18 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) vjp_kernel(V
     const int ngc = 4 * (P.geo.n_grid - 1) * P.geo.n_species;
     double* s_gc = reinterpret_cast<double*>(s_map + map_elems);     // VJP: coefficient gradients
     double* s_red = s_gc + (JVP ? 0 : ngc);
-    R* s_dsp = reinterpret_cast<R*>(s_red + 12 * 8);                  // JVP: tangent coefficients
+    // JVP: tangent coefficients; FP32 VJP: the segment's coefficient-gradient sums
+    R* s_dsp = reinterpret_cast<R*>(s_red + 12 * 8);
     {
         const R* gc = static_cast<const R*>(P.coef);
         for (int k = threadIdx.x; k < ngc; k += blockDim.x) {
             s_spline[k] = gc[k];
-            if constexpr (JVP) s_dsp[k] = static_cast<const R*>(V.dcoef)[k];
-            else s_gc[k] = 0.0;
+            if constexpr (JVP) {
+                s_dsp[k] = static_cast<const R*>(V.dcoef)[k];
+            } else {
+                s_gc[k] = 0.0;
+                if constexpr (sizeof(R) == 4) s_dsp[k] = R(0);
+            }
         }
         const R* gk = static_cast<const R*>(P.knots);
         for (int k = threadIdx.x; k < P.geo.n_grid; k += blockDim.x) s_spline[ngc + k] = gk[k];
