@@ -35,6 +35,11 @@ WORKLOAD = "c2_bose_2to2"
 DT = 0.5          # requested Heun step (bounded by Eq. (16) inside each step)
 # DRAM bytes per sample-kernel launch from the last ncu capture of this kernel version
 TRAFFIC_BYTES_PER_LAUNCH = 1.511424e6
+# Thread instructions per sample of the 2->2 Bose sample kernel, from the same ncu capture
+# (smsp__inst_executed.sum x 32 x lanes-active ratio / samples): the kernel is issue-bound, so its
+# instruction issue rate against the SMs' issue peak says how close it is to the hardware limit.
+INSTR_PER_SAMPLE_C2 = 433.0
+ISSUE_PEAK_TINSTR = 152 * 4 * 32 * 2.07e9 / 1e12     # 4 schedulers x 1 warp instruction / clock
 FP32_PEAK_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
@@ -341,6 +346,11 @@ def run_native(args, rank, world):
             "share_of_step": kern_ms / (ms / args.steps) if ms > 0 else None,
             "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz max SM clock (nominal unit "
                           "counts; MEASURED_PEAKS.json has no FP32 figure)"}
+    if WORKLOAD_KEY == "c2":
+        issued = INSTR_PER_SAMPLE_C2 * samples_per_launch / (per_launch_ms / 1e3) / 1e12
+        roof["issue"] = {"achieved": issued, "peak": ISSUE_PEAK_TINSTR, "unit": "T thread-instructions/s",
+                         "frac": issued / ISSUE_PEAK_TINSTR, "instructions_per_sample": INSTR_PER_SAMPLE_C2,
+                         "source": "ncu capture in profiles/eval_kernel_f32_c2_bose_2to2.md"}
 
     out = {
         "metric": METRIC, "value": sweeps_per_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
