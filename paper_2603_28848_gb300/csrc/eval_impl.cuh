@@ -196,11 +196,12 @@ __device__ __forceinline__ R weight_at(const SegConst<R, NLEG>& C, const R* y, R
         const R qc = pc2 * (pc2 > R(0) ? RMath<R>::rsqrt_(pc2) : R(0)) * C.a;
         const bool below = qc < q0, above = qc > qN;
         if constexpr (F32) {
-            // spline and tail for every lane, then a select: the warp
-            // never diverges on the conserved leg
+            // spline for every lane, the tail only in warps where some lane
+            // left the grid, then a select: the warp never diverges on the
+            // conserved leg (the mask is the lanes still in the sample loop)
             const SplineView<R> sv{s_spline + C.sp_cons * ncoef, knots};
             fc = spline_eval<R>(sv, fminf(fmaxf(qc, q0), qN), g, inv_step, q0, lq0_step);
-            {
+            if (__any_sync(__activemask(), below || above)) {
                 const float x = below ? fmaf(C.tlo_b, Ec, C.tlo_a) : fmaf(C.thi_b, Ec, C.thi_a);
                 const float ft = tail_f32(x, C.eta_c);
                 fc = (below || above) ? ft : fc;
@@ -358,7 +359,7 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
         for (int sgi = 0; sgi < G; ++sgi) {
             // samples past the budget (only in a task's last group) are
             // computed and given weight 0: no branch inside the group
-            const bool valid = static_cast<int64_t>(grp) * G + sgi < N;
+            const bool valid = static_cast<uint32_t>(grp) * G + sgi < static_cast<uint32_t>(N);   // N <= 2^31
             // VEGAS map and scaling to (r, theta, phi - pi)
             R y[D];
             int bin[D];
