@@ -172,7 +172,12 @@ def _integrand(problem, si, term, i, f, dists, masses, coupling, a, y, q, w_frac
     prodE = torch.ones(N, dtype=torch.float64)
     for k in range(n):
         prodE = prodE * 2.0 * E[k]
-    w = coupling ** 2 * stat * torch.tensor(jac) * gauss / (TWO_PI ** (3 * (n - 1) - 4) * prodE)
+    Ein = sum(E[k] for k in range(n) if si.is_in(k))
+    Pin = sum(mom[k] for k in range(n) if si.is_in(k))
+    s_inv = Ein * Ein - torch.tensor(np.sum(Pin * Pin, axis=1))
+    c = getattr(proc, "me_coef", (1.0, 0.0, 0.0, 0.0))
+    me = ((c[3] * s_inv + c[2]) * s_inv + c[1]) * s_inv + c[0]
+    w = coupling ** 2 * me * stat * torch.tensor(jac) * gauss / (TWO_PI ** (3 * (n - 1) - 4) * prodE)
     return torch.where(cut, torch.zeros_like(w), w)
 
 

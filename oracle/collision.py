@@ -20,7 +20,9 @@ parametrised as in Sec. 2D and App. A:
     or the fractional width w (E_in + E_out) / 2 of App. C (``width``);
   * the weight is Eq. (12) / App. A: prod r^2 sin(theta) over
     ((2 pi)^(3(n-1)-4) prod_{all n legs} 2E) times the Gaussian, times |M|^2
-    and the gain or loss product;
+    and the gain or loss product; |M|^2 = coupling^2 P(s) with P a cubic in
+    the invariant s of the initial state (the paper takes any callable of the
+    momenta; its examples are all constant, P = 1);
   * gain = prod_{other side} f * prod_{observed side} (1 + eta f) and
     loss = prod_{observed side} f * prod_{other side} (1 + eta f), the f of
     the observed leg being the grid value f_a(q_i) (Sec. 2C, Eq. (5) and the
@@ -113,6 +115,19 @@ def kinematics(problem, si, i, m, a, y):
     return mom, E, qcom, jac
 
 
+def invariant_s(si, mom, E):
+    """s = (sum of initial energies)^2 - |sum of initial momenta|^2 per sample."""
+    Ein = sum(E[k] for k in range(si.n) if si.is_in(k))
+    Pin = sum(mom[k] for k in range(si.n) if si.is_in(k))
+    return Ein * Ein - np.sum(Pin * Pin, axis=-1)
+
+
+def matrix_element_poly(proc, s):
+    """|M|^2 / coupling^2 = c0 + c1 s + c2 s^2 + c3 s^3 (Horner)."""
+    c = getattr(proc, "me_coef", (1.0, 0.0, 0.0, 0.0))
+    return ((c[3] * s + c[2]) * s + c[1]) * s + c[0]
+
+
 def integrand(problem, si, term, i, f_obs, dists, m, a, y, w_frac=None):
     """Integrand on the unit cube (before the VEGAS Jacobian), shape (N,);
     w_frac: the process's fractional width (default: its initial width)."""
@@ -144,7 +159,8 @@ def integrand(problem, si, term, i, f_obs, dists, m, a, y, w_frac=None):
             gain *= fk
             loss *= enh
     stat = gain if term == 0 else loss
-    w = (proc.coupling ** 2) * stat * jac * gauss / (TWO_PI ** (3 * (n - 1) - 4) * np.prod(2.0 * E, axis=0))
+    w = (proc.coupling ** 2) * matrix_element_poly(proc, invariant_s(si, mom, E)) * stat * jac * gauss / \
+        (TWO_PI ** (3 * (n - 1) - 4) * np.prod(2.0 * E, axis=0))
     w[cut] = 0.0
     return w
 

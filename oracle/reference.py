@@ -46,7 +46,7 @@ def composite_gl(breaks, n):
 
 def two_body_cm(p1, masses, f1, dist2, dist3, dist4, eta, lam=1.0, term="loss",
                 r_cut=None, p2_breaks=(0, 0.25, 0.5, 1, 2, 4, 8, 16, 32, 64),
-                n_p2=24, n_c2=48, n_cs=48, omega=0.0):
+                n_p2=24, n_c2=48, n_cs=48, omega=0.0, me=None):
     """Single-position 2 -> 2 gain or loss term at observed momentum p1.
 
     Legs: 1 = observed (initial side), 2 = other initial leg, 3 and 4 = final
@@ -56,7 +56,9 @@ def two_body_cm(p1, masses, f1, dist2, dist3, dist4, eta, lam=1.0, term="loss",
     balance to E3 + E4 = E1 + E2 - omega (used by ``two_body_cm_smeared``);
     a callable omega(E_in) returns (omega, weight) arrays for the initial
     energy E_in = E1 + E2 of each node, the weight multiplying the integrand
-    (used by ``two_body_cm_fractional``).
+    (used by ``two_body_cm_fractional``).  ``me(s)`` multiplies |M|^2 = lam^2 by
+    a function of the initial state's invariant mass squared s = (E1 + E2)^2 -
+    |p1 + p2|^2 (constant when None).
     """
     m1, m2, m3, m4 = masses
     e1, e2, e3, e4 = eta
@@ -99,6 +101,9 @@ def two_body_cm(p1, masses, f1, dist2, dist3, dist4, eta, lam=1.0, term="loss",
     phase = TWO_PI * pstar / (16.0 * np.pi ** 2 * rs)
     # d^3p2 / ((2pi)^3 2E2) with the azimuth of p2 giving 2 pi
     meas = TWO_PI * P2 ** 2 / (TWO_PI ** 3 * 2.0 * E2)
+    if me is not None:
+        sin_ = (E1 + E2) ** 2 - Ptot ** 2          # initial state, before the omega shift
+        extra = extra * me(sin_)
     val = lam ** 2 * stat * phase * meas / (2.0 * E1) * extra
     return float(np.sum(np.where(keep, val, 0.0) * W))
 

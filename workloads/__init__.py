@@ -85,6 +85,9 @@ class Process:
     strat: int = 0
     strat_beta: float = 0.75
     strat_max_hcubes: int = 64
+    # |M|^2 = coupling^2 * (c0 + c1 s + c2 s^2 + c3 s^3), s the squared
+    # invariant mass of the initial state (constant |M|^2 by default).
+    me_coef: Tuple[float, float, float, float] = (1.0, 0.0, 0.0, 0.0)
 
 
 @dataclass(frozen=True)
