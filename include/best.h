@@ -67,6 +67,12 @@ typedef struct {
     double mass0, mass1;
 } best_species;
 
+/* Matrix element.  The paper registers |M|^2 as a callable of the momenta
+ * (Sec. 3A), which a kernel cannot call; here |M|^2 = coupling^2 P(s) with
+ * P(s) = me_coef[0] + me_coef[1] s + me_coef[2] s^2 + me_coef[3] s^3 and
+ * s = (sum of the initial energies)^2 - |sum of the initial momenta|^2 of the
+ * sample (physical units).  All-zero me_coef is rejected; {1, 0, 0, 0} is
+ * the constant |M|^2 = coupling^2 of all the paper's examples. */
 /* Adaptive stratified sampling (strat = 1; the vegas library's default
  * since 2021, Lepage, J. Comput. Phys. 439 (2021) 110386): a task draws
  * 8 floor(N/8) samples in items of 8; the map's unit cube is cut into M^D
@@ -109,6 +115,7 @@ typedef struct {
     int32_t strat;         /* 1: adaptive stratified sampling (see below) */
     int32_t strat_max_hcubes;   /* 1 .. 2^20 */
     double strat_beta;     /* >= 0 */
+    double me_coef[4];     /* |M|^2 = coupling^2 (c0 + c1 s + c2 s^2 + c3 s^3), see below */
 } best_process;
 
 typedef struct {

@@ -60,6 +60,8 @@ def config_from_problem(problem, precision):
         pr[k].strat = int(getattr(p, "strat", 0))
         pr[k].strat_max_hcubes = int(getattr(p, "strat_max_hcubes", 64))
         pr[k].strat_beta = float(getattr(p, "strat_beta", 0.75))
+        for j, c in enumerate(getattr(p, "me_coef", (1.0, 0.0, 0.0, 0.0))):
+            pr[k].me_coef[j] = float(c)
     cfg = _lib.best_config()
     cfg.grid.n = int(g.n)
     cfg.grid.log_spaced = 1 if g.log_spaced else 0

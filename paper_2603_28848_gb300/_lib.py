@@ -27,7 +27,7 @@ class best_process(ctypes.Structure):
                 ("alpha", c_double), ("width_mode", c_int32), ("pad_", c_int32), ("width", c_double),
                 ("width_rel_lo", c_double), ("width_rel_hi", c_double), ("width_factor", c_double),
                 ("width_min", c_double), ("width_max", c_double), ("strat", c_int32),
-                ("strat_max_hcubes", c_int32), ("strat_beta", c_double)]
+                ("strat_max_hcubes", c_int32), ("strat_beta", c_double), ("me_coef", c_double * 4)]
 
 
 class best_config(ctypes.Structure):

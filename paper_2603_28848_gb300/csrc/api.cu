@@ -277,6 +277,15 @@ best_status validate(const best_config* cfg) {
             return fail(ctx, BEST_ERR_INVALID,
                         "process %d: adaptive width needs 0 < width_min <= width <= width_max, width_factor > 1, "
                         "0 <= width_rel_lo < width_rel_hi", p);
+        {
+            bool finite = true, zero = true;
+            for (int k = 0; k < 4; ++k) {
+                finite = finite && std::isfinite(pr.me_coef[k]);
+                zero = zero && pr.me_coef[k] == 0.0;
+            }
+            if (!finite || zero)
+                return fail(ctx, BEST_ERR_INVALID, "process %d: me_coef must be finite and not all zero", p);
+        }
         if (pr.strat != 0 && pr.strat != 1) return fail(ctx, BEST_ERR_INVALID, "process %d: strat must be 0 or 1", p);
         if (pr.strat && (!(pr.strat_beta >= 0.0) || !std::isfinite(pr.strat_beta) || pr.strat_max_hcubes < 1 ||
                          pr.strat_max_hcubes > (1 << 20)))
@@ -295,6 +304,12 @@ best_status validate(const best_config* cfg) {
         }
     }
     return BEST_OK;
+}
+
+// |M|^2 / coupling^2 = P(s) of a process into its side descriptor.
+void set_matrix_element(SideDesc& sd, const best_process& pr) {
+    for (int k = 0; k < 4; ++k) sd.me_coef[k] = pr.me_coef[k];
+    sd.me_on = !(pr.me_coef[0] == 1.0 && pr.me_coef[1] == 0.0 && pr.me_coef[2] == 0.0 && pr.me_coef[3] == 0.0);
 }
 
 int group_size(int D, bool f32) {
@@ -562,6 +577,7 @@ bool describe_task(const best_config* cfg, int32_t task, SideDesc* out_sd, TaskD
                     sd.sigma = pr.sigma_E;
                     sd.width_mode = pr.width_mode;
                     sd.width0 = pr.width;
+                    set_matrix_element(sd, pr);
                     TaskDesc td{};
                     td.si = 0;
                     td.point = (task / 2) % n_grid;
@@ -657,6 +673,7 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
                 sd.sigma = pr.sigma_E;
                 sd.width_mode = pr.width_mode;
                 sd.width0 = pr.width;
+                set_matrix_element(sd, pr);
                 ctx->sides.push_back(sd);
             }
         }
@@ -705,7 +722,10 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return bail(fail(ctx, BEST_ERR_CUDA, "no CUDA device"));
-    ctx->n_variants = eval_variants(f32, ctx->nmax_legs, ctx->variant_fn, ctx->variant_mb, ctx->any_strat);
+    bool any_me = false;
+    for (const SideDesc& sd : ctx->sides) any_me = any_me || sd.me_on;
+    // stratified tasks and s-dependent |M|^2 run in the extended instantiations
+    ctx->n_variants = eval_variants(f32, ctx->nmax_legs, ctx->variant_fn, ctx->variant_mb, ctx->any_strat || any_me);
     {
         const size_t rs = f32 ? 4 : 8;
         const size_t spl = static_cast<size_t>(g.n_species) * 4 * (g.n_grid - 1) + g.n_grid;

@@ -98,6 +98,11 @@ struct SegConst {
     R gauss_k;              // -log2(e) / (2 sigma^2); fractional width: -2 log2(e) / w^2
     R e_obs;                // E_obs (fractional width: sigma_ref / sigma = 2 E_obs / (E_in + E_out))
     bool frac;              // fractional width of App. C
+    bool me_on;             // |M|^2 / coupling^2 = P(s) not constant
+    R me[4];                // P(s) coefficients
+    R inw[NI];              // 1: integrated leg j is initial (enters s), else 0
+    R cons_inw;             // 1: conserved leg initial
+    R obs_in_p, obs_in_E;   // observed leg's p_z and E if it is initial, else 0
     R e_cut;
     R eta_c;                // eta of the conserved leg (tail formula)
     R tlo_a, tlo_b, thi_a, thi_b;   // Eq. (13) end fits of the conserved leg's species
@@ -145,7 +150,8 @@ __device__ __forceinline__ float tail_f32(float x, float eta) {
 // Weight of one sample at the mapped point y (r, theta, phi - pi per
 // integrated leg) with map Jacobian jac: momenta, conserved leg, energies,
 // statistical factor, Gaussian and Eq. (12); 0 for a cut sample.
-template <typename R, int NLEG>
+// EXT: the instantiation also supports an s-dependent |M|^2 (see run_segment).
+template <typename R, int NLEG, bool EXT>
 __device__ __forceinline__ R weight_at(const SegConst<R, NLEG>& C, const R* y, R jac, const R* s_spline,
                                        const R* knots, const Geometry& g, R inv_step, R q0, R lq0_step, R qN,
                                        int ncoef) {
@@ -155,6 +161,7 @@ __device__ __forceinline__ R weight_at(const SegConst<R, NLEG>& C, const R* y, R
     R px = R(0), py = R(0), pz = C.pobs_sig;
     R dE = C.sgn_obs_E;
     R Esum = C.e_obs;                   // E_in + E_out (used when C.frac)
+    R Qx = R(0), Qy = R(0), Qz = C.obs_in_p, Ein = C.obs_in_E;   // initial state (used when C.me_on)
     R meas = jac;
     R stat = C.c0;
     R rinvE_prod = R(1);
@@ -177,6 +184,13 @@ __device__ __forceinline__ R weight_at(const SegConst<R, NLEG>& C, const R* y, R
         cut |= E < C.e_cut;
         dE = fma(C.sgnE[j], E, dE);
         Esum += E;
+        if (EXT && C.me_on) {
+            const R iw = C.inw[j];
+            Qx = fma(-iw * ps, cp, Qx);
+            Qy = fma(-iw * ps, sp, Qy);
+            Qz = fma(iw * p, ct, Qz);
+            Ein = fma(iw, E, Ein);
+        }
         meas *= r * r * st;
         rinvE_prod *= rE;
         const SplineView<R> sv{s_spline + C.spc[j] * ncoef, knots};
@@ -230,12 +244,22 @@ __device__ __forceinline__ R weight_at(const SegConst<R, NLEG>& C, const R* y, R
     } else {
         gauss = RMath<R>::exp2_(C.gauss_k * dE * dE);
     }
-    const R w = stat * meas * rinvE_prod * rEc * gauss;
+    R w = stat * meas * rinvE_prod * rEc * gauss;
+    if (EXT && C.me_on) {
+        // |M|^2 / coupling^2 = P(s), s of the initial state (the conserved
+        // leg's momentum is (px, py, pz))
+        const R cw = C.cons_inw;
+        const R qx = fma(cw, px, Qx), qy = fma(cw, py, Qy), qz = fma(cw, pz, Qz);
+        const R e = fma(cw, Ec, Ein);
+        const R sv = fma(e, e, -fma(qx, qx, fma(qy, qy, qz * qz)));
+        w *= fma(fma(fma(C.me[3], sv, C.me[2]), sv, C.me[1]), sv, C.me[0]);
+    }
     return cut ? R(0) : w;
 }
 
-// STRAT: the instantiation also handles stratified tasks (kept apart so that
-// the plain kernel's register allocation is not affected).
+// STRAT: the instantiation also handles stratified tasks and s-dependent
+// matrix elements (kept apart so that the plain kernel's register allocation
+// is not affected).
 template <typename R, int NLEG, bool STRAT>
 __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& seg,
                                             const SideDesc& sd, const TaskDesc& td,
@@ -331,6 +355,16 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
     C.gauss_k = static_cast<R>(C.frac ? -2.0 * 1.4426950408889634 / (tc.wfrac * tc.wfrac)
                                       : -1.4426950408889634 / (2.0 * sd.sigma * sd.sigma));
     C.e_obs = static_cast<R>(tc.E_obs);
+    C.me_on = sd.me_on != 0;
+    for (int k = 0; k < 4; ++k) C.me[k] = static_cast<R>(sd.me_coef[k]);
+    {
+        const bool obs_in = (sd.in_mask >> sd.obs) & 1;
+        C.obs_in_p = obs_in ? static_cast<R>(tc.p_obs) : R(0);
+        C.obs_in_E = obs_in ? static_cast<R>(tc.E_obs) : R(0);
+        C.cons_inw = cons_in ? R(1) : R(0);
+#pragma unroll
+        for (int j = 0; j < NI; ++j) C.inw[j] = ((sd.in_mask >> sd.integ[j]) & 1) ? R(1) : R(0);
+    }
     C.e_cut = static_cast<R>(g.e_cut);
     const R nbR = static_cast<R>(nb);
     const R q0 = static_cast<R>(g.q_min);
@@ -385,7 +419,7 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
                 jac *= e.dy;
                 bin[d] = b;
             }
-            R w = weight_at<R, NLEG>(C, y, jac, s_spline, knots, g, inv_step, q0, lq0_step, qN, ncoef);
+            R w = weight_at<R, NLEG, STRAT>(C, y, jac, s_spline, knots, g, inv_step, q0, lq0_step, qN, ncoef);
             w = valid ? w : R(0);
             const R w2 = w * w;
             acc_w.add(w);
@@ -456,7 +490,7 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
                         jac *= e.dy;
                         bin[d] = b;
                     }
-                    const R w = weight_at<R, NLEG>(C, y, jac, s_spline, knots, g, inv_step, q0, lq0_step, qN,
+                    const R w = weight_at<R, NLEG, STRAT>(C, y, jac, s_spline, knots, g, inv_step, q0, lq0_step, qN,
                                                    ncoef);
                     const R w2 = w * w;
                     s1 += w;

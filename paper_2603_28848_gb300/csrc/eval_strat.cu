@@ -1,5 +1,6 @@
 // Instantiations of the sample kernel that also run stratified (VEGAS+)
-// tasks; used by contexts with at least one stratified process.
+// tasks and s-dependent matrix elements; used by contexts with at least one
+// such process.
 #include "eval_impl.cuh"
 
 namespace best {

@@ -34,8 +34,9 @@ struct SideDesc {
     double sigma;           // sigma_E
     double eta_obs;         // eta of the observed species
     int32_t width_mode;     // 0: sigma_E; 1: fractional w; 2: fractional, adapted (App. C)
-    int32_t pad_;
+    int32_t me_on;          // |M|^2 depends on s (me_coef other than {1, 0, 0, 0})
     double width0;          // initial fractional width
+    double me_coef[4];      // |M|^2 / coupling^2 = c0 + c1 s + c2 s^2 + c3 s^3
 };
 
 // One task: side integral x grid point x {gain, loss}.

@@ -156,6 +156,8 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     if (td.nbins > kMaxBins) return report(BEST_ERR_INVALID, "noalloc: nbins exceeds 64");
     if (cfg->processes[sd.process].strat)
         return report(BEST_ERR_INVALID, "noalloc: stratified sampling is not supported here");
+    if (sd.me_on)
+        return report(BEST_ERR_INVALID, "noalloc: s-dependent matrix elements are not supported here");
     const bool f32 = cfg->precision == BEST_FP32;
 
     // Set-up once per device: the device address of the scratch array.

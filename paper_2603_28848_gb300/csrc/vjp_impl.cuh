@@ -151,6 +151,19 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
     const R inv_sig2_abs = static_cast<R>(1.0 / (sd.sigma * sd.sigma));
     const R four_over_w2 = static_cast<R>(frac ? 4.0 / (tc.wfrac * tc.wfrac) : 0.0);
     const R e_obs = static_cast<R>(tc.E_obs);
+    // |M|^2 / coupling^2 = P(s), s of the initial state
+    const bool me_on = sd.me_on != 0;
+    R mec[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) mec[k] = static_cast<R>(sd.me_coef[k]);
+    const bool obs_in = (sd.in_mask >> sd.obs) & 1;
+    const R obs_in_p = obs_in ? static_cast<R>(tc.p_obs) : R(0);
+    const R obs_in_E = obs_in ? static_cast<R>(tc.E_obs) : R(0);
+    const R obs_inw = obs_in ? R(1) : R(0);
+    const R cons_inw = cons_in ? R(1) : R(0);
+    R inw[NI];
+#pragma unroll
+    for (int j = 0; j < NI; ++j) inw[j] = ((sd.in_mask >> sd.integ[j]) & 1) ? R(1) : R(0);
     const R e_cut = static_cast<R>(g.e_cut);
     const R inv_Eobs = static_cast<R>(1.0 / tc.E_obs);
     const R U = static_cast<R>(V.task_u[seg.task]);     // VJP: adjoint seed; JVP: obs tangent factor
@@ -208,6 +221,7 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
             R px = R(0), py = R(0), pz = pobs_sig;
             R dE = sgn_obs_E;
             R Esum = e_obs;
+            R Qx = R(0), Qy = R(0), Qz = obs_in_p, Ein = obs_in_E;
             R meas = jac;
             R rinv = R(1);
             bool cut = obs_cut;
@@ -230,6 +244,12 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
                 cut |= E < e_cut;
                 dE = fma(sgnE[j], E, dE);
                 Esum += E;
+                if (me_on) {
+                    Qx = fma(-inw[j] * ps, cp, Qx);
+                    Qy = fma(-inw[j] * ps, sp, Qy);
+                    Qz = fma(inw[j] * p, ct, Qz);
+                    Ein = fma(inw[j], E, Ein);
+                }
                 meas *= r * r * st;
                 rinv *= rr;
                 rE[j] = rr;
@@ -292,6 +312,16 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
             }
             R base = meas * rinv * rEc * gs;
             base = (cut || !valid) ? R(0) : base;
+            R me_d = R(0);          // d log P / d E_k of every initial leg: P'(s) / P(s) 2 E_in
+            if (me_on) {
+                const R qx = fma(cons_inw, px, Qx), qy = fma(cons_inw, py, Qy), qz = fma(cons_inw, pz, Qz);
+                const R e = fma(cons_inw, Ec, Ein);
+                const R sv = fma(e, e, -fma(qx, qx, fma(qy, qy, qz * qz)));
+                const R P = fma(fma(fma(mec[3], sv, mec[2]), sv, mec[1]), sv, mec[0]);
+                const R dP = fma(fma(R(3) * mec[3], sv, R(2) * mec[2]), sv, mec[1]);
+                me_d = P != R(0) ? R(2) * e * dP * RMath<R>::rcp_(P) : R(0);
+                base *= P;
+            }
             // products excluding each factor
             R pre[NI + 2];
             pre[0] = R(1);
@@ -328,15 +358,17 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
             } else {
             const R dEterm = -wn * dE * inv_sig2;
             const R wsig = wn * sig_term;           // fractional width: same for every leg
+            const R wme = wn * me_d;                // s-dependent |M|^2: every initial leg
 #pragma unroll
             for (int j = 0; j < NI; ++j) {
-                const R gE = fma(-wn, rE[j], fma(dEterm, sgnE[j], wsig));
+                const R gE = fma(-wn, rE[j], fma(dEterm, sgnE[j], fma(inw[j], wme, wsig)));
                 acc_m[j].add(gE * mass[j] * rE[j]);
             }
             const R gz = dwdf[NI] * dfdz;           // zero inside the grid
-            const R gEc = fma(-wn, rEc, fma(dEterm, sgn_cons, fma(gz, below ? tlo_b : thi_b, wsig)));
+            const R gEc = fma(-wn, rEc, fma(dEterm, sgn_cons, fma(gz, below ? tlo_b : thi_b,
+                                                                  fma(cons_inw, wme, wsig))));
             acc_mc.add(gEc * mass_c * rEc);
-            acc_mobs.add(fma(-wn, inv_Eobs, fma(dEterm, s_obs, wsig)));
+            acc_mobs.add(fma(-wn, inv_Eobs, fma(dEterm, s_obs, fma(obs_inw, wme, wsig))));
             if (below) { acc_tla.add(gz); acc_tlb.add(gz * Ec); }
             if (above) { acc_tha.add(gz); acc_thb.add(gz * Ec); }
             // spline coefficient gradients of this sample's lookups
