@@ -38,8 +38,8 @@ __global__ void heun_correct_kernel(Geometry, double*, const double*, const doub
 // variants.cu
 int eval_variants(bool f32, int nmax, void** fn, int* mb, bool strat);
 // vjp.cu
-void* vjp_kernel_ptr(bool f32, int nmax);
-void* jvp_kernel_ptr(bool f32, int nmax);
+void* vjp_kernel_ptr(bool f32, int nmax, bool me);
+void* jvp_kernel_ptr(bool f32, int nmax, bool me);
 __global__ void jvp_seed_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskConst*, const SpeciesConst*,
                                 const double*, double*);
 __global__ void jvp_finish_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskConst*, const double*, double*,
@@ -156,6 +156,7 @@ struct best_ctx {
     WidthCtl* d_wctl = nullptr;
     std::vector<int> width_mode;
     bool any_adaptive = false;
+    bool any_me = false;            // some process has an s-dependent |M|^2
     // adaptive stratified sampling (VEGAS+)
     bool any_strat = false;
     int64_t strat_total_h = 0, strat_total_items = 0;
@@ -722,10 +723,10 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return bail(fail(ctx, BEST_ERR_CUDA, "no CUDA device"));
-    bool any_me = false;
-    for (const SideDesc& sd : ctx->sides) any_me = any_me || sd.me_on;
+    for (const SideDesc& sd : ctx->sides) ctx->any_me = ctx->any_me || sd.me_on;
     // stratified tasks and s-dependent |M|^2 run in the extended instantiations
-    ctx->n_variants = eval_variants(f32, ctx->nmax_legs, ctx->variant_fn, ctx->variant_mb, ctx->any_strat || any_me);
+    ctx->n_variants = eval_variants(f32, ctx->nmax_legs, ctx->variant_fn, ctx->variant_mb,
+                                    ctx->any_strat || ctx->any_me);
     {
         const size_t rs = f32 ? 4 : 8;
         const size_t spl = static_cast<size_t>(g.n_species) * 4 * (g.n_grid - 1) + g.n_grid;
@@ -1042,7 +1043,7 @@ best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, con
     if (!std::isfinite(t)) return fail(ctx, BEST_ERR_INVALID, "t must be finite");
     const Geometry& g = ctx->geo;
     const bool f32 = ctx->precision == BEST_FP32;
-    void* fn = vjp_kernel_ptr(f32, ctx->nmax_legs);
+    void* fn = vjp_kernel_ptr(f32, ctx->nmax_legs, ctx->any_me);
     int max_optin = 0, dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -1137,7 +1138,7 @@ static best_status enqueue_jvp(best_ctx* ctx, const double* f_dev, double t, con
                                double* JU_dev, cudaStream_t st, bool setup) {
     const Geometry& g = ctx->geo;
     const bool f32 = ctx->precision == BEST_FP32;
-    void* fn = jvp_kernel_ptr(f32, ctx->nmax_legs);
+    void* fn = jvp_kernel_ptr(f32, ctx->nmax_legs, ctx->any_me);
     if (!ctx->jvp_ready) {
         int max_optin = 0, dev = 0;
         CK(cudaGetDevice(&dev));

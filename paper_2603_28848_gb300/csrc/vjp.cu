@@ -19,8 +19,15 @@ void* kernel_ptr(bool f32, int nmax) {
     return reinterpret_cast<void*>(&vjp_kernel<double, 6, JVP>);
 }
 
-void* vjp_kernel_ptr(bool f32, int nmax) { return kernel_ptr<false>(f32, nmax); }
-void* jvp_kernel_ptr(bool f32, int nmax) { return kernel_ptr<true>(f32, nmax); }
+void* vjp_me_kernel_ptr(bool f32, int nmax, bool jvp);     // vjp_me.cu
+
+// me: some process has an s-dependent |M|^2 (the extended instantiations)
+void* vjp_kernel_ptr(bool f32, int nmax, bool me) {
+    return me ? vjp_me_kernel_ptr(f32, nmax, false) : kernel_ptr<false>(f32, nmax);
+}
+void* jvp_kernel_ptr(bool f32, int nmax, bool me) {
+    return me ? vjp_me_kernel_ptr(f32, nmax, true) : kernel_ptr<true>(f32, nmax);
+}
 
 // Adjoint seed of every task: L = sum_{a,i} v_{a,i} C~_a(p_i) and C~ = sum
 // mult (I_gain - I_loss), I = K scale (sum w_n) / N, so dL/dw_n = v mult sign

@@ -66,7 +66,9 @@ __device__ __forceinline__ Hit<R> spline_hit(const SplineView<R>& sv, R q, const
 // JVP = false: adjoint (VJP) accumulation; true: forward tangent dC~ = J u,
 // with the tangent spline table of u in s_dsp (same layout as s_spline's
 // coefficients) and the tail tangents (da, db per end) in V.dtail.
-template <typename R, int NLEG, bool JVP>
+// ME: the instantiation supports an s-dependent |M|^2 (kept apart so that the
+// plain instantiations' register allocation is not affected).
+template <typename R, int NLEG, bool JVP, bool ME>
 __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& seg, const SideDesc& sd,
                                             const TaskDesc& td, const TaskConst& tc, R* s_spline,
                                             Real2<R>* s_map, double* s_gc, double* s_red, R* s_dsp) {
@@ -152,7 +154,7 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
     const R four_over_w2 = static_cast<R>(frac ? 4.0 / (tc.wfrac * tc.wfrac) : 0.0);
     const R e_obs = static_cast<R>(tc.E_obs);
     // |M|^2 / coupling^2 = P(s), s of the initial state
-    const bool me_on = sd.me_on != 0;
+    const bool me_on = ME && sd.me_on != 0;
     R mec[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) mec[k] = static_cast<R>(sd.me_coef[k]);
@@ -444,7 +446,7 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
     __syncthreads();
 }
 
-template <typename R, int NMAX, bool JVP>
+template <typename R, int NMAX, bool JVP, bool ME = false>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) vjp_kernel(VjpParams V) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const EvalParams& P = V.E;
@@ -479,10 +481,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) vjp_kernel(V
         const TaskConst tc = P.tconst[seg.task];
         __syncthreads();
         switch (sd.n) {
-            case 3: if constexpr (NMAX >= 3) vjp_segment<R, 3, JVP>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp); break;
-            case 4: if constexpr (NMAX >= 4) vjp_segment<R, 4, JVP>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp); break;
-            case 5: if constexpr (NMAX >= 5) vjp_segment<R, 5, JVP>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp); break;
-            case 6: if constexpr (NMAX >= 6) vjp_segment<R, 6, JVP>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp); break;
+            case 3: if constexpr (NMAX >= 3) vjp_segment<R, 3, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp); break;
+            case 4: if constexpr (NMAX >= 4) vjp_segment<R, 4, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp); break;
+            case 5: if constexpr (NMAX >= 5) vjp_segment<R, 5, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp); break;
+            case 6: if constexpr (NMAX >= 6) vjp_segment<R, 6, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp); break;
             default: break;
         }
     }
