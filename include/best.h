@@ -132,6 +132,8 @@ typedef struct {
     int32_t pad_;
     double a0, t0;
     double eps_dt;                   /* bound on max |dt C/f| of Eq. (16) */
+    int32_t point_lo, point_hi;      /* shard: grid points [point_lo, point_hi) only; 0, 0 = all
+                                        (see best_step_stage) */
 } best_config;
 
 typedef struct best_ctx best_ctx;
@@ -177,6 +179,32 @@ best_status best_step_euler(best_ctx* ctx, double* logf_dev, double* t_dev,
  */
 best_status best_step_heun(best_ctx* ctx, double* logf_dev, double* t_dev,
                            double* dt_dev, double* C_dev, void* stream);
+
+/*
+ * Sharded runs (the paper's MPI design over grid points, Sec. 3D): each
+ * process builds its context with config.point_lo/point_hi, so that it holds
+ * only the tasks of its grid points; best_collision_eval writes C and err for
+ * those points and zero elsewhere, so the processes' C arrays add up to the
+ * full C (an all-reduce sum, or an all-gather of the slices).  Task ids and
+ * hence the Philox streams are those of the whole grid: the shards draw
+ * exactly the samples a whole-grid context would.  The adaptive width
+ * (width_mode 2) needs every task in one context and is rejected in a shard.
+ *
+ * best_collision_eval_log: best_collision_eval from log f (f = exp(log f)).
+ * best_step_stage: one stage of a step from the assembled C, every process
+ * applying it to its copy of the whole distribution (same arithmetic as
+ * best_step_euler / best_step_heun, Eq. (14)-(16)); all pointers device:
+ *   method 0 (Euler), stage 0: k1 = C(f) at t: dt = min(*dt_dev, eps/max|k1/f|),
+ *       log f += dt k1/f, *t_dev += dt, *dt_dev = dt.
+ *   method 1 (Heun), stage 0: k1 = C(f) at t: dt as above, fstar = exp(log f +
+ *       dt k1/f), *dt_dev = dt (t unchanged); evaluate k2 = C(fstar) at t + dt;
+ *   method 1, stage 1: log f += dt/2 (k1/f + k2/fstar), *t_dev += dt.
+ * logf, k1, k2, fstar: [n_species*n_grid]; asynchronous on `stream`.
+ */
+best_status best_collision_eval_log(best_ctx* ctx, const double* logf_dev, double t, double* C_dev,
+                                    double* err_dev, void* stream);
+best_status best_step_stage(best_ctx* ctx, int32_t method, int32_t stage, double* logf_dev, const double* k1_dev,
+                            const double* k2_dev, double* fstar_dev, double* t_dev, double* dt_dev, void* stream);
 
 /*
  * n_steps Euler (method 0, Eq. (14)) or Heun (method 1, Eq. (15)) steps

@@ -110,7 +110,7 @@ class Collision:
     """One context of libbest: the tasks, VEGAS maps and device state of a
     problem.  ``precision``: workloads.PREC_FP64 or PREC_FP32."""
 
-    def __init__(self, problem, precision):
+    def __init__(self, problem, precision, points=None):
         import torch
         if not torch.cuda.is_available():
             raise BestError("a CUDA device is required")
@@ -121,6 +121,10 @@ class Collision:
         self.n_species = len(problem.species)
         self.n_grid = problem.grid.n
         cfg, keep = config_from_problem(problem, precision)
+        if points is not None:
+            # a shard: the tasks of grid points [lo, hi) only (see dist.sharded_step)
+            cfg.point_lo, cfg.point_hi = int(points[0]), int(points[1])
+        self.points = (0, problem.grid.n) if points is None else (int(points[0]), int(points[1]))
         ctx = ctypes.c_void_p()
         check(self.lib.best_collision_init(ctypes.byref(cfg), ctypes.byref(ctx)))
         del keep
@@ -146,6 +150,26 @@ class Collision:
         _require(logf, self.n_species * self.n_grid, "logf")
         check(self.lib.best_step_euler(self.ctx, _ptr(logf), _ptr(t_dev), _ptr(dt_dev), _ptr(C),
                                        _stream(stream)), self.ctx)
+
+    def eval_log(self, logf, t=0.0, C=None, err=None, stream=None):
+        """eval from log f (the sweep exponentiates on the device)."""
+        import torch
+        n = self.n_species * self.n_grid
+        _require(logf, n, "logf")
+        if C is None:
+            C = torch.empty_like(logf)
+        if err is None:
+            err = torch.empty_like(logf)
+        check(self.lib.best_collision_eval_log(self.ctx, _ptr(logf), float(t), _ptr(C), _ptr(err), _stream(stream)),
+              self.ctx)
+        return C, err
+
+    def step_stage(self, method, stage, logf, k1, t_dev, dt_dev, k2=None, fstar=None, stream=None):
+        """One stage of an Euler (method 0) or Heun (method 1) step from an
+        assembled C (best_step_stage)."""
+        _require(logf, self.n_species * self.n_grid, "logf")
+        check(self.lib.best_step_stage(self.ctx, int(method), int(stage), _ptr(logf), _ptr(k1), _ptr(k2), _ptr(fstar),
+                                       _ptr(t_dev), _ptr(dt_dev), _stream(stream)), self.ctx)
 
     def step_heun(self, logf, t_dev, dt_dev, C=None, stream=None):
         _require(logf, self.n_species * self.n_grid, "logf")

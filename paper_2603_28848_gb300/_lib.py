@@ -35,7 +35,8 @@ class best_config(ctypes.Structure):
                 ("species", POINTER(best_species)), ("processes", POINTER(best_process)),
                 ("precision", c_int32), ("tail_points", c_int32), ("seed", c_uint64),
                 ("e_cut", c_double), ("expansion", c_int32), ("pad_", c_int32),
-                ("a0", c_double), ("t0", c_double), ("eps_dt", c_double)]
+                ("a0", c_double), ("t0", c_double), ("eps_dt", c_double),
+                ("point_lo", c_int32), ("point_hi", c_int32)]
 
 
 class BestError(RuntimeError):
@@ -48,6 +49,9 @@ SIGNATURES = {
     "best_collision_eval": ([c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p], c_int32),
     "best_step_euler": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "best_step_heun": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "best_collision_eval_log": ([c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p], c_int32),
+    "best_step_stage": ([c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                         c_void_p], c_int32),
     "best_evolve": ([c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_double, c_void_p], c_int32),
     "best_autotune": ([c_void_p, c_void_p, c_double, POINTER(c_int32), c_void_p], c_int32),
     "best_collision_vjp": ([c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,

@@ -35,6 +35,8 @@ __global__ void step_first_kernel(Geometry, double*, const double*, const double
                                   double*, int);
 __global__ void heun_correct_kernel(Geometry, double*, const double*, const double*, const double*, double*,
                                     double*, TimeState*);
+__global__ void stage_kernel(Geometry, int, int, double*, const double*, const double*, double*, double*, double*,
+                             TimeState*);
 // variants.cu
 int eval_variants(bool f32, int nmax, void** fn, int* mb, bool strat);
 // vjp.cu
@@ -258,6 +260,9 @@ best_status validate(const best_config* cfg) {
         if (!std::isfinite(sp.mass0) || !std::isfinite(sp.mass1))
             return fail(ctx, BEST_ERR_INVALID, "species %d: bad mass", s);
     }
+    if (cfg->point_hi != 0 && !(cfg->point_lo >= 0 && cfg->point_lo < cfg->point_hi && cfg->point_hi <= g.n))
+        return fail(ctx, BEST_ERR_INVALID, "shard: need 0 <= point_lo < point_hi <= grid.n (or both 0)");
+    const bool shard = cfg->point_hi != 0 && !(cfg->point_lo == 0 && cfg->point_hi == g.n);
     for (int p = 0; p < cfg->n_processes; ++p) {
         const best_process& pr = cfg->processes[p];
         const int n = pr.n_in + pr.n_out;
@@ -269,6 +274,9 @@ best_status validate(const best_config* cfg) {
         if (!(pr.sigma_E > 0.0)) return fail(ctx, BEST_ERR_INVALID, "process %d: sigma_E must be > 0", p);
         if (pr.width_mode < 0 || pr.width_mode > 2)
             return fail(ctx, BEST_ERR_INVALID, "process %d: width_mode must be 0, 1 or 2", p);
+        if (shard && pr.width_mode == 2)
+            return fail(ctx, BEST_ERR_INVALID, "process %d: the adaptive width needs every task in one context "
+                        "(a shard would adapt on its own points only)", p);
         if (pr.width_mode != 0 && !(pr.width > 0.0 && std::isfinite(pr.width)))
             return fail(ctx, BEST_ERR_INVALID, "process %d: width must be > 0", p);
         if (pr.width_mode == 2 &&
@@ -583,6 +591,7 @@ bool describe_task(const best_config* cfg, int32_t task, SideDesc* out_sd, TaskD
                     td.si = 0;
                     td.point = (task / 2) % n_grid;
                     td.term = task % 2;
+                    td.gid = static_cast<uint32_t>(task);
                     td.nitn = 1;
                     td.neval = pr.neval_per_point ? pr.neval_per_point[td.point] : pr.neval;
                     td.dim = 3 * (n - 2);
@@ -630,6 +639,8 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     g.seed = cfg->seed;
     g.tail_points = cfg->tail_points;
     g.precision = cfg->precision;
+    g.pt_lo = cfg->point_hi > 0 ? cfg->point_lo : 0;
+    g.pt_hi = cfg->point_hi > 0 ? cfg->point_hi : cfg->grid.n;
     ctx->precision = cfg->precision;
     const bool f32 = cfg->precision == BEST_FP32;
 
@@ -685,12 +696,13 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     for (int si = 0; si < g.n_side; ++si) {
         const SideDesc& sd = ctx->sides[si];
         const best_process& pr = cfg->processes[sd.process];
-        for (int i = 0; i < g.n_grid; ++i)
+        for (int i = g.pt_lo; i < g.pt_hi; ++i)
             for (int term = 0; term < 2; ++term) {
                 TaskDesc td{};
                 td.si = si;
                 td.point = i;
                 td.term = term;
+                td.gid = static_cast<uint32_t>((si * g.n_grid + i) * 2 + term);
                 td.nitn = pr.nitn;
                 td.neval = pr.neval_per_point ? pr.neval_per_point[i] : pr.neval;
                 td.dim = 3 * (sd.n - 2);
@@ -887,6 +899,34 @@ best_status best_collision_eval(best_ctx* ctx, const double* f_dev, double t, do
     set_time_kernel<<<1, 32, 0, st>>>(ctx->geo, ctx->d_ts, nullptr, t, 0, ctx->d_mass0, ctx->d_mass1);
     ctx->launches += 1;
     return enqueue_sweep(ctx, f_dev, 0, C_dev, err_dev, st);
+}
+
+best_status best_collision_eval_log(best_ctx* ctx, const double* logf_dev, double t, double* C_dev,
+                                    double* err_dev, void* stream) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    if (!logf_dev || !C_dev) return fail(ctx, BEST_ERR_INVALID, "logf_dev and C_dev must not be NULL");
+    if (!std::isfinite(t)) return fail(ctx, BEST_ERR_INVALID, "t must be finite");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ctx->launches = 0;
+    set_time_kernel<<<1, 32, 0, st>>>(ctx->geo, ctx->d_ts, nullptr, t, 0, ctx->d_mass0, ctx->d_mass1);
+    ctx->launches += 1;
+    return enqueue_sweep(ctx, logf_dev, 1, C_dev, err_dev, st);
+}
+
+best_status best_step_stage(best_ctx* ctx, int32_t method, int32_t stage, double* logf_dev, const double* k1_dev,
+                            const double* k2_dev, double* fstar_dev, double* t_dev, double* dt_dev, void* stream) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    if (method != 0 && method != 1) return fail(ctx, BEST_ERR_INVALID, "method must be 0 (Euler) or 1 (Heun)");
+    if (stage != 0 && !(method == 1 && stage == 1)) return fail(ctx, BEST_ERR_INVALID, "stage must be 0, or 1 for Heun");
+    if (!logf_dev || !k1_dev || !t_dev || !dt_dev) return fail(ctx, BEST_ERR_INVALID, "logf, k1, t and dt must not be NULL");
+    if (method == 1 && !fstar_dev) return fail(ctx, BEST_ERR_INVALID, "Heun needs fstar");
+    if (stage == 1 && !k2_dev) return fail(ctx, BEST_ERR_INVALID, "the Heun corrector needs k2");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    stage_kernel<<<1, 1024, 0, st>>>(ctx->geo, method, stage, logf_dev, k1_dev, k2_dev, fstar_dev, t_dev, dt_dev,
+                                     ctx->d_ts);
+    ctx->launches = 1;
+    CK(cudaGetLastError());
+    return BEST_OK;
 }
 
 static best_status step_common(best_ctx* ctx, double* logf, double* t_dev, double* dt_dev, double* C_dev,

@@ -380,7 +380,7 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
     // ---- samples ------------------------------------------------------------
     Acc<R> acc_w, acc_w2;
     const int64_t N = td.neval;
-    const uint32_t task = static_cast<uint32_t>(seg.task);
+    const uint32_t task = td.gid;                 // the stream is keyed by the global task id
     const int32_t g1 = static_cast<int32_t>(seg.g1);
     if (!STRAT || td.strat_H == 0)
     for (int32_t grp = static_cast<int32_t>(seg.g0) + tid; grp < g1; grp += blockDim.x) {

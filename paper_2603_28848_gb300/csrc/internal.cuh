@@ -56,6 +56,8 @@ struct TaskDesc {
     int64_t strat_off_h;    // offset of the task's hypercube arrays
     int64_t strat_off_item; // offset of the task's item arrays
     double strat_beta;      // damping exponent of the allocation
+    uint32_t gid;           // task id in the whole grid's numbering (the Philox stream's task word)
+    int32_t pad2_;
 };
 
 // Per-task values recomputed at the start of every sweep (FP64).
@@ -132,6 +134,7 @@ struct Geometry {
     uint64_t seed;
     int32_t tail_points;
     int32_t precision;
+    int32_t pt_lo, pt_hi;   // grid points of this context's tasks (a shard), [pt_lo, pt_hi)
 };
 
 // Arguments of the sample kernel.

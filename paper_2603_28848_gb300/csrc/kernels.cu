@@ -631,10 +631,12 @@ __global__ void assemble_kernel(Geometry g, const SideDesc* __restrict__ sides, 
         const int s = k / n;
         const int i = k - s * n;
         double c = 0.0, v = 0.0;
-        for (int si = 0; si < g.n_side; ++si) {
+        const int nl = g.pt_hi - g.pt_lo;         // points of this context (a shard) in task order
+        const bool mine = i >= g.pt_lo && i < g.pt_hi;
+        for (int si = 0; si < (mine ? g.n_side : 0); ++si) {
             const SideDesc& sd = sides[si];
             if (sd.species_obs != s) continue;
-            const int tg = (si * n + i) * 2;
+            const int tg = (si * nl + i - g.pt_lo) * 2;
             TaskAcc& G = acc[tg];
             TaskAcc& L = acc[tg + 1];
             combine_task(G);
@@ -782,6 +784,45 @@ __global__ void step_first_kernel(Geometry g, double* logf, const double* __rest
             *dt_dev = dt;
         }
         if (!isfinite(dt)) ts->error = BEST_ERR_NUMERIC;
+    }
+}
+
+// One stage of a step from collision integrals the caller assembled (sharded
+// runs), one CTA of 1024 threads; the same arithmetic as step_first_kernel
+// and heun_correct_kernel with f = exp(log f).
+//   stage 0: dt = min(*dt_dev, eps / max |k1/f|); Euler: log f += dt k1/f,
+//            t += dt; Heun: fstar = exp(log f + dt k1/f); *dt_dev = dt.
+//   stage 1 (Heun): log f += dt/2 (k1/f + k2/fstar), t += dt.
+__global__ void stage_kernel(Geometry g, int heun, int stage, double* logf, const double* __restrict__ k1,
+                             const double* __restrict__ k2, double* fstar, double* t_dev, double* dt_dev,
+                             TimeState* ts) {
+    __shared__ double red[32];
+    const int total = g.n_species * g.n_grid;
+    if (stage == 0) {
+        double mx = 0.0;
+        for (int k = threadIdx.x; k < total; k += blockDim.x) mx = fmax(mx, fabs(k1[k] / exp(logf[k])));
+        mx = block_max(mx, red);
+        double dt = *dt_dev;
+        if (mx > 0.0) dt = fmin(dt, g.eps_dt / mx);
+        for (int k = threadIdx.x; k < total; k += blockDim.x) {
+            const double step = dt * k1[k] / exp(logf[k]);
+            if (heun) fstar[k] = exp(logf[k] + step);
+            else logf[k] += step;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ts->dt = dt;
+            ts->t_step = *t_dev;
+            if (!heun) *t_dev += dt;
+            *dt_dev = dt;
+            if (!isfinite(dt)) ts->error = BEST_ERR_NUMERIC;
+        }
+    } else {
+        const double dt = *dt_dev;
+        for (int k = threadIdx.x; k < total; k += blockDim.x)
+            logf[k] += 0.5 * dt * (k1[k] / exp(logf[k]) + k2[k] / fstar[k]);
+        __syncthreads();
+        if (threadIdx.x == 0) *t_dev += dt;
     }
 }
 

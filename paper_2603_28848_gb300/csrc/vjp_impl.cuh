@@ -190,7 +190,7 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
     Acc<R> acc_m[NI];
     Acc<R> acc_dw;                              // JVP: tangent of w_n
     const int64_t N = td.neval;
-    const uint32_t task = static_cast<uint32_t>(seg.task);
+    const uint32_t task = td.gid;                 // the stream is keyed by the global task id
     const int32_t g1 = static_cast<int32_t>(seg.g1);
     for (int32_t grp = static_cast<int32_t>(seg.g0) + tid; grp < g1; grp += blockDim.x) {
         uint32_t uw[F32 ? SS::kUniforms : 1];

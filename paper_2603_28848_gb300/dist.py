@@ -1,10 +1,13 @@
 """Host logic of multi-process runs (one process per GPU, torchrun).
 
 The collision integral partitions by grid points (independent tasks, the
-paper's MPI design of Sec. 3D), so ranks need no data-path collective:
-bench.py runs an independent replica of the workload on every rank (weak
-scaling) and only reduces its timing.  `shard` is the contiguous,
-budget-balanced partition of grid points a sharded evolution would use.
+paper's MPI design of Sec. 3D).  bench.py runs an independent replica of the
+workload on every rank (weak scaling) and only reduces its timing.  A sharded
+evolution gives each rank the tasks of a contiguous, budget-balanced block of
+grid points (`shard`, a context built with points=(lo, hi)); every C
+evaluation is followed by one exchange, a sum of the ranks' disjoint C slices
+(`sharded_step`), after which every rank applies the same step to its copy of
+the whole distribution.
 """
 import numpy as np
 
@@ -35,3 +38,35 @@ def shard(budgets, rank, world):
     if rank == world - 1:
         hi = len(b)
     return min(lo, len(b)), min(hi, len(b))
+
+
+def all_reduce_sum(t):
+    """In-place sum over the default process group (no-op without one)."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t
+
+
+def sharded_step(col, logf, t_dev, dt_dev, dt_request, method="heun", reduce=all_reduce_sum, buffers=None):
+    """One Euler or Heun step of a sharded run on this rank.
+
+    ``col`` evaluates C on this rank's grid points (zero elsewhere);
+    ``reduce`` sums a tensor over the ranks in place; every rank holds the
+    same ``logf`` (whole grid), ``t_dev`` and ``dt_dev`` (device scalars) and
+    updates them identically.  ``buffers`` (k1, k2, fstar) may be passed to
+    avoid allocations.  Returns the step used."""
+    import torch
+    k1, k2, fstar = buffers if buffers is not None else (torch.empty_like(logf), torch.empty_like(logf),
+                                                           torch.empty_like(logf))
+    heun = method == "heun"
+    dt_dev.fill_(dt_request)
+    col.eval_log(logf, float(t_dev.item()), C=k1)
+    reduce(k1)
+    col.step_stage(1 if heun else 0, 0, logf, k1, t_dev, dt_dev, fstar=fstar if heun else None)
+    dt = float(dt_dev.item())
+    if heun:
+        col.eval(fstar, float(t_dev.item()) + dt, C=k2)
+        reduce(k2)
+        col.step_stage(1, 1, logf, k1, t_dev, dt_dev, k2=k2, fstar=fstar)
+    return dt

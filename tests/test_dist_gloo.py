@@ -55,3 +55,89 @@ def test_shard_covers_and_balances(world):
         assert b == c
     loads = [sum(budgets[a:b]) for a, b in ranges]
     assert max(loads) <= sum(budgets) / world + max(budgets)
+
+
+class _Relaxation:
+    """Stand-in for a shard's collision context on CPU: C_i = -k_i (f_i - g_i)
+    on the shard's grid points, zero elsewhere, and the step stages of
+    best_step_stage restated in torch.  Only the orchestration of
+    dist.sharded_step (evaluate, exchange, identical stages) is under test."""
+
+    def __init__(self, n, lo, hi, eps=0.3):
+        import torch
+        self.k = torch.linspace(0.5, 3.0, n, dtype=torch.float64)
+        self.g = torch.linspace(0.2, 1.0, n, dtype=torch.float64)
+        self.lo, self.hi, self.eps = lo, hi, eps
+
+    def _C(self, f, t, C):
+        C.zero_()
+        sl = slice(self.lo, self.hi)
+        C[sl] = -self.k[sl] * (f[sl] - self.g[sl]) * (1.0 + 0.1 * t)
+        return C, None
+
+    def eval_log(self, logf, t, C):
+        return self._C(logf.exp(), t, C)
+
+    def eval(self, f, t, C):
+        return self._C(f, t, C)
+
+    def step_stage(self, method, stage, logf, k1, t_dev, dt_dev, k2=None, fstar=None):
+        if stage == 0:
+            f = logf.exp()
+            mx = float((k1 / f).abs().max())
+            dt = min(float(dt_dev), self.eps / mx) if mx > 0 else float(dt_dev)
+            if method == 1:
+                fstar.copy_((logf + dt * k1 / f).exp())
+            else:
+                logf.add_(dt * k1 / f)
+                t_dev.add_(dt)
+            dt_dev.fill_(dt)
+        else:
+            logf.add_(0.5 * float(dt_dev) * (k1 / logf.exp() + k2 / fstar))
+            t_dev.add_(float(dt_dev))
+
+
+def _shard_worker(rank, world, port, out, method):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    n = 12
+    lo, hi = bdist.shard([1.0] * n, rank, world)
+    col = _Relaxation(n, lo, hi)
+    logf = torch.linspace(-2.0, 0.5, n, dtype=torch.float64)
+    t = torch.tensor([0.0], dtype=torch.float64)
+    dt = torch.tensor([0.0], dtype=torch.float64)
+    for _ in range(4):
+        bdist.sharded_step(col, logf, t, dt, 0.2, method)
+    out[rank] = (logf.tolist(), float(t))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("method", ["heun", "euler"])
+def test_sharded_steps_on_two_ranks_equal_one_rank(method):
+    import torch
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_shard_worker, args=(r, 2, port, out, method)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=120)
+            assert p.exitcode == 0
+        got = [out[0], out[1]]
+    n = 12
+    col = _Relaxation(n, 0, n)
+    logf = torch.linspace(-2.0, 0.5, n, dtype=torch.float64)
+    t = torch.tensor([0.0], dtype=torch.float64)
+    dt = torch.tensor([0.0], dtype=torch.float64)
+    for _ in range(4):
+        bdist.sharded_step(col, logf, t, dt, 0.2, method, reduce=lambda x: x)
+    for lf, tt in got:
+        assert np.allclose(lf, logf.tolist(), rtol=0, atol=1e-14)
+        assert tt == pytest.approx(float(t), rel=1e-15)
+    assert float(t) > 0.2            # the steps moved time (some were limited by Eq. (16))

@@ -1,0 +1,163 @@
+"""Sharded evaluation emulated on one GPU (disjoint grid-point ranges in
+separate contexts, as the ranks of a multi-GPU run would hold them): a shard
+against the oracle restricted to its points, the shards' C adding up to the
+whole grid's, and Heun steps from the assembled C (best_step_stage) against
+the whole-grid step."""
+import numpy as np
+import pytest
+
+import workloads as W
+from paper_2603_28848_gb300 import dist as bdist
+from tests._helpers import oracle_sweep, side_integrals, task_arrays
+
+pytestmark = pytest.mark.gpu
+
+
+def _f(f0):
+    import torch
+    return torch.tensor(np.ascontiguousarray(f0), dtype=torch.float64, device="cuda")
+
+
+def _budgets(prob):
+    n = prob.grid.n
+    per = np.zeros(n)
+    for p in prob.processes:
+        per += np.asarray(p.neval_per_point if p.neval_per_point is not None else [p.neval] * n, dtype=float)
+    return per
+
+
+def test_shard_matches_oracle_on_its_points():
+    from paper_2603_28848_gb300 import Collision
+    prob, f0 = W.c4_multi_species(n=8, nmin=500, nmax=3000, nitn=2)
+    lo, hi = 3, 7
+    col = Collision(prob, W.PREC_FP64, points=(lo, hi))
+    C, err = col.eval(_f(f0), 2.0)
+    col.check()
+    Co, erro, detail, _ = oracle_sweep(prob, f0, 2.0, "f64", points=range(lo, hi))
+    Cg = C.cpu().numpy()
+    assert np.all(Cg[:, :lo] == 0) and np.all(Cg[:, hi:] == 0)
+    scale = np.max(np.abs(Co[:, lo:hi]))
+    assert np.max(np.abs(Cg - Co)) <= 1e-7 * scale
+    # local task order: side, point in [lo, hi), term
+    mean, _ = col.task_results()
+    n, nl = prob.grid.n, hi - lo
+    # tasks 1e12 below the largest are kinematically suppressed (their weights
+    # underflow differently): compared against that floor, as in the parity tests
+    floor = 1e-12 * max(abs(v[0]) for v in detail.values())
+    for k in range(len(side_integrals(prob))):
+        for i in range(lo, hi):
+            for term in (0, 1):
+                om = detail[(k * n + i) * 2 + term][0]
+                gm = mean[(k * nl + i - lo) * 2 + term]
+                assert abs(gm - om) <= 1e-5 * abs(om) + floor
+    col.close()
+
+
+@pytest.mark.parametrize("precision,rtol", [(W.PREC_FP64, 1e-10), (W.PREC_FP32, 2e-5)])
+def test_shards_add_up_to_the_whole_grid(precision, rtol):
+    from paper_2603_28848_gb300 import Collision
+    prob, f0 = W.c4_multi_species(n=12, nmin=500, nmax=3000, nitn=2)
+    f = _f(f0)
+    whole = Collision(prob, precision)
+    Cw, ew = [x.cpu().numpy() for x in whole.eval(f, 2.0)]
+    Cs = np.zeros_like(Cw)
+    es2 = np.zeros_like(Cw)
+    for r in range(3):
+        lo, hi = bdist.shard(_budgets(prob), r, 3)
+        col = Collision(prob, precision, points=(lo, hi))
+        C, e = [x.cpu().numpy() for x in col.eval(f, 2.0)]
+        Cs += C
+        es2 += e * e
+        col.close()
+    scale = np.max(np.abs(Cw))
+    assert np.max(np.abs(Cs - Cw)) <= rtol * scale
+    assert np.allclose(np.sqrt(es2), ew, rtol=max(rtol, 1e-9) * 100, atol=0)
+    whole.close()
+
+
+def test_staged_heun_equals_the_fused_step():
+    """On a whole-grid context, dist.sharded_step (evaluate, no exchange,
+    stages) reproduces best_step_heun."""
+    import torch
+    from paper_2603_28848_gb300 import Collision
+    prob, f0 = W.c1_maxwell_2to2(n=16, neval=4000, nitn=2)
+    out = []
+    for staged in (False, True):
+        col = Collision(prob, W.PREC_FP64)
+        logf = torch.log(_f(f0)).contiguous()
+        t = torch.tensor([1.0], dtype=torch.float64, device="cuda")
+        dt = torch.tensor([0.0], dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            if staged:
+                bdist.sharded_step(col, logf, t, dt, 0.05, "heun", reduce=lambda x: x)
+            else:
+                dt.fill_(0.05)
+                col.step_heun(logf, t, dt)
+        torch.cuda.synchronize()
+        out.append((logf.cpu().numpy(), float(t.item())))
+        col.close()
+    assert np.max(np.abs(out[0][0] - out[1][0])) <= 1e-12
+    assert out[0][1] == pytest.approx(out[1][1], rel=1e-15)
+
+
+@pytest.mark.parametrize("method", ["heun", "euler"])
+def test_emulated_two_shard_evolution_equals_whole_grid(method):
+    """Two shard contexts, each with its own copy of log f; after every
+    evaluation their C are summed (the exchange) and both apply the stage:
+    the copies stay identical and equal the whole grid's evolution."""
+    import torch
+    from paper_2603_28848_gb300 import Collision
+    prob, f0 = W.c4_multi_species(n=10, nmin=600, nmax=2000, nitn=2)
+    heun = method == "heun"
+    m = 1 if heun else 0
+    ranges = [bdist.shard(_budgets(prob), r, 2) for r in range(2)]
+    shards = [Collision(prob, W.PREC_FP64, points=r) for r in ranges]
+    whole = Collision(prob, W.PREC_FP64)
+    state = []
+    for _ in range(3):
+        state.append({"logf": torch.log(_f(f0)).contiguous(),
+                      "t": torch.tensor([2.0], dtype=torch.float64, device="cuda"),
+                      "dt": torch.tensor([0.0], dtype=torch.float64, device="cuda"),
+                      "k1": torch.zeros_like(_f(f0)), "k2": torch.zeros_like(_f(f0)),
+                      "fs": torch.zeros_like(_f(f0))})
+    for _ in range(3):
+        # whole grid (third state) through the same stages
+        w = state[2]
+        bdist.sharded_step(whole, w["logf"], w["t"], w["dt"], 0.5, method, reduce=lambda x: x,
+                           buffers=(w["k1"], w["k2"], w["fs"]))
+        # the two shards with an emulated exchange
+        for s in state[:2]:
+            s["dt"].fill_(0.5)
+        parts = [col.eval_log(s["logf"], float(s["t"].item()))[0] for col, s in zip(shards, state)]
+        k1 = parts[0] + parts[1]
+        for col, s in zip(shards, state):
+            s["k1"].copy_(k1)
+            col.step_stage(m, 0, s["logf"], s["k1"], s["t"], s["dt"], fstar=s["fs"] if heun else None)
+        if heun:
+            parts = [col.eval(s["fs"], float(s["t"].item()) + float(s["dt"].item()))[0]
+                     for col, s in zip(shards, state)]
+            k2 = parts[0] + parts[1]
+            for col, s in zip(shards, state):
+                s["k2"].copy_(k2)
+                col.step_stage(1, 1, s["logf"], s["k1"], s["t"], s["dt"], k2=s["k2"], fstar=s["fs"])
+    torch.cuda.synchronize()
+    a, b, w = (s["logf"].cpu().numpy() for s in state)
+    assert np.array_equal(a, b)
+    # the shards' and the whole grid's work partitions sum segment records in
+    # different orders; VEGAS refinement amplifies those last-bit differences
+    # over the 12 refinements of three Heun steps (as in the map parity tests)
+    assert np.max(np.abs(a - w)) <= 1e-6
+    assert float(state[0]["t"].item()) == pytest.approx(float(state[2]["t"].item()), rel=1e-8)   # dt from max|C/f|
+    assert np.max(np.abs(w - np.log(f0))) > 1e-6           # the distribution moved
+    for col in shards + [whole]:
+        col.close()
+
+
+def test_adaptive_width_is_rejected_in_a_shard():
+    from dataclasses import replace
+    from paper_2603_28848_gb300 import BestError, Collision
+    prob, f0 = W.c1_maxwell_2to2(n=8, neval=1000, nitn=1)
+    prob = replace(prob, processes=tuple(replace(p, width_mode=W.WIDTH_ADAPTIVE) for p in prob.processes))
+    with pytest.raises(BestError):
+        Collision(prob, W.PREC_FP32, points=(0, 4))
+    Collision(prob, W.PREC_FP32, points=(0, 8)).close()      # the whole grid is not a shard
