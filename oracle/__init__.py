@@ -13,6 +13,11 @@ Modules (each function cites the passage of the paper it restates):
   collision    the Monte Carlo integrand and C_a(p_i) (Sec. 2B-2D, App. A)
   step         log-space Euler / Heun with adaptive dt (Sec. 3C)
   reference    independent exact-energy reductions used as pins (Sec. 4, App. B)
+  width        fractional Gaussian width and its error-threshold controller (App. C)
+  stratified   adaptive stratified sampling on top of the map (the vegas library's default)
+  moments      number and energy densities for conservation checks (Sec. 5C)
+  adjoint      the fixed-sample integral as a torch function; its reverse and forward derivatives
+  implicit     backward-Euler log-space step by dense-Jacobian Newton
 
 Parity pins live in ``tests/test_oracle_*.py``.  Items without an external
 pin are marked "parity unpinned" in their docstrings.
