@@ -352,7 +352,10 @@ int64_t best_sweep_samples(const best_ctx* ctx, int32_t iteration);
  * estimate of task t and its standard error.  Task numbering:
  * t = (side_integral * n_grid + grid_point) * 2 + term, term 0 = gain,
  * 1 = loss; side integrals ordered by process, side (initial first), then
- * observed species.  Either pointer may be NULL.
+ * observed species.  In a shard (config.point_lo/point_hi) the numbering is
+ * t = (side_integral * (point_hi - point_lo) + grid_point - point_lo) * 2 +
+ * term; the same numbering indexes maps, strata and the state blob.  Either
+ * pointer may be NULL.
  */
 best_status best_get_task_results(best_ctx* ctx, double* mean, double* err, void* stream);
 
