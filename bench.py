@@ -62,6 +62,7 @@ def mufu_per_sample(n_legs):
 
 NEVAL = None      # per-task samples per iteration; None = the workload's own
 WORKLOAD_KEY = "c2"
+STRAT = False     # stratified sampling (VEGAS+) in every process
 # per workload: (builder, integrator, requested dt, start time, description)
 WORKLOADS = {
     "c1": ("c1_maxwell_2to2", "euler", 0.1, 0.0,
@@ -80,6 +81,14 @@ WORKLOADS = {
 
 
 def workload():
+    prob, f0 = _workload()
+    if STRAT:
+        from dataclasses import replace
+        prob = replace(prob, processes=tuple(replace(p, strat=1) for p in prob.processes))
+    return prob, f0
+
+
+def _workload():
     import workloads as W
     name = WORKLOADS[WORKLOAD_KEY][0]
     fn = getattr(W, name)
@@ -357,7 +366,7 @@ def run_native(args, rank, world):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded; BE(T=1) + Gaussian bump, no dataset)",
-        "config": {"workload": f"{wl[0]}: {wl[4]}",
+        "config": {"workload": f"{wl[0]}: {wl[4]}" + (" + stratified sampling (VEGAS+)" if STRAT else ""),
                    "grid_points": prob.grid.n, "tasks": col_tasks, "neval": prob.processes[0].neval,
                    "nitn": prob.processes[0].nitn,
                    "step": f"one {method} step = {sweeps_per_step} sweep(s)", "l2": "flushed between steps "
@@ -457,9 +466,11 @@ def main():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--vjp", action="store_true", help="also time the adjoint")
     ap.add_argument("--implicit", action="store_true", help="also time the tangent and one implicit Euler step")
+    ap.add_argument("--strat", action="store_true", help="adaptive stratified sampling (VEGAS+) in every process")
     args = ap.parse_args()
-    global NEVAL, WORKLOAD_KEY
+    global NEVAL, WORKLOAD_KEY, STRAT
     NEVAL = args.neval
+    STRAT = args.strat
     WORKLOAD_KEY = args.workload
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
