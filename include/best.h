@@ -51,6 +51,7 @@ typedef enum { BEST_FP64 = 0, BEST_FP32 = 1 } best_precision;
 #define BEST_MAX_LEGS 6        /* n_total <= 6: up to 12 VEGAS dimensions */
 #define BEST_MAX_SPECIES 8
 #define BEST_MAX_PROCESSES 16
+#define BEST_MAX_MASS_KNOTS 8
 
 /* Comoving momentum grid shared by all species (Sec. 3A): n points over
  * [q_min, q_max], logarithmic (log_spaced != 0) or linear; 4 <= n <= 4096. */
@@ -60,11 +61,17 @@ typedef struct {
     double q_min, q_max;
 } best_grid;
 
-/* A species: statistics and mass m(t) = mass0 + mass1 * t (Sec. 3A). */
+/* A species: statistics and mass m(t) (Sec. 3A): m(t) = mass0 + mass1 * t,
+ * or, with 2 <= n_mass_knots <= BEST_MAX_MASS_KNOTS, the piecewise-linear
+ * interpolation of (mass_t[k], mass_m[k]) (mass_t strictly increasing, masses
+ * >= 0), constant before the first and after the last knot; a step in the
+ * mass (the paper's example of a phase transition) is a steep ramp between two
+ * close knots. */
 typedef struct {
     int32_t stat;          /* best_stat */
-    int32_t pad_;
+    int32_t n_mass_knots;  /* 0: the linear law */
     double mass0, mass1;
+    double mass_t[BEST_MAX_MASS_KNOTS], mass_m[BEST_MAX_MASS_KNOTS];
 } best_species;
 
 /* Matrix element.  The paper registers |M|^2 as a callable of the momenta
@@ -337,6 +344,12 @@ best_status best_get_strata(best_ctx* ctx, int32_t task, int32_t* M, int32_t* H,
  */
 best_status best_get_widths(best_ctx* ctx, double* w, double* rel);
 best_status best_set_widths(best_ctx* ctx, const double* w);
+
+/* The species' masses m_s(t) at time t (Sec. 3A), by the formula the
+ * kernels use (equal to theirs up to rounding): m (caller-owned host array of
+ * n_species) receives them.  No device work.  BEST_ERR_INVALID when ctx or m is NULL or t is
+ * not finite. */
+best_status best_species_masses(const best_ctx* ctx, double t, double* m);
 
 /* Context geometry. */
 int32_t best_num_tasks(const best_ctx* ctx);

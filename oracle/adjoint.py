@@ -20,7 +20,7 @@ import torch
 from scipy.interpolate import CubicSpline
 
 from . import philox, vegas, width as owidth
-from .collision import TWO_PI, grid_q, scale_factor, task_budget
+from .collision import TWO_PI, grid_q, masses, scale_factor, task_budget
 from .spline import ETA
 from .tasks import SIDE_IN, side_integrals, task_id
 
@@ -184,7 +184,7 @@ def _integrand(problem, si, term, i, f, dists, masses, coupling, a, y, q, w_frac
 def vjp(problem, f0, t, v, maps, call, mode="f64", widths=None):
     """(C~, dL/df, dL/dm, dL/dcoupling) for L = sum(v * C~)."""
     f = torch.tensor(np.asarray(f0, dtype=np.float64), requires_grad=True)
-    m = torch.tensor([s.mass0 + s.mass1 * t for s in problem.species], dtype=torch.float64, requires_grad=True)
+    m = torch.tensor(masses(problem, t), dtype=torch.float64, requires_grad=True)
     lam = torch.tensor([p.coupling for p in problem.processes], dtype=torch.float64, requires_grad=True)
     C = fixed_sample_C(problem, f, m, lam, t, maps, call, mode, widths)
     Lv = (C * torch.tensor(np.asarray(v, dtype=np.float64))).sum()
@@ -197,7 +197,7 @@ def jvp(problem, f0, t, u, maps, call, mode="f64", widths=None):
     """(C~, J u) with J = dC~/df at fixed masses and couplings: the
     directional derivative of ``fixed_sample_C`` along u (forward mode, by
     torch's double-backward construction)."""
-    m = torch.tensor([s.mass0 + s.mass1 * t for s in problem.species], dtype=torch.float64)
+    m = torch.tensor(masses(problem, t), dtype=torch.float64)
     lam = torch.tensor([p.coupling for p in problem.processes], dtype=torch.float64)
     f = torch.tensor(np.asarray(f0, dtype=np.float64))
     ut = torch.tensor(np.asarray(u, dtype=np.float64))

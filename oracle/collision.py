@@ -63,9 +63,24 @@ def scale_factor(problem, t):
     return problem.expansion.a0 * np.sqrt(t / problem.expansion.t0)
 
 
+def mass_of(species, t):
+    """m(t) of one species (time-dependent mass, Sec. 3A): mass0 + mass1 t,
+    or, when the species carries a knot table, the straight line between the
+    two knots around t, and the end knot's mass beyond either end."""
+    tab = species.mass_table
+    if tab is None:
+        return species.mass0 + species.mass1 * t
+    if t <= tab[0][0]:
+        return tab[0][1]
+    for (ta, ma), (tb, mb) in zip(tab[:-1], tab[1:]):
+        if t <= tb:
+            return ma + (mb - ma) * ((t - ta) / (tb - ta))
+    return tab[-1][1]
+
+
 def masses(problem, t):
-    """m_s(t) = mass0 + mass1 t per species (time-dependent mass, Sec. 3A)."""
-    return np.array([s.mass0 + s.mass1 * t for s in problem.species])
+    """m_s(t) per species."""
+    return np.array([mass_of(s, t) for s in problem.species])
 
 
 def distributions(problem, f, t):

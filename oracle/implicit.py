@@ -18,6 +18,7 @@ import numpy as np
 import torch
 
 from . import adjoint
+from .collision import masses
 
 
 def newton(residual, jacobian, g0, tol, max_iter=50):
@@ -55,7 +56,7 @@ def collision_step(problem, logf, t, dt, maps, call, tol=1e-12, mode="f64"):
     iterations, ||R||_inf)."""
     shape = np.shape(logf)
     t1 = t + dt
-    m = torch.tensor([s.mass0 + s.mass1 * t1 for s in problem.species], dtype=torch.float64)
+    m = torch.tensor(masses(problem, t1), dtype=torch.float64)
     lam = torch.tensor([p.coupling for p in problem.processes], dtype=torch.float64)
 
     def C_of(g):

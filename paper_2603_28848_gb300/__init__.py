@@ -31,6 +31,14 @@ def config_from_problem(problem, precision):
         sp[k].stat = int(s.stat)
         sp[k].mass0 = float(s.mass0)
         sp[k].mass1 = float(s.mass1)
+        tab = getattr(s, "mass_table", None)
+        if tab is not None:
+            if not 2 <= len(tab) <= _lib.MAX_MASS_KNOTS:
+                raise BestError(f"species {s.name}: a mass table needs 2..{_lib.MAX_MASS_KNOTS} knots")
+            sp[k].n_mass_knots = len(tab)
+            for j, (tj, mj) in enumerate(tab):
+                sp[k].mass_t[j] = float(tj)
+                sp[k].mass_m[j] = float(mj)
     pr = (_lib.best_process * len(problem.processes))()
     for k, p in enumerate(problem.processes):
         legs = tuple(p.species_in) + tuple(p.species_out)
@@ -270,6 +278,12 @@ class Collision:
               self.ctx)
         return M.value, H.value, m
 
+    def species_masses(self, t):
+        """m_s(t) of every species as the library evaluates it (numpy)."""
+        m = (ctypes.c_double * self.n_species)()
+        check(self.lib.best_species_masses(self.ctx, float(t), m), self.ctx)
+        return np.array(m[:])
+
     def widths(self):
         """(w, rel): the fractional Gaussian width of every process as the
         next evaluation uses it, and the relative error that last set it."""
@@ -395,7 +409,7 @@ def fixed_sample_collision(col, f, t=0.0, masses=None, couplings=None):
     if _FSC is None:
         _FSC = _autograd_function()
     prob = col.problem
-    m_now = torch.tensor([s.mass0 + s.mass1 * t for s in prob.species], dtype=torch.float64, device=f.device)
+    m_now = torch.tensor(col.species_masses(t), dtype=torch.float64, device=f.device)
     lam_now = torch.tensor([p.coupling for p in prob.processes], dtype=torch.float64, device=f.device)
     if masses is None:
         masses = m_now

@@ -16,8 +16,12 @@ class best_grid(ctypes.Structure):
     _fields_ = [("n", c_int32), ("log_spaced", c_int32), ("q_min", c_double), ("q_max", c_double)]
 
 
+MAX_MASS_KNOTS = 8
+
+
 class best_species(ctypes.Structure):
-    _fields_ = [("stat", c_int32), ("pad_", c_int32), ("mass0", c_double), ("mass1", c_double)]
+    _fields_ = [("stat", c_int32), ("n_mass_knots", c_int32), ("mass0", c_double), ("mass1", c_double),
+                ("mass_t", c_double * MAX_MASS_KNOTS), ("mass_m", c_double * MAX_MASS_KNOTS)]
 
 
 class best_process(ctypes.Structure):
@@ -62,6 +66,7 @@ SIGNATURES = {
     "best_moments": ([c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p], c_int32),
     "best_get_strata": ([c_void_p, c_int32, POINTER(c_int32), POINTER(c_int32), c_void_p], c_int32),
     "best_get_widths": ([c_void_p, c_void_p, c_void_p], c_int32),
+    "best_species_masses": ([c_void_p, c_double, c_void_p], c_int32),
     "best_set_widths": ([c_void_p, c_void_p], c_int32),
     "best_state_size": ([c_void_p], c_int64),
     "best_save_state": ([c_void_p, c_void_p, c_int64], c_int32),

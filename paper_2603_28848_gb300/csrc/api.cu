@@ -16,7 +16,7 @@
 
 namespace best {
 // kernels.cu
-__global__ void set_time_kernel(Geometry, TimeState*, const double*, double, int, const double*, const double*);
+__global__ void set_time_kernel(Geometry, TimeState*, const double*, double, int, const MassLaw*);
 __global__ void spline_build_kernel(Geometry, const double*, int, const double*, TimeState*, SpeciesConst*,
                                     double*, double*, float*);
 __global__ void prepare_kernel(Geometry, const SideDesc*, const TaskDesc*, const double*, const double*,
@@ -125,8 +125,8 @@ struct best_ctx {
     double* d_coef64 = nullptr;
     float* d_coef32 = nullptr;
     double* d_fgrid = nullptr;
-    double* d_mass0 = nullptr;
-    double* d_mass1 = nullptr;
+    MassLaw* d_mass_law = nullptr;  // [species]
+    std::vector<MassLaw> mass_law;
     double* d_partials = nullptr;
     double* d_k1 = nullptr;
     double* d_k2 = nullptr;
@@ -226,7 +226,7 @@ void free_all(best_ctx* c) {
     }
     c->plans.clear();
     void* bufs[] = {c->d_sides, c->d_tasks, c->d_tconst, c->d_acc, c->d_sconst, c->d_ts, c->d_edges,
-                    c->d_knots, c->d_knots32, c->d_coef64, c->d_coef32, c->d_fgrid, c->d_mass0, c->d_mass1,
+                    c->d_knots, c->d_knots32, c->d_coef64, c->d_coef32, c->d_fgrid, c->d_mass_law,
                     c->d_partials, c->d_k1, c->d_k2, c->d_fstar, c->d_prev, c->d_dtreq,
                     c->d_gcoef, c->d_vjp_tot, c->d_u, c->d_gtail, c->d_coupling, c->d_dcoef64,
                     c->d_dcoef32, c->d_dtail, c->d_nk, c->d_width, c->d_width_rel, c->d_wctl,
@@ -259,6 +259,17 @@ best_status validate(const best_config* cfg) {
         if (sp.stat < 0 || sp.stat > 2) return fail(ctx, BEST_ERR_INVALID, "species %d: bad stat", s);
         if (!std::isfinite(sp.mass0) || !std::isfinite(sp.mass1))
             return fail(ctx, BEST_ERR_INVALID, "species %d: bad mass", s);
+        if (sp.n_mass_knots != 0) {
+            if (sp.n_mass_knots < 2 || sp.n_mass_knots > BEST_MAX_MASS_KNOTS)
+                return fail(ctx, BEST_ERR_INVALID, "species %d: n_mass_knots must be 0 or in [2, %d]", s,
+                            BEST_MAX_MASS_KNOTS);
+            for (int k = 0; k < sp.n_mass_knots; ++k) {
+                if (!std::isfinite(sp.mass_t[k]) || !std::isfinite(sp.mass_m[k]) || sp.mass_m[k] < 0.0 ||
+                    (k > 0 && !(sp.mass_t[k] > sp.mass_t[k - 1])))
+                    return fail(ctx, BEST_ERR_INVALID, "species %d: mass knots need increasing finite times and "
+                                "finite masses >= 0", s);
+            }
+        }
     }
     if (cfg->point_hi != 0 && !(cfg->point_lo >= 0 && cfg->point_lo < cfg->point_hi && cfg->point_hi <= g.n))
         return fail(ctx, BEST_ERR_INVALID, "shard: need 0 <= point_lo < point_hi <= grid.n (or both 0)");
@@ -779,13 +790,19 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     knots[n - 1] = g.q_max;
     std::vector<float> knots32(knots.begin(), knots.end());
     std::vector<SpeciesConst> sconst(S);
-    std::vector<double> m0(S), m1(S);
+    ctx->mass_law.assign(S, MassLaw{});
     for (int s = 0; s < S; ++s) {
         sconst[s] = SpeciesConst{};
         sconst[s].stat = cfg->species[s].stat;
         sconst[s].eta = cfg->species[s].stat == BEST_BE ? 1.0 : (cfg->species[s].stat == BEST_FD ? -1.0 : 0.0);
-        m0[s] = cfg->species[s].mass0;
-        m1[s] = cfg->species[s].mass1;
+        MassLaw& L = ctx->mass_law[s];
+        L.m0 = cfg->species[s].mass0;
+        L.m1 = cfg->species[s].mass1;
+        L.n = cfg->species[s].n_mass_knots;
+        for (int k = 0; k < L.n; ++k) {
+            L.t[k] = cfg->species[s].mass_t[k];
+            L.m[k] = cfg->species[s].mass_m[k];
+        }
     }
     std::vector<double> edges(static_cast<size_t>(T) * g.map_stride, 0.0);
     for (int t = 0; t < T; ++t) {
@@ -810,8 +827,7 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     CKI(dalloc(&ctx->d_coef64, static_cast<size_t>(S) * (n - 1) * 4));
     CKI(dalloc(&ctx->d_coef32, static_cast<size_t>(S) * (n - 1) * 4));
     CKI(dalloc(&ctx->d_fgrid, static_cast<size_t>(S) * n));
-    CKI(dalloc(&ctx->d_mass0, S));
-    CKI(dalloc(&ctx->d_mass1, S));
+    CKI(dalloc(&ctx->d_mass_law, S));
     CKI(dalloc(&ctx->d_k1, static_cast<size_t>(S) * n));
     CKI(dalloc(&ctx->d_k2, static_cast<size_t>(S) * n));
     CKI(dalloc(&ctx->d_fstar, static_cast<size_t>(S) * n));
@@ -866,8 +882,7 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     CKI(cudaMemcpy(ctx->d_edges, edges.data(), edges.size() * sizeof(double), cudaMemcpyHostToDevice));
     CKI(cudaMemcpy(ctx->d_knots, knots.data(), n * sizeof(double), cudaMemcpyHostToDevice));
     CKI(cudaMemcpy(ctx->d_knots32, knots32.data(), n * sizeof(float), cudaMemcpyHostToDevice));
-    CKI(cudaMemcpy(ctx->d_mass0, m0.data(), S * sizeof(double), cudaMemcpyHostToDevice));
-    CKI(cudaMemcpy(ctx->d_mass1, m1.data(), S * sizeof(double), cudaMemcpyHostToDevice));
+    CKI(cudaMemcpy(ctx->d_mass_law, ctx->mass_law.data(), S * sizeof(MassLaw), cudaMemcpyHostToDevice));
     CKI(dalloc(&ctx->d_strat_est, static_cast<size_t>(T) * 4));
     CKI(cudaMemset(ctx->d_strat_est, 0, sizeof(double) * 4 * T));
     if (ctx->any_strat) {
@@ -896,7 +911,7 @@ best_status best_collision_eval(best_ctx* ctx, const double* f_dev, double t, do
     if (!std::isfinite(t)) return fail(ctx, BEST_ERR_INVALID, "t must be finite");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     ctx->launches = 0;
-    set_time_kernel<<<1, 32, 0, st>>>(ctx->geo, ctx->d_ts, nullptr, t, 0, ctx->d_mass0, ctx->d_mass1);
+    set_time_kernel<<<1, 32, 0, st>>>(ctx->geo, ctx->d_ts, nullptr, t, 0, ctx->d_mass_law);
     ctx->launches += 1;
     return enqueue_sweep(ctx, f_dev, 0, C_dev, err_dev, st);
 }
@@ -908,7 +923,7 @@ best_status best_collision_eval_log(best_ctx* ctx, const double* logf_dev, doubl
     if (!std::isfinite(t)) return fail(ctx, BEST_ERR_INVALID, "t must be finite");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     ctx->launches = 0;
-    set_time_kernel<<<1, 32, 0, st>>>(ctx->geo, ctx->d_ts, nullptr, t, 0, ctx->d_mass0, ctx->d_mass1);
+    set_time_kernel<<<1, 32, 0, st>>>(ctx->geo, ctx->d_ts, nullptr, t, 0, ctx->d_mass_law);
     ctx->launches += 1;
     return enqueue_sweep(ctx, logf_dev, 1, C_dev, err_dev, st);
 }
@@ -937,7 +952,7 @@ static best_status step_common(best_ctx* ctx, double* logf, double* t_dev, doubl
     const Geometry& g = ctx->geo;
     ctx->launches = 0;
     double* k1 = C_dev ? C_dev : ctx->d_k1;
-    set_time_kernel<<<1, 32, 0, st>>>(g, ctx->d_ts, t_dev, 0.0, 1, ctx->d_mass0, ctx->d_mass1);
+    set_time_kernel<<<1, 32, 0, st>>>(g, ctx->d_ts, t_dev, 0.0, 1, ctx->d_mass_law);
     ctx->launches += 1;
     best_status s = enqueue_sweep(ctx, logf, 1, k1, nullptr, st);
     if (s != BEST_OK) return s;
@@ -945,7 +960,7 @@ static best_status step_common(best_ctx* ctx, double* logf, double* t_dev, doubl
                                           heun ? 1 : 0);
     ctx->launches += 1;
     if (heun) {
-        set_time_kernel<<<1, 32, 0, st>>>(g, ctx->d_ts, t_dev, 0.0, 2, ctx->d_mass0, ctx->d_mass1);
+        set_time_kernel<<<1, 32, 0, st>>>(g, ctx->d_ts, t_dev, 0.0, 2, ctx->d_mass_law);
         ctx->launches += 1;
         s = enqueue_sweep(ctx, ctx->d_fstar, 0, ctx->d_k2, nullptr, st);
         if (s != BEST_OK) return s;
@@ -1095,7 +1110,7 @@ best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, con
         CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(ctx->vjp_smem)));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     ctx->launches = 0;
-    set_time_kernel<<<1, 32, 0, st>>>(g, ctx->d_ts, nullptr, t, 0, ctx->d_mass0, ctx->d_mass1);
+    set_time_kernel<<<1, 32, 0, st>>>(g, ctx->d_ts, nullptr, t, 0, ctx->d_mass_law);
     spline_build_kernel<<<g.n_species, 256, ctx->spline_smem, st>>>(
         g, f_dev, 0, ctx->d_knots, ctx->d_ts, ctx->d_sconst, ctx->d_fgrid, ctx->d_coef64, ctx->d_coef32);
     prepare_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_knots, ctx->d_fgrid,
@@ -1193,7 +1208,7 @@ static best_status enqueue_jvp(best_ctx* ctx, const double* f_dev, double t, con
         ctx->jvp_ready = true;
     }
     if (setup) {
-        set_time_kernel<<<1, 32, 0, st>>>(g, ctx->d_ts, nullptr, t, 0, ctx->d_mass0, ctx->d_mass1);
+        set_time_kernel<<<1, 32, 0, st>>>(g, ctx->d_ts, nullptr, t, 0, ctx->d_mass_law);
         spline_build_kernel<<<g.n_species, 256, ctx->spline_smem, st>>>(
             g, f_dev, 0, ctx->d_knots, ctx->d_ts, ctx->d_sconst, ctx->d_fgrid, ctx->d_coef64, ctx->d_coef32);
         prepare_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_knots,
@@ -1306,7 +1321,7 @@ best_status best_step_implicit_euler(best_ctx* ctx, double* logf_dev, double t, 
     const double t1 = t + dt;
 
     if (train) {
-        set_time_kernel<<<1, 32, 0, st>>>(g, ctx->d_ts, nullptr, t1, 0, ctx->d_mass0, ctx->d_mass1);
+        set_time_kernel<<<1, 32, 0, st>>>(g, ctx->d_ts, nullptr, t1, 0, ctx->d_mass_law);
         ctx->launches += 1;
         s = enqueue_sweep(ctx, logf_dev, 1, ctx->d_k1, nullptr, st);
         if (s != BEST_OK) return s;
@@ -1457,7 +1472,7 @@ best_status best_moments(best_ctx* ctx, const double* f_dev, double t, double* n
     if (!std::isfinite(t)) return fail(ctx, BEST_ERR_INVALID, "t must be finite");
     const Geometry& g = ctx->geo;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    set_time_kernel<<<1, 32, 0, st>>>(g, ctx->d_ts, nullptr, t, 0, ctx->d_mass0, ctx->d_mass1);
+    set_time_kernel<<<1, 32, 0, st>>>(g, ctx->d_ts, nullptr, t, 0, ctx->d_mass_law);
     spline_build_kernel<<<g.n_species, 256, ctx->spline_smem, st>>>(
         g, f_dev, 0, ctx->d_knots, ctx->d_ts, ctx->d_sconst, ctx->d_fgrid, ctx->d_coef64, ctx->d_coef32);
     moments_kernel<<<g.n_species, 256, 0, st>>>(g, ctx->d_knots, ctx->d_coef64, ctx->d_ts, n_dev, rho_dev);
@@ -1476,6 +1491,13 @@ best_status best_get_strata(best_ctx* ctx, int32_t task, int32_t* M, int32_t* H,
         CK(cudaDeviceSynchronize());
         CK(cudaMemcpy(m, ctx->d_strat_m + td.strat_off_h, td.strat_H * sizeof(int32_t), cudaMemcpyDeviceToHost));
     }
+    return BEST_OK;
+}
+
+best_status best_species_masses(const best_ctx* ctx, double t, double* m) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    if (!m || !std::isfinite(t)) return fail(const_cast<best_ctx*>(ctx), BEST_ERR_INVALID, "need m and a finite t");
+    for (size_t s = 0; s < ctx->mass_law.size(); ++s) m[s] = mass_at(ctx->mass_law[s], t);
     return BEST_OK;
 }
 

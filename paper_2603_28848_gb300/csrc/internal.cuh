@@ -71,6 +71,24 @@ struct TaskConst {
     double wfrac;           // fractional width w of App. C this sweep (0: absolute sigma_E)
 };
 
+// Mass law of one species: m(t) = m0 + m1 t, or with n >= 2 knots the
+// piecewise-linear interpolation of (t[k], m[k]) (t increasing), constant
+// beyond the first and last knot.
+struct MassLaw {
+    double m0, m1;
+    int32_t n;
+    int32_t pad_;
+    double t[BEST_MAX_MASS_KNOTS], m[BEST_MAX_MASS_KNOTS];
+};
+
+__host__ __device__ inline double mass_at(const MassLaw& L, double t) {
+    if (L.n < 2) return L.m0 + L.m1 * t;
+    if (t <= L.t[0]) return L.m[0];
+    for (int k = 1; k < L.n; ++k)
+        if (t <= L.t[k]) return L.m[k - 1] + (L.m[k] - L.m[k - 1]) * ((t - L.t[k - 1]) / (L.t[k] - L.t[k - 1]));
+    return L.m[L.n - 1];
+}
+
 // Width controller of one process (App. C).
 struct WidthCtl {
     int32_t mode;           // width_mode of the process

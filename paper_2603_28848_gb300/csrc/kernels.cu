@@ -13,7 +13,7 @@ namespace best {
 // mode 0: t = t_host; mode 1: t = *t_dev; mode 2: t = *t_dev + state dt.
 // ---------------------------------------------------------------------------
 __global__ void set_time_kernel(Geometry g, TimeState* ts, const double* t_dev, double t_host,
-                                int mode, const double* mass0, const double* mass1) {
+                                int mode, const MassLaw* law) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double t = t_host;
     if (mode == 1) t = *t_dev;
@@ -21,7 +21,7 @@ __global__ void set_time_kernel(Geometry g, TimeState* ts, const double* t_dev, 
     ts->t = t;
     ts->a = g.expansion ? g.a0 * sqrt(t / g.t0) : 1.0;
     if (!(ts->a > 0.0) || !isfinite(ts->a)) ts->error = BEST_ERR_NUMERIC;
-    for (int s = 0; s < g.n_species; ++s) ts->mass[s] = mass0[s] + mass1[s] * t;
+    for (int s = 0; s < g.n_species; ++s) ts->mass[s] = mass_at(law[s], t);
 }
 
 // Second derivatives M_j of the not-a-knot cubic spline through (q_j, f_j):

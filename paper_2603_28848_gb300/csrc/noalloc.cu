@@ -223,7 +223,16 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     if (!(A.ts.a > 0.0)) return report(BEST_ERR_INVALID, "noalloc: a(t) must be positive");
     A.ts.call = call;
     for (int s = 0; s < S; ++s) {
-        A.ts.mass[s] = cfg->species[s].mass0 + cfg->species[s].mass1 * t;
+        const best_species& sp = cfg->species[s];
+        MassLaw L{};
+        L.m0 = sp.mass0;
+        L.m1 = sp.mass1;
+        L.n = sp.n_mass_knots;
+        for (int k = 0; k < L.n && k < BEST_MAX_MASS_KNOTS; ++k) {
+            L.t[k] = sp.mass_t[k];
+            L.m[k] = sp.mass_m[k];
+        }
+        A.ts.mass[s] = mass_at(L, t);
         A.sc[s].stat = cfg->species[s].stat;
         A.sc[s].eta = cfg->species[s].stat == BEST_BE ? 1.0 : (cfg->species[s].stat == BEST_FD ? -1.0 : 0.0);
     }

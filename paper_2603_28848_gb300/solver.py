@@ -15,7 +15,9 @@ It only assembles a ``workloads.Problem`` and sequences libbest calls
 Differences from the paper's interface, by necessity of running on the GPU:
 the matrix element is |M|^2 = coupling^2 P(s) with P a cubic in the initial
 state's invariant mass squared (``me_coef``), not a Python callable; a mass
-may depend on time linearly (``set_mass_linear``), not through a callable.
+may depend on time linearly (``set_mass_linear``) or piecewise linearly
+through up to eight knots (``set_mass_table``); ``set_mass_func`` samples a
+callable at given times into such a table.
 """
 import numpy as np
 
@@ -68,6 +70,26 @@ class Solver:
         n, sp, f = self._species[k]
         self._species[k] = (n, W.Species(n, sp.stat, float(mass), float(slope)), f)
         self._invalidate()
+
+    def set_mass_table(self, name, times, masses):
+        """m(t) of a registered species as the straight lines through the knots
+        (times[k], masses[k]) (2..8 knots, times increasing), constant
+        beyond either end."""
+        t = [float(x) for x in times]
+        m = [float(x) for x in masses]
+        if not 2 <= len(t) <= W.MAX_MASS_KNOTS or len(m) != len(t):
+            raise ValueError(f"a mass table needs 2..{W.MAX_MASS_KNOTS} knots and one mass per time")
+        if any(b <= a for a, b in zip(t[:-1], t[1:])) or any(not np.isfinite(x) or x < 0 for x in m):
+            raise ValueError("mass knots need increasing times and finite masses >= 0")
+        k = self._index(name)
+        n, sp, f = self._species[k]
+        self._species[k] = (n, W.Species(n, sp.stat, m[0], 0.0, tuple(zip(t, m))), f)
+        self._invalidate()
+
+    def set_mass_func(self, name, fn, times):
+        """m(t) = fn(t) sampled at ``times`` (2..8 of them) and joined by
+        straight lines."""
+        self.set_mass_table(name, times, [float(fn(float(x))) for x in times])
 
     def add_process(self, name, initial, final, coupling=1.0, neval=10 ** 6, delta_width=0.01, nitn=2,
                     alpha=0.5, nbins=50, me_coef=(1.0, 0.0, 0.0, 0.0), **options):

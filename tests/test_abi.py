@@ -55,11 +55,14 @@ def test_struct_layout_matches_c(tmp_path):
         pytest.skip("gcc missing")
     fields = {
         "best_grid": ["n", "log_spaced", "q_min", "q_max"],
-        "best_species": ["stat", "mass0", "mass1"],
+        "best_species": ["stat", "n_mass_knots", "mass0", "mass1", "mass_t", "mass_m"],
         "best_process": ["n_in", "n_out", "species", "coupling", "sigma_E", "neval", "neval_per_point",
-                         "nitn", "nbins", "alpha"],
+                         "nitn", "nbins", "alpha", "width_mode", "width", "width_rel_lo", "width_rel_hi",
+                         "width_factor", "width_min", "width_max", "strat", "strat_max_hcubes", "strat_beta",
+                         "me_coef"],
         "best_config": ["grid", "n_species", "n_processes", "species", "processes", "precision",
-                        "tail_points", "seed", "e_cut", "expansion", "a0", "t0", "eps_dt"],
+                        "tail_points", "seed", "e_cut", "expansion", "a0", "t0", "eps_dt", "point_lo",
+                        "point_hi"],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for st, fs in fields.items():

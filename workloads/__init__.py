@@ -11,7 +11,8 @@ Problem layout (Sec. 3A of the paper):
   * one comoving momentum grid shared by all species, log or linear spaced
     over [q_min, q_max] with n points;
   * species with a statistics label (MB, BE, FD) and a mass
-    m(t) = mass0 + mass1 * t (the time-dependent mass of Sec. 3A);
+    m(t) = mass0 + mass1 * t or a piecewise-linear table of (t, m) knots
+    (the time-dependent mass of Sec. 3A);
   * processes n_in -> n_out given by species index lists, a constant
     |M|^2 = coupling^2, the Gaussian width sigma_E of Eq. (11) and the VEGAS
     parameters neval (samples per iteration per task), nitn, alpha, nbins;
@@ -45,12 +46,24 @@ class Grid:
     log_spaced: bool = True
 
 
+MAX_MASS_KNOTS = 8
+
+
 @dataclass(frozen=True)
 class Species:
     name: str
     stat: int
     mass0: float
     mass1: float = 0.0          # m(t) = mass0 + mass1 * t
+    # Optional knots ((t_0, m_0), ..., (t_k, m_k)), t increasing, 2..8 of
+    # them: m(t) is then the piecewise-linear interpolant, held constant
+    # outside [t_0, t_k] (mass0 and mass1 are ignored).
+    mass_table: Optional[Tuple[Tuple[float, float], ...]] = None
+
+    def __post_init__(self):
+        if self.mass_table is not None:
+            tab = tuple((float(a), float(b)) for a, b in self.mass_table)
+            object.__setattr__(self, "mass_table", tab)
 
 
 @dataclass(frozen=True)
