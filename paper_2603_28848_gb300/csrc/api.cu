@@ -756,7 +756,8 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
         const size_t map_elems = static_cast<size_t>(kMaxDim) * nb_max;
         const size_t hist_elems = static_cast<size_t>(kThreads / 32) * map_elems;
         ctx->eval_smem = rs * ((spl + 3) & ~size_t(3)) + 2 * rs * map_elems + rs * ((hist_elems + 3) & ~size_t(3)) +
-                         2 * 32 * sizeof(double);
+                         2 * 32 * sizeof(double) +
+                         (f32 ? sizeof(float) * (kThreads / 32) * kQueueSlots * queue_words(ctx->nmax_legs) : 0);
         int max_optin = 0;
         cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (ctx->eval_smem > static_cast<size_t>(max_optin))

@@ -147,32 +147,30 @@ __device__ __forceinline__ float tail_f32(float x, float eta) {
     return den > 0.0f ? __fdividef(1.0f, den) : 0.0f;      // MUFU reciprocal (2 ulp)
 }
 
-// Weight of one sample at the mapped point y (r, theta, phi - pi per
-// integrated leg) with map Jacobian jac: momenta, conserved leg, energies,
-// statistical factor, Gaussian and Eq. (12); 0 for a cut sample.
-// EXT: the instantiation also supports an s-dependent |M|^2 (see run_segment).
+// Kinematic part of the weight of one sample at the mapped point y (r,
+// theta, phi - pi per integrated leg) with map Jacobian jac: momenta, the
+// conserved leg from momentum conservation, energies, the Gaussian of
+// Eq. (11), the phase-space measure of Eq. (12) and, in the EXT
+// instantiation, an s-dependent |M|^2.  Returns 0 for a cut sample and leaves
+// what the statistical factor needs in r (comoving radii of the integrated
+// legs), qc (comoving momentum of the conserved leg) and Ec (its energy).
 template <typename R, int NLEG, bool EXT>
-__device__ __forceinline__ R weight_at(const SegConst<R, NLEG>& C, const R* y, R jac, const R* s_spline,
-                                       const R* knots, const Geometry& g, R inv_step, R q0, R lq0_step, R qN,
-                                       int ncoef) {
+__device__ __forceinline__ R kin_at(const SegConst<R, NLEG>& C, const R* y, R jac, R* r, R& qc, R& Ec) {
     constexpr int NI = NLEG - 2;
-    constexpr bool F32 = RMath<R>::kF32;
-    // integrated legs
     R px = R(0), py = R(0), pz = C.pobs_sig;
     R dE = C.sgn_obs_E;
     R Esum = C.e_obs;                   // E_in + E_out (used when C.frac)
     R Qx = R(0), Qy = R(0), Qz = C.obs_in_p, Ein = C.obs_in_E;   // initial state (used when C.me_on)
     R meas = jac;
-    R stat = C.c0;
     R rinvE_prod = R(1);
     bool cut = false;
 #pragma unroll
     for (int j = 0; j < NI; ++j) {
-        const R r = y[3 * j];
+        r[j] = y[3 * j];
         R st, ct, sp, cp;
         RMath<R>::sincos_(y[3 * j + 1], &st, &ct);
         RMath<R>::sincos_(y[3 * j + 2], &sp, &cp);   // angle phi - pi
-        const R p = r * C.inv_a;
+        const R p = r[j] * C.inv_a;
         const R ps = p * st;
         const R sg = C.sig[j];
         px = fma(-sg * ps, cp, px);                    // cos(phi) = -cos(phi - pi)
@@ -191,28 +189,66 @@ __device__ __forceinline__ R weight_at(const SegConst<R, NLEG>& C, const R* y, R
             Qz = fma(iw * p, ct, Qz);
             Ein = fma(iw, E, Ein);
         }
-        meas *= r * r * st;
+        meas *= r[j] * r[j] * st;
         rinvE_prod *= rE;
-        const SplineView<R> sv{s_spline + C.spc[j] * ncoef, knots};
-        R f = spline_eval<R>(sv, r, g, inv_step, q0, lq0_step);
-        f = C.fd[j] ? (f < R(1) ? f : R(1)) : f;
-        stat *= fma(C.cb[j], f, C.ca[j]);
     }
     // conserved leg (Eq. (10), App. A)
     const R pc2 = fma(px, px, fma(py, py, pz * pz));
     const R Ec2 = pc2 + C.m2c;
     const R rEc = RMath<R>::rsqrt_(Ec2 > R(0) ? Ec2 : R(1e-30));
-    const R Ec = Ec2 * rEc;
+    Ec = Ec2 * rEc;
     cut |= Ec < C.e_cut;
     dE = fma(C.sgn_cons, Ec, dE);
+    qc = pc2 * (pc2 > R(0) ? RMath<R>::rsqrt_(pc2) : R(0)) * C.a;
+    R gauss;
+    if (C.frac) {
+        // sigma = w S / 2 with S = E_in + E_out: exponent
+        // -2 dE^2 / (w S)^2, normalisation sigma_ref / sigma = 2 E_obs / S
+        Esum += Ec;
+        const R iS = RMath<R>::rcp_(Esum);
+        const R x = dE * iS;
+        gauss = RMath<R>::exp2_(C.gauss_k * x * x) * (R(2) * C.e_obs * iS);
+    } else {
+        gauss = RMath<R>::exp2_(C.gauss_k * dE * dE);
+    }
+    R w = meas * rinvE_prod * rEc * gauss;
+    if (EXT && C.me_on) {
+        // |M|^2 / coupling^2 = P(s), s of the initial state (the conserved
+        // leg's momentum is (px, py, pz))
+        const R cw = C.cons_inw;
+        const R qx = fma(cw, px, Qx), qy = fma(cw, py, Qy), qz = fma(cw, pz, Qz);
+        const R e = fma(cw, Ec, Ein);
+        const R sv = fma(e, e, -fma(qx, qx, fma(qy, qy, qz * qz)));
+        w *= fma(fma(fma(C.me[3], sv, C.me[2]), sv, C.me[1]), sv, C.me[0]);
+    }
+    return cut ? R(0) : w;
+}
+
+// Statistical factor of Eq. (5) of one sample: the observed leg's factor
+// over the scale, times c_a + c_b f of every other leg, f from the spline
+// (Sec. 3B) or, for the conserved leg outside the grid, the tails of
+// Eq. (13).
+template <typename R, int NLEG>
+__device__ __forceinline__ R stat_at(const SegConst<R, NLEG>& C, const R* r, R qc, R Ec, const R* s_spline,
+                                     const R* knots, const Geometry& g, R inv_step, R q0, R lq0_step, R qN,
+                                     int ncoef) {
+    constexpr int NI = NLEG - 2;
+    constexpr bool F32 = RMath<R>::kF32;
+    R stat = C.c0;
+#pragma unroll
+    for (int j = 0; j < NI; ++j) {
+        const SplineView<R> sv{s_spline + C.spc[j] * ncoef, knots};
+        R f = spline_eval<R>(sv, r[j], g, inv_step, q0, lq0_step);
+        f = C.fd[j] ? (f < R(1) ? f : R(1)) : f;
+        stat *= fma(C.cb[j], f, C.ca[j]);
+    }
     R fc;
     {
-        const R qc = pc2 * (pc2 > R(0) ? RMath<R>::rsqrt_(pc2) : R(0)) * C.a;
         const bool below = qc < q0, above = qc > qN;
         if constexpr (F32) {
             // spline for every lane, the tail only in warps where some lane
             // left the grid, then a select: the warp never diverges on the
-            // conserved leg (the mask is the lanes still in the sample loop)
+            // conserved leg (the mask is the lanes present)
             const SplineView<R> sv{s_spline + C.sp_cons * ncoef, knots};
             fc = spline_eval<R>(sv, fminf(fmaxf(qc, q0), qN), g, inv_step, q0, lq0_step);
             if (__any_sync(__activemask(), below || above)) {
@@ -232,29 +268,18 @@ __device__ __forceinline__ R weight_at(const SegConst<R, NLEG>& C, const R* y, R
         }
         fc = C.fd_c ? (fc < R(1) ? fc : R(1)) : fc;
     }
-    stat *= fma(C.cbc, fc, C.cac);
-    R gauss;
-    if (C.frac) {
-        // sigma = w S / 2 with S = E_in + E_out: exponent
-        // -2 dE^2 / (w S)^2, normalisation sigma_ref / sigma = 2 E_obs / S
-        Esum += Ec;
-        const R iS = RMath<R>::rcp_(Esum);
-        const R x = dE * iS;
-        gauss = RMath<R>::exp2_(C.gauss_k * x * x) * (R(2) * C.e_obs * iS);
-    } else {
-        gauss = RMath<R>::exp2_(C.gauss_k * dE * dE);
-    }
-    R w = stat * meas * rinvE_prod * rEc * gauss;
-    if (EXT && C.me_on) {
-        // |M|^2 / coupling^2 = P(s), s of the initial state (the conserved
-        // leg's momentum is (px, py, pz))
-        const R cw = C.cons_inw;
-        const R qx = fma(cw, px, Qx), qy = fma(cw, py, Qy), qz = fma(cw, pz, Qz);
-        const R e = fma(cw, Ec, Ein);
-        const R sv = fma(e, e, -fma(qx, qx, fma(qy, qy, qz * qz)));
-        w *= fma(fma(fma(C.me[3], sv, C.me[2]), sv, C.me[1]), sv, C.me[0]);
-    }
-    return cut ? R(0) : w;
+    return stat * fma(C.cbc, fc, C.cac);
+}
+
+// Weight of one sample (Eq. (12)): statistical factor times kinematic part.
+// EXT: the instantiation also supports an s-dependent |M|^2 (see run_segment).
+template <typename R, int NLEG, bool EXT>
+__device__ __forceinline__ R weight_at(const SegConst<R, NLEG>& C, const R* y, R jac, const R* s_spline,
+                                       const R* knots, const Geometry& g, R inv_step, R q0, R lq0_step, R qN,
+                                       int ncoef) {
+    R r[NLEG - 2], qc, Ec;
+    const R kin = kin_at<R, NLEG, EXT>(C, y, jac, r, qc, Ec);
+    return stat_at<R, NLEG>(C, r, qc, Ec, s_spline, knots, g, inv_step, q0, lq0_step, qN, ncoef) * kin;
 }
 
 // STRAT: the instantiation also handles stratified tasks and s-dependent
@@ -264,7 +289,7 @@ template <typename R, int NLEG, bool STRAT>
 __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& seg,
                                             const SideDesc& sd, const TaskDesc& td,
                                             const TaskConst& tc, R* s_spline,
-                                            Real2<R>* s_map, R* s_hist, double* s_red) {
+                                            Real2<R>* s_map, R* s_hist, double* s_red, float* s_queue) {
     constexpr int NI = NLEG - 2;
     constexpr int D = 3 * NI;
     constexpr bool F32 = RMath<R>::kF32;
@@ -382,53 +407,135 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
     const int64_t N = td.neval;
     const uint32_t task = td.gid;                 // the stream is keyed by the global task id
     const int32_t g1 = static_cast<int32_t>(seg.g1);
-    if (!STRAT || td.strat_H == 0)
-    for (int32_t grp = static_cast<int32_t>(seg.g0) + tid; grp < g1; grp += blockDim.x) {
-        // FP32: raw words; FP64: 52-bit uniforms
-        uint32_t uw[F32 ? SS::kUniforms : 1];
-        R u[F32 ? 1 : SS::kUniforms];
-        if constexpr (F32) group_words<D>(uw, grp, P.itn, ts.call, task, P.rk);
-        else group_uniforms<D, F32, R>(u, grp, P.itn, ts.call, task, P.rk);
+    if (!STRAT || td.strat_H == 0) {
+        if constexpr (F32) {
+            // Samples with a non-zero kinematic part (close enough to the
+            // energy shell for the Gaussian not to underflow) are queued per
+            // warp in shared memory; the statistical factor, the sums and the
+            // training data are evaluated 32 queued samples at a time, so
+            // that those instructions run on full warps of live samples.  The
+            // warp runs the loop in step (a lane past the segment's end
+            // computes an invalid sample), so its votes see all 32 lanes.
+            constexpr int QW = queue_words(NLEG);
+            constexpr int NB = (D + 3) / 4;               // words of packed increments
+            float* q = s_queue + (tid >> 5) * (kQueueSlots * QW);
+            const int lane = tid & 31;
+            const uint32_t lanes_below = (1u << lane) - 1u;
+            int qn = 0;                                   // queued samples (warp-uniform)
+            auto drain = [&](int slot) {
+                R r[NI];
 #pragma unroll
-        for (int sgi = 0; sgi < G; ++sgi) {
-            // samples past the budget (only in a task's last group) are
-            // computed and given weight 0: no branch inside the group
-            const bool valid = static_cast<uint32_t>(grp) * G + sgi < static_cast<uint32_t>(N);   // N <= 2^31
-            // VEGAS map and scaling to (r, theta, phi - pi)
-            R y[D];
-            int bin[D];
-            R jac = R(1);
+                for (int j = 0; j < NI; ++j) r[j] = q[(1 + j) * kQueueSlots + slot];
+                const R qc = q[(1 + NI) * kQueueSlots + slot];
+                const R Ec = q[(2 + NI) * kQueueSlots + slot];
+                const R w = stat_at<R, NLEG>(C, r, qc, Ec, s_spline, knots, g, inv_step, q0, lq0_step, qN, ncoef) *
+                            q[slot];
+                const R w2 = w * w;
+                acc_w.add(w);
+                acc_w2.add(w2);
+                if (w2 != R(0)) {
 #pragma unroll
-            for (int d = 0; d < D; ++d) {
-                int b;
-                R fr;
-                if constexpr (F32) {
-                    // x nb = (2k + 1) nb / 2^24 with k = word >> 9: increment and
-                    // fraction exactly, in integer arithmetic
-                    const uint32_t m = (uw[sgi * D + d] >> 9) * (2u * nb) + static_cast<uint32_t>(nb);
-                    b = static_cast<int>(m >> 24);
-                    fr = static_cast<float>(m & 0xFFFFFFu) * 5.9604644775390625e-08f;   // 2^-24
-                } else {
-                    const R t = u[sgi * D + d] * nbR;
-                    b = static_cast<int>(t);
-                    b = b < nb - 1 ? b : nb - 1;
-                    fr = t - static_cast<R>(b);
+                    for (int k = 0; k < NB; ++k) {
+                        const uint32_t pb = __float_as_uint(q[(3 + NI + k) * kQueueSlots + slot]);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (4 * k + e < D)
+                                atomicAdd(&w_hist[(4 * k + e) * nb + ((pb >> (8 * e)) & 0xFFu)], w2);
+                    }
                 }
-                const Real2<R> e = s_map[d * nb + b];
-                y[d] = fma(e.dy, fr, e.y0);
-                jac *= e.dy;
-                bin[d] = b;
-            }
-            R w = weight_at<R, NLEG, STRAT>(C, y, jac, s_spline, knots, g, inv_step, q0, lq0_step, qN, ncoef);
-            w = valid ? w : R(0);
-            const R w2 = w * w;
-            acc_w.add(w);
-            acc_w2.add(w2);
-            // training data: a zero w^2 (far from the energy shell, or
-            // underflow) adds nothing, so such lanes skip the atomics
-            if (w2 != R(0)) {
+            };
+            for (int32_t gb = static_cast<int32_t>(seg.g0) + (tid & ~31); gb < g1; gb += blockDim.x) {
+                const int64_t grp = static_cast<int64_t>(gb) + lane;
+                uint32_t uw[SS::kUniforms];
+                group_words<D>(uw, grp, P.itn, ts.call, task, P.rk);
 #pragma unroll
-                for (int d = 0; d < D; ++d) atomicAdd(&w_hist[d * nb + bin[d]], w2);
+                for (int sgi = 0; sgi < G; ++sgi) {
+                    // samples past the budget (only in a task's last group) and
+                    // past the segment are computed and not queued
+                    const bool valid = grp < g1 && grp * G + sgi < N;
+                    R y[D];
+                    uint32_t pb[NB];
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) pb[k] = 0u;
+                    R jac = R(1);
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        // x nb = (2k + 1) nb / 2^24 with k = word >> 9: increment
+                        // and fraction exactly, in integer arithmetic
+                        const uint32_t m = (uw[sgi * D + d] >> 9) * (2u * nb) + static_cast<uint32_t>(nb);
+                        const uint32_t b = m >> 24;
+                        const float fr = static_cast<float>(m & 0xFFFFFFu) * 5.9604644775390625e-08f;   // 2^-24
+                        const Real2<R> e = s_map[d * nb + b];
+                        y[d] = fma(e.dy, fr, e.y0);
+                        jac *= e.dy;
+                        pb[d >> 2] |= b << (8 * (d & 3));
+                    }
+                    R r[NI], qc, Ec;
+                    const R kin = kin_at<R, NLEG, STRAT>(C, y, jac, r, qc, Ec);
+                    const bool keep = valid && kin != R(0);
+                    const uint32_t vote = __ballot_sync(0xffffffffu, keep);
+                    if (keep) {
+                        const int slot = qn + __popc(vote & lanes_below);     // < 2 * 32
+                        q[slot] = kin;
+#pragma unroll
+                        for (int j = 0; j < NI; ++j) q[(1 + j) * kQueueSlots + slot] = r[j];
+                        q[(1 + NI) * kQueueSlots + slot] = qc;
+                        q[(2 + NI) * kQueueSlots + slot] = Ec;
+#pragma unroll
+                        for (int k = 0; k < NB; ++k) q[(3 + NI + k) * kQueueSlots + slot] = __uint_as_float(pb[k]);
+                    }
+                    qn += __popc(vote);
+                    if (qn >= 32) {
+                        __syncwarp();
+                        drain(lane);
+                        __syncwarp();
+                        if (lane < qn - 32) {
+#pragma unroll
+                            for (int f = 0; f < QW; ++f) q[f * kQueueSlots + lane] = q[f * kQueueSlots + 32 + lane];
+                        }
+                        __syncwarp();
+                        qn -= 32;
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane < qn) drain(lane);
+        } else {
+            for (int32_t grp = static_cast<int32_t>(seg.g0) + tid; grp < g1; grp += blockDim.x) {
+                R u[SS::kUniforms];                       // 52-bit uniforms
+                group_uniforms<D, F32, R>(u, grp, P.itn, ts.call, task, P.rk);
+#pragma unroll
+                for (int sgi = 0; sgi < G; ++sgi) {
+                    // samples past the budget (only in a task's last group) are
+                    // computed and given weight 0: no branch inside the group
+                    const bool valid = static_cast<uint32_t>(grp) * G + sgi < static_cast<uint32_t>(N);   // N <= 2^31
+                    // VEGAS map and scaling to (r, theta, phi - pi)
+                    R y[D];
+                    int bin[D];
+                    R jac = R(1);
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        const R t = u[sgi * D + d] * nbR;
+                        int b = static_cast<int>(t);
+                        b = b < nb - 1 ? b : nb - 1;
+                        const R fr = t - static_cast<R>(b);
+                        const Real2<R> e = s_map[d * nb + b];
+                        y[d] = fma(e.dy, fr, e.y0);
+                        jac *= e.dy;
+                        bin[d] = b;
+                    }
+                    R w = weight_at<R, NLEG, STRAT>(C, y, jac, s_spline, knots, g, inv_step, q0, lq0_step, qN, ncoef);
+                    w = valid ? w : R(0);
+                    const R w2 = w * w;
+                    acc_w.add(w);
+                    acc_w2.add(w2);
+                    // training data: a zero w^2 (far from the energy shell, or
+                    // underflow) adds nothing, so such lanes skip the atomics
+                    if (w2 != R(0)) {
+#pragma unroll
+                        for (int d = 0; d < D; ++d) atomicAdd(&w_hist[d * nb + bin[d]], w2);
+                    }
+                }
             }
         }
     }
@@ -551,6 +658,7 @@ eval_kernel(EvalParams P) {
     const int map_elems = kMaxDim * P.geo.nbins_max;
     R* s_hist = reinterpret_cast<R*>(s_map + map_elems);      // [warps][map_elems]
     double* s_red = reinterpret_cast<double*>(s_hist + (((kThreads / 32) * map_elems + 3) & ~3));
+    float* s_queue = reinterpret_cast<float*>(s_red + 2 * 32);   // FP32: [warps][queue_words][kQueueSlots]
 
     // spline tables of all species, once per CTA
     {
@@ -568,10 +676,10 @@ eval_kernel(EvalParams P) {
         const TaskConst tc = P.tconst[seg.task];
         __syncthreads();
         switch (sd.n) {
-            case 3: if constexpr (NMAX >= 3) run_segment<R, 3, STRAT>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red); break;
-            case 4: if constexpr (NMAX >= 4) run_segment<R, 4, STRAT>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red); break;
-            case 5: if constexpr (NMAX >= 5) run_segment<R, 5, STRAT>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red); break;
-            case 6: if constexpr (NMAX >= 6) run_segment<R, 6, STRAT>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red); break;
+            case 3: if constexpr (NMAX >= 3) run_segment<R, 3, STRAT>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue); break;
+            case 4: if constexpr (NMAX >= 4) run_segment<R, 4, STRAT>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue); break;
+            case 5: if constexpr (NMAX >= 5) run_segment<R, 5, STRAT>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue); break;
+            case 6: if constexpr (NMAX >= 6) run_segment<R, 6, STRAT>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue); break;
             default: break;
         }
     }

@@ -11,6 +11,14 @@ namespace best {
 constexpr int kMaxLegs = BEST_MAX_LEGS;
 constexpr int kMaxDim = 3 * (BEST_MAX_LEGS - 2);
 constexpr int kThreads = 256;          // threads per CTA of the sample kernel
+constexpr int kQueueSlots = 64;        // FP32 sample kernel: queued samples per warp
+
+// 32-bit words per queued sample of an n-leg task: the kinematic weight, the
+// comoving radii of the n-2 integrated legs, the conserved leg's comoving
+// momentum and energy, and the 3(n-2) map increments packed 4 per word.
+__host__ __device__ constexpr int queue_words(int nleg) {
+    return 1 + (nleg - 2) + 2 + (3 * (nleg - 2) + 3) / 4;
+}
 constexpr int kItem = 8;               // samples per item of stratified sampling (a multiple of every group size)
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTwoPi = 6.28318530717958647692;

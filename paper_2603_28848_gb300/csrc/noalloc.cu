@@ -201,7 +201,8 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     const size_t map_elems = static_cast<size_t>(kMaxDim) * nb;
     const size_t hist_elems = static_cast<size_t>(kThreads / 32) * map_elems;
     const size_t smem = rs * ((spl + 3) & ~size_t(3)) + 2 * rs * map_elems + rs * ((hist_elems + 3) & ~size_t(3)) +
-                        2 * 32 * sizeof(double);
+                        2 * 32 * sizeof(double) +
+                        (f32 ? sizeof(float) * (kThreads / 32) * kQueueSlots * queue_words(sd.n) : 0);
     cudaFuncAttributes fa{};
     if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return report(BEST_ERR_CUDA, "noalloc: kernel query failed");
     if (static_cast<size_t>(fa.maxDynamicSharedSizeBytes) < smem &&
