@@ -871,9 +871,12 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
         const size_t spl = static_cast<size_t>(S) * 4 * (n - 1) + n;
         const size_t ngc = static_cast<size_t>(S) * 4 * (n - 1);
         const size_t map_elems = static_cast<size_t>(kMaxDim) * nb_max;
+        const size_t queue = sizeof(float) * (kThreads / 32) * kQueueSlots;   // FP32 per-warp sample queues
         ctx->vjp_smem = rs * ((spl + 3) & ~size_t(3)) + 2 * rs * map_elems + sizeof(double) * ngc +
-                        12 * 8 * sizeof(double) + (f32 ? sizeof(float) * ngc : 0);
-        ctx->jvp_smem = rs * ((spl + 3) & ~size_t(3)) + 2 * rs * map_elems + 12 * 8 * sizeof(double) + rs * ngc;
+                        12 * 8 * sizeof(double) +
+                        (f32 ? sizeof(float) * ngc + queue * vjp_queue_words(ctx->nmax_legs, false) : 0);
+        ctx->jvp_smem = rs * ((spl + 3) & ~size_t(3)) + 2 * rs * map_elems + 12 * 8 * sizeof(double) + rs * ngc +
+                        (f32 ? queue * vjp_queue_words(ctx->nmax_legs, true) : 0);
     }
     CKI(cudaMemset(ctx->d_prev, 0, sizeof(double) * T));
     CKI(cudaMemcpy(ctx->d_sides, ctx->sides.data(), g.n_side * sizeof(SideDesc), cudaMemcpyHostToDevice));

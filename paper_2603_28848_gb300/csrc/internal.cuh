@@ -19,6 +19,15 @@ constexpr int kQueueSlots = 64;        // FP32 sample kernel: queued samples per
 __host__ __device__ constexpr int queue_words(int nleg) {
     return 1 + (nleg - 2) + 2 + (3 * (nleg - 2) + 3) / 4;
 }
+
+// The same for the adjoint (tangent = false) and tangent sample kernels: the
+// kinematic weight, the comoving radii, then for the adjoint 1/E of each
+// integrated leg; the conserved leg's comoving momentum and energy; for the
+// adjoint also 1/E_cons, dE / sigma^2, the fractional-width term and
+// d log P / d E.
+__host__ __device__ constexpr int vjp_queue_words(int nleg, bool tangent) {
+    return tangent ? 3 + (nleg - 2) : 7 + 2 * (nleg - 2);
+}
 constexpr int kItem = 8;               // samples per item of stratified sampling (a multiple of every group size)
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTwoPi = 6.28318530717958647692;

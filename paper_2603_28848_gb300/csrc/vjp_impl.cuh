@@ -71,7 +71,8 @@ __device__ __forceinline__ Hit<R> spline_hit(const SplineView<R>& sv, R q, const
 template <typename R, int NLEG, bool JVP, bool ME>
 __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& seg, const SideDesc& sd,
                                             const TaskDesc& td, const TaskConst& tc, R* s_spline,
-                                            Real2<R>* s_map, double* s_gc, double* s_red, R* s_dsp) {
+                                            Real2<R>* s_map, double* s_gc, double* s_red, R* s_dsp,
+                                            float* s_queue) {
     const EvalParams& P = V.E;
     constexpr int NI = NLEG - 2;
     constexpr int D = 3 * NI;
@@ -192,173 +193,86 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
     const int64_t N = td.neval;
     const uint32_t task = td.gid;                 // the stream is keyed by the global task id
     const int32_t g1 = static_cast<int32_t>(seg.g1);
-    for (int32_t grp = static_cast<int32_t>(seg.g0) + tid; grp < g1; grp += blockDim.x) {
-        uint32_t uw[F32 ? SS::kUniforms : 1];
-        R u[F32 ? 1 : SS::kUniforms];
-        if constexpr (F32) group_words<D>(uw, grp, P.itn, ts.call, task, P.rk);
-        else group_uniforms<D, F32, R>(u, grp, P.itn, ts.call, task, P.rk);
+
+    // Statistical factors of one sample from its kinematic part base (0 for
+    // a cut or invalid sample), the comoving radii r of the integrated legs,
+    // 1/E of each (rE), the conserved leg's comoving momentum qc, energy Ec
+    // and 1/Ec, dE / sigma^2 (dEs), the fractional-width term and
+    // d log P / d E of the initial legs; then the sums and the derivatives.
+    auto accumulate = [&](R base, const R* r, const R* rE, R qc, R Ec, R rEc, R dEs, R sig_term, R me_d) {
+        R fac[NI + 1], dfac[NI + 1], tl[NI + 1];
+        int jl[NI + 1];
 #pragma unroll
-        for (int sgi = 0; sgi < G; ++sgi) {
-            const bool valid = static_cast<int64_t>(grp) * G + sgi < N;
-            R y[D];
-            R jac = R(1);
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                int b;
-                R fr;
+        for (int j = 0; j < NI; ++j) {
+            const SplineView<R> sv{s_spline + spc[j] * ncoef, knots};
+            const Hit<R> h = spline_hit<R>(sv, r[j], g, inv_step, q0, lq0_step, fdj[j]);
+            fac[j] = fma(cb[j], h.f, ca[j]);
+            dfac[j] = cb[j] * h.d;
+            jl[j] = h.j;
+            tl[j] = h.t;
+        }
+        const bool below = qc < q0, above = qc > qN;
+        const bool inside = !below && !above;
+        R fc, dfdz = R(0);
+        {
+            const SplineView<R> sv{s_spline + spcn * ncoef, knots};
+            const Hit<R> h = spline_hit<R>(sv, inside ? qc : (below ? q0 : qN), g, inv_step, q0, lq0_step, fd_c);
+            jl[NI] = h.j;
+            tl[NI] = h.t;
+            if (inside) {
+                fc = h.f;
+                dfac[NI] = cbc * h.d;
+            } else {
+                const R x = below ? fma(tlo_b, Ec, tlo_a) : fma(thi_b, Ec, thi_a);
+                R ft;
                 if constexpr (F32) {
-                    const uint32_t m = (uw[sgi * D + d] >> 9) * (2u * nb) + static_cast<uint32_t>(nb);
-                    b = static_cast<int>(m >> 24);
-                    fr = static_cast<float>(m & 0xFFFFFFu) * 5.9604644775390625e-08f;
+                    ft = tail_f32(x, eta_c);
                 } else {
-                    const R t = u[sgi * D + d] * nbR;
-                    b = static_cast<int>(t);
-                    b = b < nb - 1 ? b : nb - 1;
-                    fr = t - static_cast<R>(b);
+                    const R den = eta_c == R(1) ? expm1(x) : exp(x) - eta_c;
+                    ft = den > R(0) ? R(1) / den : R(0);
                 }
-                const Real2<R> e = s_map[d * nb + b];
-                y[d] = fma(e.dy, fr, e.y0);
-                jac *= e.dy;
+                dfdz = -ft * fma(eta_c, ft, R(1));
+                if (fd_c && ft > R(1)) { ft = R(1); dfdz = R(0); }
+                fc = ft;
+                dfac[NI] = cbc;
             }
-            R px = R(0), py = R(0), pz = pobs_sig;
-            R dE = sgn_obs_E;
-            R Esum = e_obs;
-            R Qx = R(0), Qy = R(0), Qz = obs_in_p, Ein = obs_in_E;
-            R meas = jac;
-            R rinv = R(1);
-            bool cut = obs_cut;
-            R fac[NI + 1], dfac[NI + 1], tl[NI + 1], rE[NI];
-            int jl[NI + 1];
+        }
+        fac[NI] = fma(cbc, fc, cac);
+        // products excluding each factor
+        R pre[NI + 2];
+        pre[0] = R(1);
 #pragma unroll
-            for (int j = 0; j < NI; ++j) {
-                const R r = y[3 * j];
-                R st, ct, sp, cp;
-                RMath<R>::sincos_(y[3 * j + 1], &st, &ct);
-                RMath<R>::sincos_(y[3 * j + 2], &sp, &cp);
-                const R p = r * inv_a;
-                const R ps = p * st;
-                px = fma(-sig[j] * ps, cp, px);
-                py = fma(-sig[j] * ps, sp, py);
-                pz = fma(sig[j] * p, ct, pz);
-                const R E2 = fma(p, p, m2[j]);
-                const R rr = RMath<R>::rsqrt_(E2);
-                const R E = E2 * rr;
-                cut |= E < e_cut;
-                dE = fma(sgnE[j], E, dE);
-                Esum += E;
-                if (me_on) {
-                    Qx = fma(-inw[j] * ps, cp, Qx);
-                    Qy = fma(-inw[j] * ps, sp, Qy);
-                    Qz = fma(inw[j] * p, ct, Qz);
-                    Ein = fma(inw[j], E, Ein);
-                }
-                meas *= r * r * st;
-                rinv *= rr;
-                rE[j] = rr;
-                const SplineView<R> sv{s_spline + spc[j] * ncoef, knots};
-                const Hit<R> h = spline_hit<R>(sv, r, g, inv_step, q0, lq0_step, fdj[j]);
-                fac[j] = fma(cb[j], h.f, ca[j]);
-                dfac[j] = cb[j] * h.d;
-                jl[j] = h.j;
-                tl[j] = h.t;
-            }
-            const R pc2 = fma(px, px, fma(py, py, pz * pz));
-            const R Ec2 = pc2 + m2c;
-            const R rEc = RMath<R>::rsqrt_(Ec2 > R(0) ? Ec2 : R(1e-30));
-            const R Ec = Ec2 * rEc;
-            cut |= Ec < e_cut;
-            dE = fma(sgn_cons, Ec, dE);
-            const R qc = pc2 * (pc2 > R(0) ? RMath<R>::rsqrt_(pc2) : R(0)) * a;
-            const bool below = qc < q0, above = qc > qN;
-            const bool inside = !below && !above;
-            R fc, dfdz = R(0);
-            {
-                const SplineView<R> sv{s_spline + spcn * ncoef, knots};
-                const Hit<R> h = spline_hit<R>(sv, inside ? qc : (below ? q0 : qN), g, inv_step, q0, lq0_step, fd_c);
-                jl[NI] = h.j;
-                tl[NI] = h.t;
-                if (inside) {
-                    fc = h.f;
-                    dfac[NI] = cbc * h.d;
+        for (int k = 0; k <= NI; ++k) pre[k + 1] = pre[k] * fac[k];
+        const R F = pre[NI + 1];
+        const R wn = c0 * base * F;
+        acc_w.add(wn);
+        acc_fobs.add(base * F);
+        R suf = R(1);
+        R dwdf[NI + 1];
+#pragma unroll
+        for (int k = NI; k >= 0; --k) {
+            dwdf[k] = c0 * base * pre[k] * suf * dfac[k];
+            suf *= fac[k];
+        }
+        if constexpr (JVP) {
+            // tangent: d w_n = sum_k dw/df_k df_k + (w_n / c0) U (U = dobs u_obs / scale)
+            R dw = base * F * U;
+#pragma unroll
+            for (int k = 0; k <= NI; ++k) {
+                R dfk;
+                if (k == NI && !inside) {
+                    dfk = dfdz * (below ? fma(dtb_lo, Ec, dta_lo) : fma(dtb_hi, Ec, dta_hi));
                 } else {
-                    const R x = below ? fma(tlo_b, Ec, tlo_a) : fma(thi_b, Ec, thi_a);
-                    R ft;
-                    if constexpr (F32) {
-                        ft = tail_f32(x, eta_c);
-                    } else {
-                        const R den = eta_c == R(1) ? expm1(x) : exp(x) - eta_c;
-                        ft = den > R(0) ? R(1) / den : R(0);
-                    }
-                    dfdz = -ft * fma(eta_c, ft, R(1));
-                    if (fd_c && ft > R(1)) { ft = R(1); dfdz = R(0); }
-                    fc = ft;
-                    dfac[NI] = cbc;
+                    const int sp = k < NI ? spc[k] : spcn;
+                    const R* dc = s_dsp + sp * ncoef + 4 * jl[k];
+                    const R t = tl[k];
+                    dfk = fma(fma(fma(dc[3], t, dc[2]), t, dc[1]), t, dc[0]);
                 }
+                dw = fma(dwdf[k], dfk, dw);
             }
-            fac[NI] = fma(cbc, fc, cac);
-            // Gaussian and, for the adjoint, 1/sigma^2 and the derivative of
-            // log(1/sigma) with exp(-dE^2 / 2 sigma^2) through sigma(E_k)
-            R gs, inv_sig2, sig_term;
-            if (frac) {
-                Esum += Ec;
-                const R iS = RMath<R>::rcp_(Esum);
-                const R x = dE * iS;
-                gs = RMath<R>::exp2_(gauss_k * x * x) * (R(2) * e_obs * iS);
-                inv_sig2 = four_over_w2 * iS * iS;
-                // d log g / d E_k from sigma: (dE^2 / sigma^2 - 1) / S for every leg
-                sig_term = fma(dE * dE, inv_sig2, R(-1)) * iS;
-            } else {
-                gs = RMath<R>::exp2_(gauss_k * dE * dE);
-                inv_sig2 = inv_sig2_abs;
-                sig_term = R(0);
-            }
-            R base = meas * rinv * rEc * gs;
-            base = (cut || !valid) ? R(0) : base;
-            R me_d = R(0);          // d log P / d E_k of every initial leg: P'(s) / P(s) 2 E_in
-            if (me_on) {
-                const R qx = fma(cons_inw, px, Qx), qy = fma(cons_inw, py, Qy), qz = fma(cons_inw, pz, Qz);
-                const R e = fma(cons_inw, Ec, Ein);
-                const R sv = fma(e, e, -fma(qx, qx, fma(qy, qy, qz * qz)));
-                const R P = fma(fma(fma(mec[3], sv, mec[2]), sv, mec[1]), sv, mec[0]);
-                const R dP = fma(fma(R(3) * mec[3], sv, R(2) * mec[2]), sv, mec[1]);
-                me_d = P != R(0) ? R(2) * e * dP * RMath<R>::rcp_(P) : R(0);
-                base *= P;
-            }
-            // products excluding each factor
-            R pre[NI + 2];
-            pre[0] = R(1);
-#pragma unroll
-            for (int k = 0; k <= NI; ++k) pre[k + 1] = pre[k] * fac[k];
-            const R F = pre[NI + 1];
-            const R wn = c0 * base * F;
-            acc_w.add(wn);
-            acc_fobs.add(base * F);
-            R suf = R(1);
-            R dwdf[NI + 1];
-#pragma unroll
-            for (int k = NI; k >= 0; --k) {
-                dwdf[k] = c0 * base * pre[k] * suf * dfac[k];
-                suf *= fac[k];
-            }
-            if constexpr (JVP) {
-                // tangent: d w_n = sum_k dw/df_k df_k + (w_n / c0) U (U = dobs u_obs / scale)
-                R dw = base * F * U;
-#pragma unroll
-                for (int k = 0; k <= NI; ++k) {
-                    R dfk;
-                    if (k == NI && !inside) {
-                        dfk = dfdz * (below ? fma(dtb_lo, Ec, dta_lo) : fma(dtb_hi, Ec, dta_hi));
-                    } else {
-                        const int sp = k < NI ? spc[k] : spcn;
-                        const R* dc = s_dsp + sp * ncoef + 4 * jl[k];
-                        const R t = tl[k];
-                        dfk = fma(fma(fma(dc[3], t, dc[2]), t, dc[1]), t, dc[0]);
-                    }
-                    dw = fma(dwdf[k], dfk, dw);
-                }
-                acc_dw.add(dw);
-            } else {
-            const R dEterm = -wn * dE * inv_sig2;
+            acc_dw.add(dw);
+        } else {
+            const R dEterm = -wn * dEs;
             const R wsig = wn * sig_term;           // fractional width: same for every leg
             const R wme = wn * me_d;                // s-dependent |M|^2: every initial leg
 #pragma unroll
@@ -401,8 +315,177 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
                     }
                 }
             }
+        }
+    };
+
+    // FP32: samples with a non-zero kinematic part are queued per warp and
+    // their statistical factors and derivatives evaluated 32 at a time (as in
+    // the sample kernel); the warp runs the loop in step so that its votes
+    // see all 32 lanes.  FP64: every sample is accumulated where it is drawn.
+    constexpr int QW = vjp_queue_words(NLEG, JVP);
+    float* q = F32 ? s_queue + (tid >> 5) * (kQueueSlots * QW) : nullptr;
+    const int lane = tid & 31;
+    const uint32_t lanes_below = (1u << lane) - 1u;
+    int qn = 0;                                   // queued samples (warp-uniform)
+    auto drain = [&](int slot) {
+        R r[NI], rE[NI];
+#pragma unroll
+        for (int j = 0; j < NI; ++j) r[j] = q[(1 + j) * kQueueSlots + slot];
+        if constexpr (JVP) {
+#pragma unroll
+            for (int j = 0; j < NI; ++j) rE[j] = R(0);
+            accumulate(q[slot], r, rE, q[(1 + NI) * kQueueSlots + slot], q[(2 + NI) * kQueueSlots + slot], R(0),
+                       R(0), R(0), R(0));
+        } else {
+#pragma unroll
+            for (int j = 0; j < NI; ++j) rE[j] = q[(1 + NI + j) * kQueueSlots + slot];
+            accumulate(q[slot], r, rE, q[(1 + 2 * NI) * kQueueSlots + slot], q[(2 + 2 * NI) * kQueueSlots + slot],
+                       q[(3 + 2 * NI) * kQueueSlots + slot], q[(4 + 2 * NI) * kQueueSlots + slot],
+                       q[(5 + 2 * NI) * kQueueSlots + slot], q[(6 + 2 * NI) * kQueueSlots + slot]);
+        }
+    };
+    for (int32_t gb = static_cast<int32_t>(seg.g0) + (tid & ~31); gb < g1; gb += blockDim.x) {
+        const int64_t grp = static_cast<int64_t>(gb) + lane;
+        uint32_t uw[F32 ? SS::kUniforms : 1];
+        R u[F32 ? 1 : SS::kUniforms];
+        if constexpr (F32) group_words<D>(uw, grp, P.itn, ts.call, task, P.rk);
+        else group_uniforms<D, F32, R>(u, grp, P.itn, ts.call, task, P.rk);
+#pragma unroll
+        for (int sgi = 0; sgi < G; ++sgi) {
+            const bool valid = grp < g1 && grp * G + sgi < N;
+            R y[D];
+            R jac = R(1);
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                int b;
+                R fr;
+                if constexpr (F32) {
+                    const uint32_t m = (uw[sgi * D + d] >> 9) * (2u * nb) + static_cast<uint32_t>(nb);
+                    b = static_cast<int>(m >> 24);
+                    fr = static_cast<float>(m & 0xFFFFFFu) * 5.9604644775390625e-08f;
+                } else {
+                    const R t = u[sgi * D + d] * nbR;
+                    b = static_cast<int>(t);
+                    b = b < nb - 1 ? b : nb - 1;
+                    fr = t - static_cast<R>(b);
+                }
+                const Real2<R> e = s_map[d * nb + b];
+                y[d] = fma(e.dy, fr, e.y0);
+                jac *= e.dy;
+            }
+            R px = R(0), py = R(0), pz = pobs_sig;
+            R dE = sgn_obs_E;
+            R Esum = e_obs;
+            R Qx = R(0), Qy = R(0), Qz = obs_in_p, Ein = obs_in_E;
+            R meas = jac;
+            R rinv = R(1);
+            bool cut = obs_cut;
+            R r[NI], rE[NI];
+#pragma unroll
+            for (int j = 0; j < NI; ++j) {
+                r[j] = y[3 * j];
+                R st, ct, sp, cp;
+                RMath<R>::sincos_(y[3 * j + 1], &st, &ct);
+                RMath<R>::sincos_(y[3 * j + 2], &sp, &cp);
+                const R p = r[j] * inv_a;
+                const R ps = p * st;
+                px = fma(-sig[j] * ps, cp, px);
+                py = fma(-sig[j] * ps, sp, py);
+                pz = fma(sig[j] * p, ct, pz);
+                const R E2 = fma(p, p, m2[j]);
+                const R rr = RMath<R>::rsqrt_(E2);
+                const R E = E2 * rr;
+                cut |= E < e_cut;
+                dE = fma(sgnE[j], E, dE);
+                Esum += E;
+                if (me_on) {
+                    Qx = fma(-inw[j] * ps, cp, Qx);
+                    Qy = fma(-inw[j] * ps, sp, Qy);
+                    Qz = fma(inw[j] * p, ct, Qz);
+                    Ein = fma(inw[j], E, Ein);
+                }
+                meas *= r[j] * r[j] * st;
+                rinv *= rr;
+                rE[j] = rr;
+            }
+            const R pc2 = fma(px, px, fma(py, py, pz * pz));
+            const R Ec2 = pc2 + m2c;
+            const R rEc = RMath<R>::rsqrt_(Ec2 > R(0) ? Ec2 : R(1e-30));
+            const R Ec = Ec2 * rEc;
+            cut |= Ec < e_cut;
+            dE = fma(sgn_cons, Ec, dE);
+            const R qc = pc2 * (pc2 > R(0) ? RMath<R>::rsqrt_(pc2) : R(0)) * a;
+            // Gaussian and, for the adjoint, 1/sigma^2 and the derivative of
+            // log(1/sigma) with exp(-dE^2 / 2 sigma^2) through sigma(E_k)
+            R gs, inv_sig2, sig_term;
+            if (frac) {
+                Esum += Ec;
+                const R iS = RMath<R>::rcp_(Esum);
+                const R x = dE * iS;
+                gs = RMath<R>::exp2_(gauss_k * x * x) * (R(2) * e_obs * iS);
+                inv_sig2 = four_over_w2 * iS * iS;
+                // d log g / d E_k from sigma: (dE^2 / sigma^2 - 1) / S for every leg
+                sig_term = fma(dE * dE, inv_sig2, R(-1)) * iS;
+            } else {
+                gs = RMath<R>::exp2_(gauss_k * dE * dE);
+                inv_sig2 = inv_sig2_abs;
+                sig_term = R(0);
+            }
+            R base = meas * rinv * rEc * gs;
+            base = (cut || !valid) ? R(0) : base;
+            R me_d = R(0);          // d log P / d E_k of every initial leg: P'(s) / P(s) 2 E_in
+            if (me_on) {
+                const R qx = fma(cons_inw, px, Qx), qy = fma(cons_inw, py, Qy), qz = fma(cons_inw, pz, Qz);
+                const R e = fma(cons_inw, Ec, Ein);
+                const R sv = fma(e, e, -fma(qx, qx, fma(qy, qy, qz * qz)));
+                const R Pv = fma(fma(fma(mec[3], sv, mec[2]), sv, mec[1]), sv, mec[0]);
+                const R dP = fma(fma(R(3) * mec[3], sv, R(2) * mec[2]), sv, mec[1]);
+                me_d = Pv != R(0) ? R(2) * e * dP * RMath<R>::rcp_(Pv) : R(0);
+                base *= Pv;
+            }
+            const R dEs = dE * inv_sig2;
+            if constexpr (F32) {
+                const bool keep = base != R(0);
+                const uint32_t vote = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int slot = qn + __popc(vote & lanes_below);     // < 2 * 32
+                    q[slot] = base;
+#pragma unroll
+                    for (int j = 0; j < NI; ++j) q[(1 + j) * kQueueSlots + slot] = r[j];
+                    if constexpr (JVP) {
+                        q[(1 + NI) * kQueueSlots + slot] = qc;
+                        q[(2 + NI) * kQueueSlots + slot] = Ec;
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < NI; ++j) q[(1 + NI + j) * kQueueSlots + slot] = rE[j];
+                        q[(1 + 2 * NI) * kQueueSlots + slot] = qc;
+                        q[(2 + 2 * NI) * kQueueSlots + slot] = Ec;
+                        q[(3 + 2 * NI) * kQueueSlots + slot] = rEc;
+                        q[(4 + 2 * NI) * kQueueSlots + slot] = dEs;
+                        q[(5 + 2 * NI) * kQueueSlots + slot] = sig_term;
+                        q[(6 + 2 * NI) * kQueueSlots + slot] = me_d;
+                    }
+                }
+                qn += __popc(vote);
+                if (qn >= 32) {
+                    __syncwarp();
+                    drain(lane);
+                    __syncwarp();
+                    if (lane < qn - 32) {
+#pragma unroll
+                        for (int f = 0; f < QW; ++f) q[f * kQueueSlots + lane] = q[f * kQueueSlots + 32 + lane];
+                    }
+                    __syncwarp();
+                    qn -= 32;
+                }
+            } else {
+                accumulate(base, r, rE, qc, Ec, rEc, dEs, sig_term, me_d);
             }
         }
+    }
+    if constexpr (F32) {
+        __syncwarp();
+        if (lane < qn) drain(lane);
     }
 
     // ---- segment record: VJP [w, fobs, mobs, mc, tla, tlb, tha, thb, m_0 .. m_{NI-1}];
@@ -418,7 +501,7 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
 #pragma unroll
         for (int j = 0; j < NI; ++j) vals[8 + j] = acc_m[j].value();
     }
-    const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+    const int warp = tid >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         double v = vals[k];
@@ -459,6 +542,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) vjp_kernel(V
     double* s_red = s_gc + (JVP ? 0 : ngc);
     // JVP: tangent coefficients; FP32 VJP: the segment's coefficient-gradient sums
     R* s_dsp = reinterpret_cast<R*>(s_red + 12 * 8);
+    // FP32: per-warp sample queues after the coefficient table
+    float* s_queue = sizeof(R) == 4 ? reinterpret_cast<float*>(s_dsp + ngc) : nullptr;
     {
         const R* gc = static_cast<const R*>(P.coef);
         for (int k = threadIdx.x; k < ngc; k += blockDim.x) {
@@ -481,10 +566,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) vjp_kernel(V
         const TaskConst tc = P.tconst[seg.task];
         __syncthreads();
         switch (sd.n) {
-            case 3: if constexpr (NMAX >= 3) vjp_segment<R, 3, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp); break;
-            case 4: if constexpr (NMAX >= 4) vjp_segment<R, 4, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp); break;
-            case 5: if constexpr (NMAX >= 5) vjp_segment<R, 5, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp); break;
-            case 6: if constexpr (NMAX >= 6) vjp_segment<R, 6, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp); break;
+            case 3: if constexpr (NMAX >= 3) vjp_segment<R, 3, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp, s_queue); break;
+            case 4: if constexpr (NMAX >= 4) vjp_segment<R, 4, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp, s_queue); break;
+            case 5: if constexpr (NMAX >= 5) vjp_segment<R, 5, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp, s_queue); break;
+            case 6: if constexpr (NMAX >= 6) vjp_segment<R, 6, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp, s_queue); break;
             default: break;
         }
     }
