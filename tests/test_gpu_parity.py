@@ -177,6 +177,28 @@ def test_multi_species_fp32_within_three_sigma():
     _compare_fp32(prob, f0, t=2.0)
 
 
+@pytest.mark.parametrize("sigma", [50.0, 5e-3])
+def test_fp32_queue_all_live_and_mostly_dead(sigma):
+    """The FP32 kernel queues the samples whose Gaussian of Eq. (11) does not
+    underflow: with a very wide width every sample is queued, with a narrow
+    one few are.  One iteration on the same stream as the oracle: every
+    significant task's mean and error agree to FP32 rounding (tasks whose
+    samples all underflow in FP32 are negligible and left out)."""
+    prob, f0 = W.c1_maxwell_2to2(n=10, neval=3001, nitn=1)
+    prob = replace(prob, processes=tuple(replace(p, sigma_E=sigma) for p in prob.processes))
+    col = _gpu(prob, W.PREC_FP32)
+    col.eval(_f(f0), 0.0)
+    col.check()
+    mean, terr = col.task_results()
+    _, _, detail, _ = oracle_sweep(prob, f0, 0.0, "f32")
+    om, oe = task_arrays(detail, col.n_tasks)
+    keep = np.abs(om) > 1e-8 * _significance(prob, om)
+    assert np.sum(keep) >= col.n_tasks // 2
+    assert np.max(rel_diff(mean[keep], om[keep])) < 5e-3
+    assert np.max(rel_diff(terr[keep], oe[keep])) < 1e-2
+    col.close()
+
+
 def test_fp32_against_fp64_oracle_stream():
     """FP32 path against the FP64 oracle on the FP64 stream (independent
     samples): agreement within 3 sigma of the combined error."""
