@@ -33,6 +33,7 @@ METRIC = "C[f] grid sweeps/s and integrand evals/s, FP32 vs FP64 path, at 1e-4 r
 UNIT = "sweeps/s"
 WORKLOAD = "c2_bose_2to2"
 DT = 0.5          # requested Heun step (bounded by Eq. (16) inside each step)
+CPU_NEVAL = 20_000  # samples per iteration of the oracle tasks timed on the host
 # DRAM bytes per sample-kernel launch from the last ncu capture of this kernel version
 TRAFFIC_BYTES_PER_LAUNCH = 1.529088e6
 # Thread instructions per sample of the 2->2 Bose sample kernel, from the same ncu capture
@@ -389,44 +390,81 @@ def run_native(args, rank, world):
         "clocks": clk,
     }
     if rank == 0 and not args.skip_cpu and WORKLOAD_KEY == "c2":
-        out["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds, evals)
+        with oracle_pool() as pool:
+            out["cpu_baseline"] = cpu_baseline(prob, workload()[1], args.cpu_seconds, evals, pool)
     return out
 
 
-def cpu_baseline(prob, seconds, evals):
-    """The oracle, as it stands, on a bounded sample of the same workload:
-    whole tasks (all iterations) at a reduced budget, scaled by evals."""
+def _oracle_tasks(prob, f0, seconds, first=0):
+    """Whole oracle tasks (all iterations, reduced budget) for `seconds`;
+    returns (samples evaluated, elapsed s, tasks)."""
     from dataclasses import replace
 
     from oracle import collision as ocol
     from oracle import vegas
     from oracle.tasks import side_integrals
 
-    neval = 20_000
-    small = replace(prob, processes=tuple(replace(p, neval=neval) for p in prob.processes))
+    small = replace(prob, processes=tuple(replace(p, neval=CPU_NEVAL) for p in prob.processes))
     sis = side_integrals(small)
-    q, f0 = None, workload()[1]
     dists = ocol.distributions(small, f0, 0.0)
+    pts = [5, 40, 70, 100, 120, 20, 60, 90]
     t0 = time.perf_counter()
     done = 0
-    k = 0
-    pts = [5, 40, 70, 100, 120, 20, 60, 90]
+    k = first
     while time.perf_counter() - t0 < seconds:
         si_idx = k % len(sis)
-        i = pts[(k // len(sis)) % len(pts)]
+        i = pts[(k // len(sis)) % len(pts)] % prob.grid.n
         term = k % 2
         si = sis[si_idx]
         p = small.processes[si.process]
         ocol.evaluate_task(small, si_idx, si, i, term, f0, 0.0, vegas.uniform_edges(si.dim, p.nbins), 0,
                            "f32", dists)
-        done += neval * p.nitn
+        done += CPU_NEVAL * p.nitn
         k += 1
-    el = time.perf_counter() - t0
-    evs = done / el
-    return {"value": evs / evals, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "evals_per_s": evs,
-            "sample": f"{k} whole tasks (8 iterations, {neval} samples each) of the same workload, "
-                      f"{el:.1f} s; sweeps/s = oracle evals/s / evals per sweep ({evals:.3g})"}
+    return done, time.perf_counter() - t0, k - first
+
+
+def _oracle_worker(job):
+    prob, f0, seconds, first = job
+    return _oracle_tasks(prob, f0, seconds, first)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(prob, f0, seconds, evals, pool=None, single=True):
+    """The oracle, as it stands, on a bounded sample of the same workload:
+    whole tasks (all iterations) at a reduced budget, scaled by evals; on
+    one core, and (with a spawn pool) on every host core at once, each
+    worker running its own tasks for the same time."""
+    out = None
+    if single or pool is None:
+        done, el, k = _oracle_tasks(prob, f0, seconds)
+        evs1 = done / el
+        out = {"value": evs1 / evals, "unit": UNIT, "cores": 1, "kind": "oracle", "evals_per_s": evs1,
+               "sample": f"{k} whole tasks ({prob.processes[0].nitn} iterations, {CPU_NEVAL} samples each) of "
+                         f"the same workload, {el:.1f} s on one core; sweeps/s = oracle evals/s / evals per "
+                         f"sweep ({evals:.3g})"}
+    if pool is not None:
+        n = host_cores()
+        res = pool.map(_oracle_worker, [(prob, f0, seconds, 1000 * w) for w in range(n)])
+        evs = sum(d / e for d, e, _ in res)
+        out = {"value": evs / evals, "unit": UNIT, "cores": n, "kind": "oracle", "evals_per_s": evs,
+               "sample": f"{sum(r[2] for r in res)} whole tasks ({prob.processes[0].nitn} iterations, {CPU_NEVAL} "
+                         f"samples each) of the same workload in {n} concurrent processes, {seconds:.1f} s each; "
+                         f"evals/s summed over the processes; sweeps/s = evals/s / evals per sweep ({evals:.3g})",
+               "single_core": out}
+    return out
+
+
+def oracle_pool():
+    """A spawn pool over the host cores (spawn: safe after CUDA use)."""
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(host_cores())
 
 
 def run_reference(args, rank, world):
@@ -434,18 +472,21 @@ def run_reference(args, rank, world):
     prob, _ = workload()
     # evaluations per sweep: 2 species x 128 points x (gain, loss) x nitn x neval
     evals = sum(2 * prob.grid.n * p.nitn * p.neval for p in prob.processes)
+    f0 = workload()[1]
     vals = []
-    for _ in range(args.warmup):
-        cpu_baseline(prob, 1.0, evals)
-    for _ in range(args.steps):
-        vals.append(cpu_baseline(prob, args.ref_seconds, evals))
+    with oracle_pool() as pool:
+        for _ in range(args.warmup):
+            cpu_baseline(prob, f0, 1.0, evals, pool, single=False)
+        for k in range(args.steps):
+            vals.append(cpu_baseline(prob, f0, args.ref_seconds, evals, pool, single=k == args.steps - 1))
     v = statistics.mean(b["value"] for b in vals)
     cb = dict(vals[-1])
     cb["value"] = v
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v if v > 0 else None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded)", "config": {"workload": WORKLOAD, "arm": "CPU oracle, 1 core"},
+            "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOAD, "arm": f"CPU oracle, {cb['cores']} host cores"},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
