@@ -6,15 +6,17 @@ repeated time steps; checkpoints hold everything needed to resume.
 It only assembles a ``workloads.Problem`` and sequences libbest calls
 (``Collision``); every step of the computation runs in the library.
 
-    s = Solver(q_min=0.1, q_max=20.0, n_grid=64)
-    s.initialize_species("phi", lambda q: 1 / (1 + np.exp((q - 3) / 2)), stat="boson", mass=1.0)
-    s.add_process("elastic", ["phi", "phi"], ["phi", "phi"], coupling=1.0, neval=10**6, delta_width=0.01)
-    for _ in range(100):
-        s.evolve_step(dt=1.0, method="heun")
+    s = Solver(q_min=0.05, q_max=25.0, n_grid=96)
+    s.initialize_species("chi", lambda q: 0.4 * np.exp(-(q - 2.0) ** 2), stat="boson", mass=0.7)
+    s.add_process("chichi", ["chi", "chi"], ["chi", "chi"], lambda k, g: g * g * np.ones(k.shape[-1]),
+                  coupling=0.5, neval=4 * 10**5, delta_width=0.02)
+    while s.current_time < 40.0:
+        s.evolve_step(dt=0.5, method="heun")
 
 Differences from the paper's interface, by necessity of running on the GPU:
 the matrix element is |M|^2 = coupling^2 P(s) with P a cubic in the initial
-state's invariant mass squared (``me_coef``), not a Python callable; a mass
+state's invariant mass squared (a callable in the paper's form is accepted
+and reduced to P by probing it, ``matrix_element_polynomial``); a mass
 may depend on time linearly (``set_mass_linear``) or piecewise linearly
 through up to eight knots (``set_mass_table``); ``set_mass_func`` samples a
 callable at given times into such a table.
@@ -25,6 +27,47 @@ import workloads as W
 
 _STATS = {"boson": W.STAT_BE, "be": W.STAT_BE, "fermion": W.STAT_FD, "fd": W.STAT_FD,
           "maxwell": W.STAT_MB, "mb": W.STAT_MB, "classical": W.STAT_MB}
+
+
+def matrix_element_polynomial(fn, coupling, m_in, m_out, p_max, n_probe=256, seed=20260328):
+    """Coefficients (c0, c1, c2, c3) with fn = coupling^2 (c0 + c1 s + c2 s^2
+    + c3 s^3) for a matrix element given as the paper's callable
+    fn(momenta, coupling) -> |M|^2 per sample (Sec. 3A).
+
+    Reading of the callable's argument: momenta has shape (n_legs, 4, N),
+    row k = (E, px, py, pz) of leg k, the initial legs first, N samples
+    (the paper's example reads N from momenta.shape[2]).  The callable is
+    probed on N random configurations (momenta up to p_max, directions
+    uniform, on-shell energies; the final legs drawn independently); s is
+    the initial state's invariant mass squared.  A callable that is not a
+    polynomial of degree <= 3 in s alone (it depends on final momenta or
+    angles, or grows faster) cannot run in the kernels and raises
+    ValueError."""
+    if not coupling:
+        raise ValueError("the coupling must be non-zero to separate |M|^2 = coupling^2 P(s)")
+    rng = np.random.default_rng(seed)
+    legs = []
+    for m in list(m_in) + list(m_out):
+        p = rng.uniform(0.0, p_max, n_probe)
+        ct = rng.uniform(-1.0, 1.0, n_probe)
+        ph = rng.uniform(0.0, 2.0 * np.pi, n_probe)
+        st = np.sqrt(1.0 - ct * ct)
+        legs.append(np.stack([np.sqrt(p * p + m * m), p * st * np.cos(ph), p * st * np.sin(ph), p * ct]))
+    momenta = np.stack(legs)
+    vals = np.broadcast_to(np.asarray(fn(momenta, coupling), dtype=np.float64), (n_probe,)) / coupling ** 2
+    if not np.all(np.isfinite(vals)):
+        raise ValueError("the matrix element is not finite on the probe configurations")
+    tot = momenta[:len(m_in)].sum(axis=0)
+    s = tot[0] ** 2 - tot[1] ** 2 - tot[2] ** 2 - tot[3] ** 2
+    scale = max(float(np.max(np.abs(s))), 1e-300)
+    a = np.polynomial.polynomial.polyfit(s / scale, vals, 3)
+    resid = float(np.max(np.abs(np.polynomial.polynomial.polyval(s / scale, a) - vals)))
+    if resid > 1e-8 * max(float(np.max(np.abs(vals))), 1e-300):
+        raise ValueError("the matrix element is not a cubic polynomial of the initial state's s alone "
+                         f"(fit residual {resid:.3g}); give P(s) coefficients instead")
+    c = a / scale ** np.arange(4)
+    c[np.abs(a) <= 1e-12 * max(float(np.max(np.abs(a))), 1e-300)] = 0.0
+    return tuple(float(x) for x in c)
 
 
 class Solver:
@@ -91,14 +134,33 @@ class Solver:
         straight lines."""
         self.set_mass_table(name, times, [float(fn(float(x))) for x in times])
 
-    def add_process(self, name, initial, final, coupling=1.0, neval=10 ** 6, delta_width=0.01, nitn=2,
-                    alpha=0.5, nbins=50, me_coef=(1.0, 0.0, 0.0, 0.0), **options):
-        """Register initial -> final (species names).  ``delta_width`` is the
-        absolute width sigma_E of Eq. (11); ``options`` are further
-        ``workloads.Process`` fields (width_mode, width, strat, ...)."""
-        p = W.Process(name, tuple(self._index(s) for s in initial), tuple(self._index(s) for s in final),
-                      float(coupling), float(delta_width), int(neval), int(nitn), float(alpha), int(nbins),
-                      me_coef=tuple(float(c) for c in me_coef), **options)
+    def add_process(self, name, initial, final, matrix_element=None, coupling=1.0, neval=10 ** 6,
+                    delta_width=0.01, nitn=2, alpha=0.5, nbins=50, me_coef=None, **options):
+        """Register initial -> final (species names).  ``matrix_element`` is
+        the paper's callable |M|^2(momenta, coupling) (see
+        ``matrix_element_polynomial``: it must be a cubic in the initial
+        state's s), or the coefficients (c0, c1, c2, c3) of P(s) with
+        |M|^2 = coupling^2 P(s), or None for |M|^2 = coupling^2 (also
+        ``me_coef=``).  ``delta_width`` is the absolute width sigma_E of
+        Eq. (11); ``options`` are further ``workloads.Process`` fields
+        (width_mode, width, strat, ...)."""
+        if matrix_element is not None and me_coef is not None:
+            raise ValueError("give the matrix element either as matrix_element or as me_coef")
+        sp_in = tuple(self._index(s) for s in initial)
+        sp_out = tuple(self._index(s) for s in final)
+        if callable(matrix_element):
+            mass = [self._species[k][1].mass0 for k in sp_in + sp_out]
+            me_coef = matrix_element_polynomial(matrix_element, float(coupling), mass[:len(sp_in)],
+                                                mass[len(sp_in):], self.grid.q_max)
+        elif matrix_element is not None:
+            me_coef = matrix_element
+        if me_coef is None:
+            me_coef = (1.0, 0.0, 0.0, 0.0)
+        me_coef = tuple(float(c) for c in me_coef) + (0.0,) * (4 - len(me_coef))
+        if len(me_coef) != 4:
+            raise ValueError("P(s) has at most four coefficients (a cubic in s)")
+        p = W.Process(name, sp_in, sp_out, float(coupling), float(delta_width), int(neval), int(nitn),
+                      float(alpha), int(nbins), me_coef=me_coef, **options)
         self._processes.append(p)
         self._invalidate()
 

@@ -70,3 +70,47 @@ def test_mass_table_marshalled_into_the_config():
     a, b = cfg.species[0], cfg.species[1]
     assert a.n_mass_knots == 0 and a.mass0 == 0.3 and a.mass1 == 0.2
     assert b.n_mass_knots == 3 and list(b.mass_t[:3]) == [0.5, 1.5, 3.0] and list(b.mass_m[:3]) == [2.0, 1.0, 0.0]
+
+
+def _s_of(momenta, n_in=2):
+    tot = momenta[:n_in].sum(axis=0)
+    return tot[0] ** 2 - tot[1] ** 2 - tot[2] ** 2 - tot[3] ** 2
+
+
+def test_matrix_element_callable_reduced_to_p_of_s():
+    """A callable |M|^2(momenta, coupling) that is a cubic in the initial
+    state's s is reduced to its coefficients; a constant one to (1, 0, 0, 0)."""
+    from paper_2603_28848_gb300.solver import matrix_element_polynomial
+    const = matrix_element_polynomial(lambda k, g: g * g * np.ones(k.shape[2]), 0.7, [1.0, 1.0], [1.0, 1.0], 20.0)
+    assert np.allclose(const, (1.0, 0.0, 0.0, 0.0), rtol=0, atol=1e-12)
+    want = (0.5, 0.3, 0.05, 0.002)
+    fn = lambda k, g: g ** 2 * (want[0] + want[1] * _s_of(k) + want[2] * _s_of(k) ** 2 + want[3] * _s_of(k) ** 3)
+    got = matrix_element_polynomial(fn, 1.3, [0.5, 0.8], [0.5, 0.8, 0.1], 10.0)
+    assert np.allclose(got, want, rtol=1e-7, atol=0)
+    # the same through the solver, with the paper's argument order
+    s = Solver(0.1, 10.0, 8)
+    s.initialize_species("A", lambda q: np.exp(-q), stat="maxwell", mass=0.5)
+    s.initialize_species("B", lambda q: np.exp(-q), stat="maxwell", mass=0.8)
+    s.add_process("AB", ["A", "B"], ["A", "B"], fn, coupling=1.3, neval=100)
+    s.add_process("AB2", ["A", "B"], ["A", "B"], (2.0, 0.1), coupling=1.0, neval=100)
+    p = s.problem().processes
+    assert np.allclose(p[0].me_coef, want, rtol=1e-7) and p[1].me_coef == (2.0, 0.1, 0.0, 0.0)
+    with pytest.raises(ValueError):
+        s.add_process("both", ["A", "B"], ["A", "B"], fn, me_coef=(1.0,))
+
+
+def test_matrix_element_not_a_cubic_in_s_is_refused():
+    """Dependence on a final momentum (a t-channel invariant), a quartic in s
+    and a zero coupling cannot be represented and raise."""
+    from paper_2603_28848_gb300.solver import matrix_element_polynomial
+
+    def t_channel(k, g):
+        d = k[0] - k[2]
+        return g * g * (1.0 + 0.1 * (d[0] ** 2 - d[1] ** 2 - d[2] ** 2 - d[3] ** 2))
+
+    with pytest.raises(ValueError):
+        matrix_element_polynomial(t_channel, 1.0, [1.0, 1.0], [1.0, 1.0], 20.0)
+    with pytest.raises(ValueError):
+        matrix_element_polynomial(lambda k, g: g * g * _s_of(k) ** 4, 1.0, [1.0, 1.0], [1.0, 1.0], 20.0)
+    with pytest.raises(ValueError):
+        matrix_element_polynomial(lambda k, g: np.ones(k.shape[2]), 0.0, [1.0, 1.0], [1.0, 1.0], 20.0)
