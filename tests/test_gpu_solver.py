@@ -55,3 +55,40 @@ def test_solver_checkpoint_resumes_bitwise(tmp_path):
     r.evolve_step(0.5)
     assert np.array_equal(a, r.distribution("phi"))
     r.close()
+
+
+def test_solver_with_callable_matrix_element_and_mass_function():
+    """A matrix element given as a callable of (momenta, coupling) and a mass
+    given as a function of time run through the library: the Solver's steps
+    equal direct steps on the problem with the fitted P(s) and the knot table,
+    and the library's m(t) follows the table."""
+    import torch
+    from paper_2603_28848_gb300 import Collision
+
+    def me(k, g):
+        tot = k[0] + k[1]
+        s2 = tot[0] ** 2 - tot[1] ** 2 - tot[2] ** 2 - tot[3] ** 2
+        return g * g * (0.8 + 0.05 * s2)
+
+    s = Solver(q_min=0.1, q_max=15.0, n_grid=20, seed=9)
+    s.initialize_species("chi", lambda q: 0.3 * np.exp(-0.5 * (q - 2.0) ** 2) + 0.05, stat="boson", mass=1.0)
+    s.add_process("chichi", ["chi", "chi"], ["chi", "chi"], me, coupling=0.9, neval=3000, delta_width=0.02)
+    s.set_mass_func("chi", lambda t: 1.0 if t < 1.6 else 0.7, [1.0, 1.5, 1.6, 10.0])
+    prob = s.problem()
+    assert np.allclose(prob.processes[0].me_coef, (0.8, 0.05, 0.0, 0.0), rtol=1e-7, atol=1e-12)
+    for _ in range(3):
+        s.evolve_step(0.4, "heun")
+    got = s.distribution("chi")
+    col = Collision(prob, W.PREC_FP32)
+    q = W.grid_points(s.grid)
+    logf = torch.tensor(np.log(0.3 * np.exp(-0.5 * (q - 2.0) ** 2) + 0.05), device="cuda")[None].contiguous()
+    t = torch.tensor([1.0], dtype=torch.float64, device="cuda")
+    dt = torch.tensor([0.0], dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        dt.fill_(0.4)
+        col.step_heun(logf, t, dt)
+    assert np.array_equal(got, np.exp(logf[0].cpu().numpy()))
+    assert np.allclose(col.species_masses(1.55), [0.85], rtol=1e-14)
+    assert np.allclose(col.species_masses(2.0), [0.7], rtol=1e-14)
+    col.close()
+    s.close()
