@@ -399,7 +399,6 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
     const R inv_step = static_cast<R>(1.0 / (g.log_spaced ? g.log_step / 0.6931471805599453 : g.log_step));
     const int ncoef = 4 * (g.n_grid - 1);
     const R* knots = s_spline + g.n_species * ncoef;
-    const SpeciesConst* scst = P.sconst;
     __syncthreads();
 
     // ---- samples ------------------------------------------------------------
