@@ -468,7 +468,8 @@ def oracle_pool():
 
 
 def run_reference(args, rank, world):
-    """The oracle timed on the host cores (the reference arm of this build)."""
+    """The oracle timed on the host cores (the reference arm: there is no other
+    implementation of the paper's method to run)."""
     prob, _ = workload()
     # evaluations per sweep: 2 species x 128 points x (gain, loss) x nitn x neval
     evals = sum(2 * prob.grid.n * p.nitn * p.neval for p in prob.processes)

@@ -10,7 +10,7 @@ halves, swaps words and XORs the high halves with the other counter words and
 the key; the key is bumped by the two Weyl constants between rounds.
 
 The paper draws its samples from the ``vegas`` library's generator
-(Sec. 3A); this build instead fixes a counter-based stream so that the GPU
+(Sec. 3A); here a counter-based stream is fixed instead, so that the GPU
 and this oracle consume identical samples.  Stream definition (a reading):
 
   key     = (seed mod 2^32, seed div 2^32)
