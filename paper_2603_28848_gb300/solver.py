@@ -85,6 +85,7 @@ class Solver:
         self._processes = []
         self._col = None
         self._logf = self._t = self._dt = None
+        self.history = None          # what load_checkpoint found saved beside the state
 
     # -- set-up ---------------------------------------------------------------
     def q(self):
@@ -207,17 +208,21 @@ class Solver:
         return {name: (float(n[k]), float(rho[k])) for k, (name, _, _) in enumerate(self._species)}
 
     # -- checkpoints ------------------------------------------------------------
-    def save_checkpoint(self, path):
+    def save_checkpoint(self, path, history=None):
         """Grid, species, processes, distributions, time and the library state
-        (VEGAS maps, allocations, widths, counter) in one .npz file."""
+        (VEGAS maps, allocations, widths, counter) in one .npz file, plus an
+        optional user history (anything JSON can hold; numpy arrays are
+        stored as lists), returned as ``.history`` by ``load_checkpoint``."""
         import json
         col = self._context()
         spec = {"grid": vars(self.grid), "precision": self.precision, "seed": self.seed, "eps_dt": self.eps_dt,
                 "tail_points": self.tail_points, "e_cut": self.e_cut,
                 "expansion": None if self.expansion is None else vars(self.expansion),
                 "species": [vars(s) for _, s, _ in self._species],
-                "processes": [vars(p) for p in self._processes]}
-        np.savez(path, spec=np.frombuffer(json.dumps(spec).encode(), dtype=np.uint8),
+                "processes": [vars(p) for p in self._processes],
+                "history": history}
+        as_json = lambda o: o.tolist() if hasattr(o, "tolist") else float(o)
+        np.savez(path, spec=np.frombuffer(json.dumps(spec, default=as_json).encode(), dtype=np.uint8),
                  logf=self._logf.cpu().numpy(), t=np.array([self.current_time]),
                  state=np.frombuffer(col.save_state(), dtype=np.uint8))
 
@@ -244,6 +249,7 @@ class Solver:
         if spec["expansion"] is not None:
             s.expansion = W.Expansion(**spec["expansion"])
         s.current_time = float(z["t"][0])
+        s.history = spec.get("history")
         col = s._context()
         col.load_state(z["state"].tobytes())
         s._logf.copy_(s._to_dev(logf))

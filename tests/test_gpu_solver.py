@@ -45,12 +45,14 @@ def test_solver_checkpoint_resumes_bitwise(tmp_path):
     s.evolve_step(0.5)
     s.evolve_step(0.5)
     path = str(tmp_path / "run.npz")
-    s.save_checkpoint(path)
+    history = {"t": [1.0, 1.5, 2.0], "n": np.array([0.2, 0.21, 0.22]), "note": "two Heun steps"}
+    s.save_checkpoint(path, history=history)
     s.evolve_step(0.5)
     s.evolve_step(0.5)
     a = s.distribution("phi")
     s.close()
     r = Solver.load_checkpoint(path)
+    assert r.history == {"t": [1.0, 1.5, 2.0], "n": [0.2, 0.21, 0.22], "note": "two Heun steps"}
     r.evolve_step(0.5)
     r.evolve_step(0.5)
     assert np.array_equal(a, r.distribution("phi"))
