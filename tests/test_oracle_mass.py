@@ -56,3 +56,16 @@ def test_masses_per_species_and_list_knots():
     assert b.mass_table == ((0.0, 0.0), (2.0, 4.0))
     prob = Problem(Grid(4, 0.1, 1.0), (a, b), (Process("ab", (0, 1), (0, 1)),))
     assert np.array_equal(masses(prob, 1.0), [1.0, 2.0])
+
+
+def test_table_equals_library_interpolation():
+    """Random tables against numpy's piecewise-linear interpolation (which
+    also holds the end values outside the knots)."""
+    rng = np.random.default_rng(7)
+    for _ in range(50):
+        k = int(rng.integers(2, 9))
+        tk = np.cumsum(rng.uniform(0.01, 2.0, k)) - 1.0
+        mk = rng.uniform(0.0, 3.0, k)
+        sp = Species("phi", STAT_BE, 0.0, 0.0, tuple(zip(tk, mk)))
+        for t in rng.uniform(tk[0] - 1.0, tk[-1] + 1.0, 20):
+            assert mass_of(sp, t) == pytest.approx(np.interp(t, tk, mk), rel=1e-13, abs=1e-15)
