@@ -114,6 +114,18 @@ def _require(t, n, name):
         raise BestError(f"{name} must have {n} elements, got {t.numel()}")
 
 
+def _require_opt(t, n, name):
+    """As _require, for an optional output (None: the library's own buffer)."""
+    if t is not None:
+        _require(t, n, name)
+
+
+def _require_time(t_dev, dt_dev):
+    """t and dt of a device-side step: one-element CUDA float64 tensors."""
+    _require(t_dev, 1, "t")
+    _require(dt_dev, 1, "dt")
+
+
 class Collision:
     """One context of libbest: the tasks, VEGAS maps and device state of a
     problem.  ``precision``: workloads.PREC_FP64 or PREC_FP32."""
@@ -146,6 +158,8 @@ class Collision:
         import torch
         n = self.n_species * self.n_grid
         _require(f, n, "f")
+        _require_opt(C, n, "C")
+        _require_opt(err, n, "err")
         if C is None:
             C = torch.empty_like(f)
         if err is None:
@@ -156,6 +170,8 @@ class Collision:
 
     def step_euler(self, logf, t_dev, dt_dev, C=None, stream=None):
         _require(logf, self.n_species * self.n_grid, "logf")
+        _require_time(t_dev, dt_dev)
+        _require_opt(C, self.n_species * self.n_grid, "C")
         check(self.lib.best_step_euler(self.ctx, _ptr(logf), _ptr(t_dev), _ptr(dt_dev), _ptr(C),
                                        _stream(stream)), self.ctx)
 
@@ -164,6 +180,8 @@ class Collision:
         import torch
         n = self.n_species * self.n_grid
         _require(logf, n, "logf")
+        _require_opt(C, n, "C")
+        _require_opt(err, n, "err")
         if C is None:
             C = torch.empty_like(logf)
         if err is None:
@@ -175,12 +193,19 @@ class Collision:
     def step_stage(self, method, stage, logf, k1, t_dev, dt_dev, k2=None, fstar=None, stream=None):
         """One stage of an Euler (method 0) or Heun (method 1) step from an
         assembled C (best_step_stage)."""
-        _require(logf, self.n_species * self.n_grid, "logf")
+        n = self.n_species * self.n_grid
+        _require(logf, n, "logf")
+        _require(k1, n, "k1")
+        _require_opt(k2, n, "k2")
+        _require_opt(fstar, n, "fstar")
+        _require_time(t_dev, dt_dev)
         check(self.lib.best_step_stage(self.ctx, int(method), int(stage), _ptr(logf), _ptr(k1), _ptr(k2), _ptr(fstar),
                                        _ptr(t_dev), _ptr(dt_dev), _stream(stream)), self.ctx)
 
     def step_heun(self, logf, t_dev, dt_dev, C=None, stream=None):
         _require(logf, self.n_species * self.n_grid, "logf")
+        _require_time(t_dev, dt_dev)
+        _require_opt(C, self.n_species * self.n_grid, "C")
         check(self.lib.best_step_heun(self.ctx, _ptr(logf), _ptr(t_dev), _ptr(dt_dev), _ptr(C),
                                       _stream(stream)), self.ctx)
 
@@ -189,6 +214,7 @@ class Collision:
         `stream` (a created torch.cuda.Stream; defaults to a private one)."""
         import torch
         _require(logf, self.n_species * self.n_grid, "logf")
+        _require_time(t_dev, dt_dev)
         if stream is None:
             if getattr(self, "_graph_stream", None) is None:
                 self._graph_stream = torch.cuda.Stream()

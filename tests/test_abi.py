@@ -7,6 +7,7 @@ import re
 import shutil
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -87,3 +88,20 @@ def test_struct_layout_matches_c(tmp_path):
 def test_build_targets_sm103a():
     from paper_2603_28848_gb300 import buildlib as b
     assert "arch=compute_103a,code=sm_103a" in b.ARCH
+
+
+def test_binding_rejects_tensors_the_library_cannot_take():
+    """Device pointers go to the library unchecked, so the binding refuses
+    host tensors, other dtypes, wrong sizes and non-scalar step times before
+    any call (checked here without a GPU: every CPU tensor is refused)."""
+    import torch
+    from paper_2603_28848_gb300 import BestError, _require, _require_opt, _require_time
+    with pytest.raises(BestError):
+        _require(torch.zeros(4, dtype=torch.float64), 4, "f")
+    with pytest.raises(BestError):
+        _require(np.zeros(4), 4, "f")
+    with pytest.raises(BestError):
+        _require_time(torch.zeros(1, dtype=torch.float64), torch.zeros(1, dtype=torch.float64))
+    with pytest.raises(BestError):
+        _require_opt(torch.zeros(4, dtype=torch.float32), 4, "C")
+    _require_opt(None, 4, "C")                       # None: the library's own buffer
