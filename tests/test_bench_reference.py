@@ -24,3 +24,6 @@ def test_reference_arm_json_line():
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert cb["single_core"]["cores"] == 1 and cb["single_core"]["value"] > 0
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    # the per-step time is the wall time each timed step actually ran, not an extrapolation
+    assert d["timed"]["steps"] == 2 and d["timed"]["samples_per_step"] > 0
+    assert 0.4e3 < d["ms_per_step"] < 30e3
