@@ -16,6 +16,7 @@ Modules (each function cites the passage of the paper it restates):
   width        fractional Gaussian width and its error-threshold controller (App. C)
   stratified   adaptive stratified sampling on top of the map (the vegas library's default)
   moments      number and energy densities for conservation checks (Sec. 5C)
+  budget       variance-driven per-task sample budgets (Sec. 3D integrator reuse, App. C)
   adjoint      the fixed-sample integral as a torch function; its reverse and forward derivatives
   implicit     backward-Euler log-space step by dense-Jacobian Newton
 

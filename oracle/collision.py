@@ -37,6 +37,7 @@ from typing import Dict
 import numpy as np
 
 from workloads import PREC_FP32
+from . import budget as obudget
 from . import philox, stratified, vegas, width as owidth
 from .spline import ETA, Distribution
 from .tasks import SIDE_IN, side_integrals, task_id
@@ -191,6 +192,7 @@ class State:
     widths: Dict[int, float] = field(default_factory=dict)
     width_rel: Dict[int, float] = field(default_factory=dict)
     strata: Dict[int, np.ndarray] = field(default_factory=dict)
+    budgets: Dict[int, int] = field(default_factory=dict)     # variance-driven budgets of the next sweep
 
 
 def task_budget(proc, i):
@@ -202,7 +204,7 @@ def task_budget(proc, i):
 
 
 def evaluate_task(problem, si_index, si, i, term, f, t, edges, call, mode="f64", dists=None, w_frac=None,
-                  strata=None):
+                  strata=None, N=None):
     """Run the nitn VEGAS iterations of one task.
 
     Returns (mean, err, edges_after, per-iteration list of (mean, var),
@@ -216,7 +218,7 @@ def evaluate_task(problem, si_index, si, i, term, f, t, edges, call, mode="f64",
     m = masses(problem, t)
     f_obs = f[si.species][i]
     D = si.dim
-    N = task_budget(proc, i)
+    N = task_budget(proc, i) if N is None else int(N)
     tid = task_id(si_index, i, term, problem.grid.n)
     strat = bool(getattr(proc, "strat", 0))
     if strat:
@@ -275,6 +277,7 @@ def collision(problem, f, t, state, mode="f64", points=None):
     dists = distributions(problem, f, t)
     widths = {p: state.widths.get(p, proc.width) for p, proc in enumerate(problem.processes)}
     per_process = {p: ([], []) for p in range(len(problem.processes))}
+    used = {p: [] for p in range(len(problem.processes))}          # (task id, budget, mean, err)
     for k, si in enumerate(side_integrals(problem)):
         nb = problem.processes[si.process].nbins
         for i in pts:
@@ -284,8 +287,11 @@ def collision(problem, f, t, state, mode="f64", points=None):
                 edges = state.maps.get(tid)
                 if edges is None:
                     edges = vegas.uniform_edges(si.dim, nb)
+                N = state.budgets.get(tid, task_budget(problem.processes[si.process], i))
                 mean, err, edges, _, alloc = evaluate_task(problem, k, si, i, term, f, t, edges, state.call,
-                                                           mode, dists, widths[si.process], state.strata.get(tid))
+                                                           mode, dists, widths[si.process], state.strata.get(tid),
+                                                           N)
+                used[si.process].append((tid, N, mean, err))
                 state.maps[tid] = edges
                 if alloc is not None:
                     state.strata[tid] = alloc
@@ -300,6 +306,13 @@ def collision(problem, f, t, state, mode="f64", points=None):
         rel = owidth.relative_error(*per_process[p])
         state.widths[p] = owidth.adapt(widths[p], rel, proc)
         state.width_rel[p] = rel
+        if getattr(proc, "budget", 0) and used[p]:
+            # variance-driven budgets of the next sweep; the pool is the
+            # process's tasks evaluated here, its total their configured budgets
+            tids, Ns, means, errs = (np.array(c) for c in zip(*used[p]))
+            total = float(sum(task_budget(proc, (tid // 2) % n) for tid in tids))
+            nxt = obudget.next_budgets(Ns, means, errs, total, proc.neval_min, proc.neval_max)
+            state.budgets.update({int(tid): int(b) for tid, b in zip(tids, nxt)})
     state.call += 1
     return C, np.sqrt(var), detail
 

@@ -101,6 +101,13 @@ class Process:
     # |M|^2 = coupling^2 * (c0 + c1 s + c2 s^2 + c3 s^3), s the squared
     # invariant mass of the initial state (constant |M|^2 by default).
     me_coef: Tuple[float, float, float, float] = (1.0, 0.0, 0.0, 0.0)
+    # Variance-driven budgets: budget = 1 re-sets the per-task samples per
+    # iteration after every sweep in proportion to the last sweep's relative
+    # variance per sample, within [neval_min, neval_max], keeping the sum of
+    # the configured budgets of the process (neval or neval_per_point).
+    budget: int = 0
+    neval_min: int = 0
+    neval_max: int = 0
 
 
 @dataclass(frozen=True)
@@ -192,18 +199,22 @@ def c3_cannibal_2to3(n=256, neval=4_000_000, nitn=10, with_2to2=False):
     return prob, f0
 
 
-def c4_multi_species(n=512, nmin=100_000, nmax=10_000_000, nitn=2):
+def c4_multi_species(n=512, nmin=100_000, nmax=10_000_000, nitn=2, variance_budgets=False):
     """Two coupled species (A: BE, m(t)=1+0.1t; B: FD, m=0.3) with
     AB->AB, AA->AAA and AAA->BB, radiation-dominated expansion
     (a0=1, t0=1), 512 log points on [0.01,25], uneven budgets
-    N_i = nmin (nmax/nmin)^(i/(n-1)) per grid point."""
+    N_i = nmin (nmax/nmin)^(i/(n-1)) per grid point; with variance_budgets
+    that schedule is the first sweep's, and later sweeps re-set every task's
+    budget from the last sweep's variance within [nmin, nmax], keeping the
+    schedule's total."""
     grid = Grid(n, 0.01, 25.0, True)
     sp = (Species("A", STAT_BE, 1.0, 0.1), Species("B", STAT_FD, 0.3, 0.0))
     i = np.arange(n)
     sched = tuple(int(round(nmin * (nmax / nmin) ** (k / max(n - 1, 1)))) for k in i)
-    pr = (Process("AB->AB", (0, 1), (0, 1), 1.0, 0.01, nmin, nitn, 0.5, 50, sched),
-          Process("AA->AAA", (0, 0), (0, 0, 0), 1.0, 0.01, nmin, nitn, 0.5, 50, sched),
-          Process("AAA->BB", (0, 0, 0), (1, 1), 1.0, 0.01, nmin, nitn, 0.5, 50, sched))
+    vb = dict(budget=1, neval_min=nmin, neval_max=nmax) if variance_budgets else {}
+    pr = (Process("AB->AB", (0, 1), (0, 1), 1.0, 0.01, nmin, nitn, 0.5, 50, sched, **vb),
+          Process("AA->AAA", (0, 0), (0, 0, 0), 1.0, 0.01, nmin, nitn, 0.5, 50, sched, **vb),
+          Process("AAA->BB", (0, 0, 0), (1, 1), 1.0, 0.01, nmin, nitn, 0.5, 50, sched, **vb))
     prob = Problem(grid, sp, pr, seed=SEEDS[3], expansion=Expansion(1.0, 1.0))
     q = grid_points(grid)
     fA = 1.0 / np.expm1(np.sqrt(q * q + 1.0))
