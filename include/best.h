@@ -123,7 +123,25 @@ typedef struct {
     int32_t strat_max_hcubes;   /* 1 .. 2^20 */
     double strat_beta;     /* >= 0 */
     double me_coef[4];     /* |M|^2 = coupling^2 (c0 + c1 s + c2 s^2 + c3 s^3), see below */
+    int32_t budget;        /* 1: variance-driven budgets (see below) */
+    int32_t sides;         /* side integrals of Eq. (7) evaluated: 0 all; 1 observed leg initial only;
+                              2 observed leg final only (e.g. C_3 alone, Sec. 5D) */
+    int64_t neval_min, neval_max;   /* budget = 1: bounds of a task's samples per iteration */
 } best_process;
+
+/* Variance-driven budgets (budget = 1; the paper reuses each grid point's
+ * integrator from step to step, Sec. 3D, and its budget per point need not
+ * be uniform): the first evaluation uses the configured budgets (neval or
+ * neval_per_point); after every evaluation each of the process's tasks t
+ * gets N_t' = lambda v_t with v_t = N_t (err_t / I_t)^2 its relative variance
+ * per sample (0 where I_t = 0 or a value is not finite), rounded down to a
+ * multiple of 256 and held within [neval_min, neval_max]; lambda is found by
+ * 200 bisection steps so that sum_t min(max(lambda v_t, neval_min),
+ * neval_max) stays at the sum of the configured budgets of the process's
+ * tasks in this context.  All on the device (no host round trip, so the
+ * steps stay capturable); the budgets persist like the maps and are
+ * checkpointed.  Needs 2 <= neval_min <= neval_max <= 2^31 with
+ * neval_max * dim <= 2^33; not combined with strat. */
 
 typedef struct {
     best_grid grid;
@@ -230,15 +248,22 @@ best_status best_evolve(best_ctx* ctx, int32_t method, int32_t n_steps, double* 
 
 /*
  * Project autotuner of the sample kernel's launch shape: runs one sweep of
- * f_dev at time t with each compiled variant of the sample kernel (register
- * budgets for 2..5 CTAs per SM; the persistent grid and the work partition
- * follow from the variant's occupancy), times the sample-kernel launches
- * with CUDA events, keeps the fastest, and restores the VEGAS maps, the
- * per-task scales and the evaluation counter, so that the context's later
- * results do not depend on whether it was tuned (beyond summation order in
- * the FP32 path).  Synchronous; allocates a temporary copy of the maps.
- * *ctas_per_sm (may be NULL) receives the chosen budget.
+ * f_dev at time t with each compiled variant of the sample kernel -- its
+ * register budget (2..10 CTAs per SM), threads per CTA (128, 256, 512) and
+ * samples a lane evaluates per step (1, or 2 in packed FP32x2 arithmetic);
+ * the persistent grid and the work partition follow from the variant's
+ * occupancy -- times the sample-kernel launches with CUDA events, keeps the
+ * fastest, and restores the VEGAS maps, the per-task scales, the budgets and
+ * the evaluation counter, so that the context's later results do not depend
+ * on whether it was tuned (beyond summation order in the FP32 path).
+ * Synchronous; allocates a temporary copy of the maps.  *ctas_per_sm (may be
+ * NULL) receives the chosen budget; best_launch_shape reports the rest.
  */
+/* The sample kernel's current launch shape: CTAs per SM of its register
+ * budget, threads per CTA and samples per lane per step (any may be NULL). */
+best_status best_launch_shape(const best_ctx* ctx, int32_t* ctas_per_sm, int32_t* threads,
+                              int32_t* samples_per_lane);
+
 best_status best_autotune(best_ctx* ctx, const double* f_dev, double t, int32_t* ctas_per_sm,
                           void* stream);
 
@@ -302,7 +327,8 @@ best_status best_step_implicit_euler(best_ctx* ctx, double* logf_dev, double t, 
  * Checkpoint of a context's evolving state (the paper checkpoints its
  * integrator states with the distributions, Sec. 3F): the VEGAS maps of
  * every task, the per-task accumulation scales, the evaluation counter and
- * the time state, behind a header with a hash of the configuration.  With
+ * the time state (and the variance-driven budgets, when a process has them),
+ * behind a header with a hash of the configuration.  With
  * the same distribution values, time and step, a context restored from a
  * state continues bit for bit like the one that saved it.  Both calls are
  * synchronous; buffers are host memory of at least best_state_size bytes.
@@ -355,8 +381,17 @@ best_status best_species_masses(const best_ctx* ctx, double t, double* m);
 int32_t best_num_tasks(const best_ctx* ctx);
 int32_t best_num_side_integrals(const best_ctx* ctx);
 
+/* Samples per VEGAS iteration of every task (host array [n_tasks], in the
+ * order of best_get_task_results) that the next sweep will use: the
+ * configured budgets, or the variance-driven ones set after the last sweep.
+ * Synchronises `stream`. */
+best_status best_get_budgets(best_ctx* ctx, int64_t* neval, void* stream);
+
 /* Integrand evaluations of one sweep: in VEGAS iteration `iteration` (one
- * launch of the sample kernel), or in all iterations when iteration < 0. */
+ * launch of the sample kernel), or in all iterations when iteration < 0.
+ * With variance-driven budgets these are the next sweep's budgets as the
+ * device holds them (the call then synchronises the device; -1 on a CUDA
+ * error). */
 int64_t best_sweep_samples(const best_ctx* ctx, int32_t iteration);
 
 /*
@@ -414,9 +449,11 @@ int32_t best_last_launch_count(const best_ctx* ctx);
 /*
  * One VEGAS iteration of one task without allocating device memory.  The
  * paper has no counterpart: this serves callers that cannot call cudaMalloc
- * at the point of use, for example code running inside CUDA-graph capture,
- * or a host application whose device memory is handed out only by its own
- * pool allocator.  It calls no cudaMalloc, cudaFree or other allocating
+ * where they run -- a host application whose device memory is handed out
+ * only by its own pool allocator (a framework that reserved the GPU's memory
+ * up front, a service held to a fixed memory budget), or a latency-bound
+ * loop that must not take the device-wide synchronisation a cudaMalloc or
+ * cudaFree may cause.  It calls no cudaMalloc, cudaFree or other allocating
  * routine, and needs no context.
  *
  * Inputs: cfg (host, as for best_collision_init; precision selects the
@@ -429,7 +466,10 @@ int32_t best_last_launch_count(const best_ctx* ctx);
  * out[1] = sum of w^2, out[2 + d*nbins + b] = sum of w^2 over the samples
  * falling in increment b of dimension d (the training data of the map).
  * The estimate of the iteration is out[0] / neval with variance
- * (out[1]/neval - mean^2) / (neval - 1).
+ * (out[1]/neval - mean^2) / (neval - 1).  Grid values that the spline build
+ * rejects (a value <= 0 or not finite) make every out[] value NaN (the
+ * context path's BEST_ERR_NUMERIC); the call itself still returns BEST_OK,
+ * since it does not wait for the GPU.
  *
  * Device scratch comes from one static array of about 3.5 MiB that every
  * GPU loading the library holds until the process exits.  Limits: grid.n

@@ -23,6 +23,10 @@ Roles inside a side integral (App. A):
   * integrated: the remaining n - 2 legs in index order, each with three
     VEGAS dimensions (r, theta, phi) in that order.
 
+A process may restrict the side integrals evaluated (``sides`` = 1: those
+with the observed leg initial, 2: final), as in the paper's comparison of
+C = 2 C_2 + 3 C_3 with C_3 alone (Sec. 5D).
+
 Task enumeration (shared convention with the CUDA library): side integrals
 are ordered by process, then side (initial before final), then species index;
 task id = (side_integral * n_grid + grid_point) * 2 + term, term 0 = gain and
@@ -89,6 +93,9 @@ def side_integrals(problem) -> List[SideIntegral]:
         legs = sp_in + sp_out
         symmetric = sorted(sp_in) == sorted(sp_out)
         sides = [SIDE_IN] if symmetric else [SIDE_IN, SIDE_OUT]
+        keep = getattr(proc, "sides", 0)           # 1: initial side only, 2: final side only
+        if keep:
+            sides = [s for s in sides if s == keep - 1]
         for side in sides:
             side_species = sp_in if side == SIDE_IN else sp_out
             offset = 0 if side == SIDE_IN else n_in

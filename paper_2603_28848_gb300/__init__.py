@@ -13,7 +13,8 @@ import numpy as np
 from . import _lib
 from ._lib import BestError, check
 
-__all__ = ["Collision", "BestError", "build", "config_from_problem", "fixed_sample_collision"]
+__all__ = ["Collision", "BestError", "build", "config_from_problem", "fixed_sample_collision",
+           "vegas_iteration_noalloc"]
 
 
 def build(verbose=False, force=False):
@@ -70,6 +71,10 @@ def config_from_problem(problem, precision):
         pr[k].strat_beta = float(getattr(p, "strat_beta", 0.75))
         for j, c in enumerate(getattr(p, "me_coef", (1.0, 0.0, 0.0, 0.0))):
             pr[k].me_coef[j] = float(c)
+        pr[k].budget = int(getattr(p, "budget", 0))
+        pr[k].sides = int(getattr(p, "sides", 0))
+        pr[k].neval_min = int(getattr(p, "neval_min", 0))
+        pr[k].neval_max = int(getattr(p, "neval_max", 0))
     cfg = _lib.best_config()
     cfg.grid.n = int(g.n)
     cfg.grid.log_spaced = 1 if g.log_spaced else 0
@@ -346,6 +351,18 @@ class Collision:
                                              err.ctypes.data_as(ctypes.c_void_p), _stream(stream)), self.ctx)
         return mean, err
 
+    def launch_shape(self):
+        """(CTAs per SM, threads per CTA, samples per lane per step) of the sample kernel."""
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(self.lib.best_launch_shape(self.ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), self.ctx)
+        return a.value, b.value, c.value
+
+    def budgets(self, stream=None):
+        """Samples per iteration of every task in the next sweep (int64 array)."""
+        out = np.zeros(self.n_tasks, dtype=np.int64)
+        check(self.lib.best_get_budgets(self.ctx, out.ctypes.data_as(ctypes.c_void_p), _stream(stream)), self.ctx)
+        return out
+
     def maps(self):
         stride = self.lib.best_map_stride(self.ctx)
         out = np.zeros(self.n_tasks * stride)
@@ -446,3 +463,41 @@ def fixed_sample_collision(col, f, t=0.0, masses=None, couplings=None):
     elif not torch.allclose(couplings.detach(), lam_now, rtol=1e-12, atol=0):
         raise BestError("couplings must equal the context's couplings")
     return _FSC.apply(col, f, masses, couplings, float(t))
+
+
+def _task_process(problem, task):
+    """The process whose side integral holds task id `task` (tasks are
+    numbered (side integral * n_grid + point) * 2 + term, side integrals by
+    process, then side, then species)."""
+    n = problem.grid.n
+    si = task // (2 * n) if task >= 0 else -1
+    k = 0
+    for p in problem.processes:
+        sym = sorted(p.species_in) == sorted(p.species_out)
+        count = len(set(p.species_in)) + (0 if sym else len(set(p.species_out)))
+        if 0 <= si < k + count:
+            return p
+        k += count
+    raise BestError(f"task {task} out of range")
+
+
+def vegas_iteration_noalloc(problem, precision, task, f, t, edges, out, iteration=0, call=0, stream=None):
+    """One VEGAS iteration of one task through best_vegas_iteration_noalloc,
+    which allocates no device memory (its scratch is a static device array).
+    f: (n_species * n_grid) grid values; edges: the task's map,
+    D * (nbins + 1) values; out: 2 + D * nbins values (sum w, sum w^2, the
+    per-increment sums of w^2); all contiguous CUDA float64 tensors."""
+    p = _task_process(problem, task)
+    D = 3 * (len(p.species_in) + len(p.species_out) - 2)
+    _require(f, len(problem.species) * problem.grid.n, "f")
+    _require(edges, D * (p.nbins + 1), "edges")
+    _require(out, 2 + D * p.nbins, "out")
+    lib = _lib.load()
+    cfg, keep = config_from_problem(problem, precision)
+    st = lib.best_vegas_iteration_noalloc(ctypes.byref(cfg), int(task), _ptr(f), float(t), _ptr(edges),
+                                          int(iteration) & 0xFFFFFFFF, int(call) & 0xFFFFFFFF, _ptr(out),
+                                          _stream(stream))
+    del keep
+    if st != 0:
+        raise BestError(f"best_vegas_iteration_noalloc: {lib.best_last_error(None).decode()}")
+    return out

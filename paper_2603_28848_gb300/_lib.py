@@ -31,7 +31,8 @@ class best_process(ctypes.Structure):
                 ("alpha", c_double), ("width_mode", c_int32), ("pad_", c_int32), ("width", c_double),
                 ("width_rel_lo", c_double), ("width_rel_hi", c_double), ("width_factor", c_double),
                 ("width_min", c_double), ("width_max", c_double), ("strat", c_int32),
-                ("strat_max_hcubes", c_int32), ("strat_beta", c_double), ("me_coef", c_double * 4)]
+                ("strat_max_hcubes", c_int32), ("strat_beta", c_double), ("me_coef", c_double * 4),
+                ("budget", c_int32), ("sides", c_int32), ("neval_min", c_int64), ("neval_max", c_int64)]
 
 
 class best_config(ctypes.Structure):
@@ -63,6 +64,8 @@ SIGNATURES = {
     "best_collision_jvp": ([c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "best_step_implicit_euler": ([c_void_p, c_void_p, c_double, c_double, c_int32, c_double, c_int32, c_int32,
                                   c_double, c_void_p, c_void_p], c_int32),
+    "best_get_budgets": ([c_void_p, c_void_p, c_void_p], c_int32),
+    "best_launch_shape": ([c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)], c_int32),
     "best_moments": ([c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p], c_int32),
     "best_get_strata": ([c_void_p, c_int32, POINTER(c_int32), POINTER(c_int32), c_void_p], c_int32),
     "best_get_widths": ([c_void_p, c_void_p, c_void_p], c_int32),

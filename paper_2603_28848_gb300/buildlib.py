@@ -8,7 +8,7 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libbest.so")
-SOURCES = ["api.cu", "kernels.cu", "eval_f32.cu", "eval_f32_n6.cu", "eval_f64.cu", "variants.cu", "vjp.cu", "newton.cu", "noalloc.cu", "eval_strat.cu", "vjp_me.cu"]
+SOURCES = ["api.cu", "kernels.cu", "eval_f32.cu", "eval_f32_n6.cu", "eval_f64.cu", "variants.cu", "vjp.cu", "newton.cu", "noalloc.cu", "eval_strat.cu", "vjp_me.cu", "budget.cu", "eval_f32_b.cu", "eval_f32_n6_b.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

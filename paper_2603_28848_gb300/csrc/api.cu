@@ -38,7 +38,7 @@ __global__ void heun_correct_kernel(Geometry, double*, const double*, const doub
 __global__ void stage_kernel(Geometry, int, int, double*, const double*, const double*, double*, double*, double*,
                              TimeState*);
 // variants.cu
-int eval_variants(bool f32, int nmax, void** fn, int* mb, bool strat);
+int eval_variants(bool f32, int nmax, SampleVariant* v, bool strat);
 // vjp.cu
 void* vjp_kernel_ptr(bool f32, int nmax, bool me);
 void* jvp_kernel_ptr(bool f32, int nmax, bool me);
@@ -64,6 +64,8 @@ __global__ void vjp_finish_kernel(Geometry, const SideDesc*, const TaskDesc*, co
                                   double*, double*, double*, double*, double*, int);
 __global__ void spline_adjoint_kernel(Geometry, const double*, const double*, const SpeciesConst*, const TimeState*,
                                       const double*, const double*, double*, double*);
+__global__ void budget_kernel(const BudgetCtl*, const TaskAcc*, TaskDesc*, double*);
+__global__ void plan_kernel(const TaskDesc*, int, const PlanDev*, int, int, int64_t*);
 }  // namespace best
 
 using namespace best;
@@ -102,10 +104,10 @@ struct best_ctx {
     size_t spline_smem = 0;
     size_t refine_smem = 0;
     void* eval_fn = nullptr;
-    int n_variants = 0;             // sample-kernel variants (CTAs-per-SM register budgets)
-    void* variant_fn[4] = {};
-    int variant_mb[4] = {};
+    int n_variants = 0;             // sample-kernel variants (register budget, CTA size, samples per step)
+    SampleVariant variants[kMaxVariants] = {};
     int variant = 0;
+    int eval_threads = kThreads;    // threads per CTA of the selected variant
     int64_t partial_capacity = 0;   // doubles allocated at d_partials
     int launches = 0;
     int max_nitn = 0;
@@ -173,6 +175,15 @@ struct best_ctx {
     int nk_m = 0;
     int n_processes = 0;
     size_t vjp_smem = 0;
+    // variance-driven budgets: per-process controls, the device budgets as last
+    // read back (for host-built partitions), and the device partition builder
+    bool any_budget = false;
+    std::vector<BudgetCtl> bctl;
+    BudgetCtl* d_bctl = nullptr;
+    double* d_bv = nullptr;         // [task] relative variance per sample (scratch)
+    int64_t* d_plan_scratch = nullptr;
+    PlanDev* d_plandev = nullptr;   // [max_nitn]
+    std::vector<int64_t> neval_now;
     // timing of the sample kernel (best_profile_*)
     bool profiling = false;
     std::vector<cudaEvent_t> ev;    // start/stop pairs
@@ -234,6 +245,7 @@ void free_all(best_ctx* c) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
     for (void* b : bufs) cudaFree(b);
+    cudaFree(c->d_bctl); cudaFree(c->d_bv); cudaFree(c->d_plan_scratch); cudaFree(c->d_plandev);
 }
 
 best_status validate(const best_config* cfg) {
@@ -311,6 +323,12 @@ best_status validate(const best_config* cfg) {
                          pr.strat_max_hcubes > (1 << 20)))
             return fail(ctx, BEST_ERR_INVALID, "process %d: stratification needs strat_beta >= 0 and "
                         "1 <= strat_max_hcubes <= 2^20", p);
+        if (pr.budget != 0 && pr.budget != 1) return fail(ctx, BEST_ERR_INVALID, "process %d: budget must be 0 or 1", p);
+        if (pr.sides < 0 || pr.sides > 2) return fail(ctx, BEST_ERR_INVALID, "process %d: sides must be 0, 1 or 2", p);
+        if (pr.budget && (pr.strat || pr.neval_min < 2 || pr.neval_min > pr.neval_max ||
+                          pr.neval_max > (int64_t(1) << 31) || pr.neval_max * 3 * (n - 2) > (int64_t(1) << 33)))
+            return fail(ctx, BEST_ERR_INVALID, "process %d: variance-driven budgets need 2 <= neval_min <= neval_max, "
+                        "neval_max <= 2^31, neval_max * dim <= 2^33, and no stratification", p);
         if (pr.nitn < 1 || pr.nitn > 1000) return fail(ctx, BEST_ERR_INVALID, "process %d: nitn in [1,1000]", p);
         if (pr.nbins < 2 || pr.nbins > 256) return fail(ctx, BEST_ERR_INVALID, "process %d: nbins in [2,256]", p);
         if (!(pr.alpha >= 0.0)) return fail(ctx, BEST_ERR_INVALID, "process %d: alpha must be >= 0", p);
@@ -339,6 +357,21 @@ int group_size(int D, bool f32) {
     return per / a;
 }
 
+// Dynamic shared memory of the sample kernel with `threads` per CTA: spline
+// tables of all species, the map table, per-warp histograms, the reduction
+// scratch and (FP32) the per-warp sample queues, in the kernel's layout.
+size_t sample_smem(const best_ctx* ctx, int threads) {
+    const Geometry& g = ctx->geo;
+    const bool f32 = ctx->precision == BEST_FP32;
+    const size_t rs = f32 ? 4 : 8;
+    const size_t spl = static_cast<size_t>(g.n_species) * 4 * (g.n_grid - 1) + g.n_grid;
+    const size_t map_elems = static_cast<size_t>(kMaxDim) * g.nbins_max;
+    const size_t hist_elems = static_cast<size_t>(threads / 32) * map_elems;
+    return rs * ((spl + 3) & ~size_t(3)) + 2 * rs * map_elems + rs * ((hist_elems + 3) & ~size_t(3)) +
+           2 * 32 * sizeof(double) +
+           (f32 ? sizeof(float) * (threads / 32) * kQueueSlots * queue_words(ctx->nmax_legs) : 0);
+}
+
 // Static partition of the active tasks of one iteration over `grid` CTAs,
 // balanced by an estimate of the cost of a sample group (its samples times
 // the number of dimensions plus a constant).  Segments come out ordered by
@@ -355,8 +388,9 @@ best_status build_plan(best_ctx* ctx, int it, IterPlan& plan) {
     for (int a = 0; a < A; ++a) {
         const TaskDesc& td = ctx->tasks[active[a]];
         const int G = group_size(td.dim, f32);
+        const int64_t N = ctx->any_budget ? ctx->neval_now[active[a]] : td.neval;
         unit[a] = td.strat_H > 0 ? kItem / G : 1;
-        groups[a] = (td.neval + G - 1) / G / unit[a];
+        groups[a] = (N + G - 1) / G / unit[a];
         cost[a] = static_cast<int64_t>(G) * unit[a] * (td.dim + 6);
         cum[a + 1] = cum[a] + groups[a] * cost[a];
     }
@@ -404,9 +438,20 @@ best_status build_plan(best_ctx* ctx, int it, IterPlan& plan) {
     plan.n_active = A;
     plan.n_segs = static_cast<int>(segs.size());
     plan.partial_doubles = off;
+    if (ctx->any_budget) {
+        // the device rebuilds this partition when the budgets change: room for
+        // the largest one (each CTA boundary splits at most one task)
+        int64_t cap = 0, rmax = 0;
+        for (int a = 0; a < A; ++a) {
+            const TaskDesc& td = ctx->tasks[active[a]];
+            cap += record_doubles(td.dim, td.nbins);
+            rmax = std::max(rmax, record_doubles(td.dim, td.nbins));
+        }
+        plan.partial_doubles = std::max(off, cap + static_cast<int64_t>(B) * rmax);
+    }
     CK(dalloc(&plan.d_active, A));
     CK(dalloc(&plan.d_task_seg, A + 1));
-    CK(dalloc(&plan.d_segs, segs.size()));
+    CK(dalloc(&plan.d_segs, ctx->any_budget ? static_cast<size_t>(A) + B : segs.size()));
     CK(dalloc(&plan.d_cta_seg, B + 1));
     CK(cudaMemcpy(plan.d_active, active.data(), A * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(plan.d_task_seg, task_seg.data(), (A + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -421,13 +466,15 @@ best_status set_variant(best_ctx* ctx, int v) {
     int dev = 0, nsm = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    void* fn = ctx->variant_fn[v];
+    void* fn = ctx->variants[v].fn;
+    const int threads = ctx->variants[v].threads;
+    ctx->eval_smem = sample_smem(ctx, threads);
     cudaFuncAttributes fa{};
     CK(cudaFuncGetAttributes(&fa, fn));
     if (static_cast<size_t>(fa.maxDynamicSharedSizeBytes) < ctx->eval_smem)
         CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(ctx->eval_smem)));
     int occ = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, ctx->eval_smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, ctx->eval_smem));
     if (occ < 1) return fail(ctx, BEST_ERR_INVALID, "sample kernel does not fit on an SM");
     // a captured step graph refers to the old partition: drop it
     if (ctx->graph) {
@@ -436,11 +483,18 @@ best_status set_variant(best_ctx* ctx, int v) {
     }
     ctx->eval_fn = fn;
     ctx->variant = v;
+    ctx->eval_threads = threads;
     ctx->grid = nsm * occ;
     for (auto& pl : ctx->plans) {
         cudaFree(pl.d_active); cudaFree(pl.d_task_seg); cudaFree(pl.d_segs); cudaFree(pl.d_cta_seg);
     }
     ctx->plans.assign(ctx->max_nitn, IterPlan{});
+    if (ctx->any_budget) {
+        std::vector<TaskDesc> cur(ctx->tasks.size());
+        CK(cudaMemcpy(cur.data(), ctx->d_tasks, cur.size() * sizeof(TaskDesc), cudaMemcpyDeviceToHost));
+        ctx->neval_now.resize(cur.size());
+        for (size_t t = 0; t < cur.size(); ++t) ctx->neval_now[t] = cur[t].neval;
+    }
     int64_t part_max = 0;
     for (int it = 0; it < ctx->max_nitn; ++it) {
         best_status s = build_plan(ctx, it, ctx->plans[it]);
@@ -453,6 +507,22 @@ best_status set_variant(best_ctx* ctx, int v) {
         ctx->partial_capacity = 0;
         CK(dalloc(&ctx->d_partials, static_cast<size_t>(part_max)));
         ctx->partial_capacity = part_max;
+    }
+    if (ctx->any_budget) {
+        std::vector<PlanDev> pd(ctx->max_nitn);
+        int amax = 0;
+        for (int it = 0; it < ctx->max_nitn; ++it) {
+            const IterPlan& pl = ctx->plans[it];
+            pd[it] = PlanDev{pl.n_active, 0, pl.d_active, pl.d_task_seg, pl.d_segs, pl.d_cta_seg};
+            amax = std::max(amax, pl.n_active);
+        }
+        cudaFree(ctx->d_plandev);
+        cudaFree(ctx->d_plan_scratch);
+        ctx->d_plandev = nullptr;
+        ctx->d_plan_scratch = nullptr;
+        CK(dalloc(&ctx->d_plandev, pd.size()));
+        CK(cudaMemcpy(ctx->d_plandev, pd.data(), pd.size() * sizeof(PlanDev), cudaMemcpyHostToDevice));
+        CK(dalloc(&ctx->d_plan_scratch, static_cast<size_t>(amax) + 1 + 2 * static_cast<size_t>(ctx->grid)));
     }
     return BEST_OK;
 }
@@ -506,7 +576,7 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
             }
             CK(cudaEventRecordWithFlags(ctx->ev[ctx->ev_used], st, rec_flags));
         }
-        CK(cudaLaunchKernel(ctx->eval_fn, dim3(ctx->grid), dim3(kThreads), args, ctx->eval_smem, st));
+        CK(cudaLaunchKernel(ctx->eval_fn, dim3(ctx->grid), dim3(ctx->eval_threads), args, ctx->eval_smem, st));
         if (ctx->profiling) {
             CK(cudaEventRecordWithFlags(ctx->ev[ctx->ev_used + 1], st, rec_flags));
             ctx->ev_used += 2;
@@ -530,6 +600,14 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
         width_control_kernel<<<ctx->n_processes, 256, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_acc,
                                                                ctx->d_wctl, ctx->d_width, ctx->d_width_rel);
         ctx->launches += 1;
+    }
+    if (ctx->any_budget) {
+        // next sweep's budgets from this sweep's estimates, then its partition
+        budget_kernel<<<static_cast<int>(ctx->bctl.size()), 1024, 0, st>>>(ctx->d_bctl, ctx->d_acc, ctx->d_tasks,
+                                                                          ctx->d_bv);
+        plan_kernel<<<1, 1024, 0, st>>>(ctx->d_tasks, ctx->max_nitn, ctx->d_plandev, ctx->grid, f32 ? 1 : 0,
+                                        ctx->d_plan_scratch);
+        ctx->launches += 2;
     }
     CK(cudaGetLastError());
     return BEST_OK;
@@ -564,6 +642,7 @@ bool describe_task(const best_config* cfg, int32_t task, SideDesc* out_sd, TaskD
         std::sort(s_out, s_out + n_out);
         const bool symmetric = n_in == n_out && std::equal(s_in, s_in + n_in, s_out);
         for (int side = 0; side < (symmetric ? 1 : 2); ++side) {
+            if (pr.sides && side != pr.sides - 1) continue;
             const int offset = side == 0 ? 0 : n_in;
             const int cnt = side == 0 ? n_in : n_out;
             const int* sorted = side == 0 ? s_in : s_out;
@@ -641,6 +720,8 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     g.q_min = cfg->grid.q_min;
     g.q_max = cfg->grid.q_max;
     g.log_step = g.log_spaced ? std::log(g.q_max / g.q_min) / (g.n_grid - 1) : (g.q_max - g.q_min) / (g.n_grid - 1);
+    g.inv_step = 1.0 / (g.log_spaced ? g.log_step / 0.6931471805599453 : g.log_step);
+    g.lq0_step = g.log_spaced ? std::log2(g.q_min) * g.inv_step : 0.0;
     g.n_species = cfg->n_species;
     g.expansion = cfg->expansion ? 1 : 0;
     g.a0 = cfg->a0;
@@ -669,6 +750,7 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
         ctx->nmax_legs = std::max(ctx->nmax_legs, n);
         ctx->max_nitn = std::max(ctx->max_nitn, pr.nitn);
         for (int side = 0; side < (symmetric ? 1 : 2); ++side) {
+            if (pr.sides && side != pr.sides - 1) continue;   // a restricted set of side integrals
             const std::vector<int>& sp = side == 0 ? a_in : a_out;
             const int offset = side == 0 ? 0 : n_in;
             std::vector<int> distinct = sp;
@@ -702,6 +784,13 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
         }
     }
     g.n_side = static_cast<int>(ctx->sides.size());
+    for (int p = 0; p < cfg->n_processes; ++p) {
+        bool any = false;
+        for (const SideDesc& sd : ctx->sides) any = any || sd.process == p;
+        if (!any)
+            return bail(fail(ctx, BEST_ERR_INVALID, "process %d: its sides setting leaves no side integral (a "
+                             "process with equal initial and final species has only the initial side)", p));
+    }
     g.nbins_max = nb_max;
     g.map_stride = kMaxDim * (nb_max + 1);
     for (int si = 0; si < g.n_side; ++si) {
@@ -741,6 +830,24 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     }
     g.n_tasks = static_cast<int>(ctx->tasks.size());
     if (static_cast<int64_t>(g.n_tasks) >= (int64_t(1) << 31)) return bail(fail(ctx, BEST_ERR_INVALID, "too many tasks"));
+    // variance-driven budgets: a process's tasks are contiguous (side integrals by process)
+    for (int p = 0; p < cfg->n_processes; ++p) {
+        const best_process& pr = cfg->processes[p];
+        if (!pr.budget) continue;
+        BudgetCtl c{};
+        c.first = -1;
+        for (int t = 0; t < g.n_tasks; ++t) {
+            if (ctx->sides[ctx->tasks[t].si].process != p) continue;
+            if (c.first < 0) c.first = t;
+            c.count = t - c.first + 1;
+            c.total += static_cast<double>(ctx->tasks[t].neval);
+        }
+        if (c.first < 0) continue;
+        c.n_min = pr.neval_min;
+        c.n_max = pr.neval_max;
+        ctx->bctl.push_back(c);
+    }
+    ctx->any_budget = !ctx->bctl.empty();
 
     // ---- launch shape of the sample kernel -------------------------------------------------
     int dev = 0, nsm = 0;
@@ -748,21 +855,20 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
         return bail(fail(ctx, BEST_ERR_CUDA, "no CUDA device"));
     for (const SideDesc& sd : ctx->sides) ctx->any_me = ctx->any_me || sd.me_on;
     // stratified tasks and s-dependent |M|^2 run in the extended instantiations
-    ctx->n_variants = eval_variants(f32, ctx->nmax_legs, ctx->variant_fn, ctx->variant_mb,
-                                    ctx->any_strat || ctx->any_me);
+    ctx->geo.nbins_max = nb_max;                   // (sample_smem reads it)
     {
-        const size_t rs = f32 ? 4 : 8;
-        const size_t spl = static_cast<size_t>(g.n_species) * 4 * (g.n_grid - 1) + g.n_grid;
-        const size_t map_elems = static_cast<size_t>(kMaxDim) * nb_max;
-        const size_t hist_elems = static_cast<size_t>(kThreads / 32) * map_elems;
-        ctx->eval_smem = rs * ((spl + 3) & ~size_t(3)) + 2 * rs * map_elems + rs * ((hist_elems + 3) & ~size_t(3)) +
-                         2 * 32 * sizeof(double) +
-                         (f32 ? sizeof(float) * (kThreads / 32) * kQueueSlots * queue_words(ctx->nmax_legs) : 0);
+        SampleVariant all[kMaxVariants];
+        const int nv = eval_variants(f32, ctx->nmax_legs, all, ctx->any_strat || ctx->any_me);
+        // variants whose tables do not fit one CTA's shared memory are left out
         int max_optin = 0;
         cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (ctx->eval_smem > static_cast<size_t>(max_optin))
+        ctx->n_variants = 0;
+        for (int v = 0; v < nv; ++v)
+            if (sample_smem(ctx, all[v].threads) <= static_cast<size_t>(max_optin))
+                ctx->variants[ctx->n_variants++] = all[v];
+        if (ctx->n_variants == 0)
             return bail(fail(ctx, BEST_ERR_INVALID, "spline and map tables need %zu B of shared memory (max %d)",
-                             ctx->eval_smem, max_optin));
+                             sample_smem(ctx, kThreads), max_optin));
         cudaFuncAttributes fa{};
         ctx->spline_smem = 3 * sizeof(double) * g.n_grid;
         if (cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(&spline_build_kernel)) != cudaSuccess)
@@ -815,6 +921,7 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     }
     TimeState ts{};
     ts.a = 1.0;
+    ts.inv_a = 1.0;
 #define CKI(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return bail(fail(ctx, e_ == cudaErrorMemoryAllocation ? BEST_ERR_OOM : BEST_ERR_CUDA, "%s: %s", #x, cudaGetErrorString(e_))); } while (0)
     CKI(dalloc(&ctx->d_sides, g.n_side));
     CKI(dalloc(&ctx->d_tasks, T));
@@ -897,6 +1004,11 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
         CKI(dalloc(&ctx->d_item_rec, static_cast<size_t>(ctx->strat_total_items) * 2));
         strat_init_kernel<<<T, 256>>>(ctx->d_tasks, ctx->d_strat_m, ctx->d_item_h, 1);
         CKI(cudaGetLastError());
+    }
+    if (ctx->any_budget) {
+        CKI(dalloc(&ctx->d_bctl, ctx->bctl.size()));
+        CKI(cudaMemcpy(ctx->d_bctl, ctx->bctl.data(), ctx->bctl.size() * sizeof(BudgetCtl), cudaMemcpyHostToDevice));
+        CKI(dalloc(&ctx->d_bv, static_cast<size_t>(T)));
     }
     {
         best_status sv = set_variant(ctx, 0);
@@ -1036,6 +1148,16 @@ best_status best_evolve(best_ctx* ctx, int32_t method, int32_t n_steps, double* 
     return BEST_OK;
 }
 
+best_status best_launch_shape(const best_ctx* ctx, int32_t* ctas_per_sm, int32_t* threads,
+                              int32_t* samples_per_lane) {
+    if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
+    const SampleVariant& v = ctx->variants[ctx->variant];
+    if (ctas_per_sm) *ctas_per_sm = v.mb;
+    if (threads) *threads = v.threads;
+    if (samples_per_lane) *samples_per_lane = v.spl;
+    return BEST_OK;
+}
+
 best_status best_autotune(best_ctx* ctx, const double* f_dev, double t, int32_t* ctas_per_sm, void* stream) {
     if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
     if (!f_dev) return fail(ctx, BEST_ERR_INVALID, "f_dev must not be NULL");
@@ -1044,16 +1166,19 @@ best_status best_autotune(best_ctx* ctx, const double* f_dev, double t, int32_t*
     const Geometry& g = ctx->geo;
     const size_t ne = static_cast<size_t>(g.n_tasks) * g.map_stride;
     double *edges0 = nullptr, *prev0 = nullptr, *Ctmp = nullptr;
+    TaskDesc* tasks0 = nullptr;                   // the budgets live in the task descriptors
     TimeState ts0;
-    auto release = [&]() { cudaFree(edges0); cudaFree(prev0); cudaFree(Ctmp); };
+    auto release = [&]() { cudaFree(edges0); cudaFree(prev0); cudaFree(Ctmp); cudaFree(tasks0); };
     if (dalloc(&edges0, ne) != cudaSuccess || dalloc(&prev0, g.n_tasks) != cudaSuccess ||
-        dalloc(&Ctmp, static_cast<size_t>(g.n_species) * g.n_grid) != cudaSuccess) {
+        dalloc(&Ctmp, static_cast<size_t>(g.n_species) * g.n_grid) != cudaSuccess ||
+        dalloc(&tasks0, g.n_tasks) != cudaSuccess) {
         release();
         return fail(ctx, BEST_ERR_OOM, "autotune: no memory for the state backup");
     }
     auto restore = [&]() -> best_status {
         CK(cudaMemcpyAsync(ctx->d_edges, edges0, ne * sizeof(double), cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(ctx->d_prev, prev0, g.n_tasks * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(ctx->d_tasks, tasks0, g.n_tasks * sizeof(TaskDesc), cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(ctx->d_ts, &ts0, sizeof(TimeState), cudaMemcpyHostToDevice, st));
         CK(cudaStreamSynchronize(st));
         return BEST_OK;
@@ -1062,6 +1187,7 @@ best_status best_autotune(best_ctx* ctx, const double* f_dev, double t, int32_t*
     do {
         if (cudaMemcpy(edges0, ctx->d_edges, ne * sizeof(double), cudaMemcpyDeviceToDevice) != cudaSuccess ||
             cudaMemcpy(prev0, ctx->d_prev, g.n_tasks * sizeof(double), cudaMemcpyDeviceToDevice) != cudaSuccess ||
+            cudaMemcpy(tasks0, ctx->d_tasks, g.n_tasks * sizeof(TaskDesc), cudaMemcpyDeviceToDevice) != cudaSuccess ||
             cudaMemcpy(&ts0, ctx->d_ts, sizeof(TimeState), cudaMemcpyDeviceToHost) != cudaSuccess) {
             s = fail(ctx, BEST_ERR_CUDA, "autotune: state backup failed");
             break;
@@ -1070,8 +1196,9 @@ best_status best_autotune(best_ctx* ctx, const double* f_dev, double t, int32_t*
         int best_v = ctx->variant;
         double best_ms = 1e300;
         for (int v = 0; v < ctx->n_variants && s == BEST_OK; ++v) {
-            if ((s = set_variant(ctx, v)) != BEST_OK) break;
+            // restored first: the partition is built from the restored budgets
             if ((s = restore()) != BEST_OK) break;
+            if ((s = set_variant(ctx, v)) != BEST_OK) break;
             ctx->profiling = true;
             ctx->ev_used = 0;
             s = best_collision_eval(ctx, f_dev, t, Ctmp, nullptr, stream);
@@ -1086,9 +1213,9 @@ best_status best_autotune(best_ctx* ctx, const double* f_dev, double t, int32_t*
             }
         }
         if (s != BEST_OK) break;
-        if ((s = set_variant(ctx, best_v)) != BEST_OK) break;
-        s = restore();
-        if (ctas_per_sm) *ctas_per_sm = ctx->variant_mb[best_v];
+        if ((s = restore()) != BEST_OK) break;
+        s = set_variant(ctx, best_v);
+        if (ctas_per_sm) *ctas_per_sm = ctx->variants[best_v].mb;
     } while (false);
     release();
     return s;
@@ -1410,7 +1537,7 @@ int64_t best_state_size(const best_ctx* ctx) {
     const int64_t T = ctx->geo.n_tasks;
     return static_cast<int64_t>(sizeof(StateHeader)) + 8 * T * ctx->geo.map_stride + 8 * T +
            static_cast<int64_t>(sizeof(TimeState)) + 16 * static_cast<int64_t>(ctx->n_processes) +
-           4 * ctx->strat_total_h;
+           4 * ctx->strat_total_h + (ctx->any_budget ? 8 * T : 0);
 }
 
 best_status best_save_state(best_ctx* ctx, void* host_buf, int64_t size) {
@@ -1434,6 +1561,12 @@ best_status best_save_state(best_ctx* ctx, void* host_buf, int64_t size) {
     p += ctx->n_processes * sizeof(double);
     if (ctx->strat_total_h > 0)
         CK(cudaMemcpy(p, ctx->d_strat_m, ctx->strat_total_h * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    p += ctx->strat_total_h * sizeof(int32_t);
+    if (ctx->any_budget) {
+        std::vector<TaskDesc> cur(ctx->geo.n_tasks);
+        CK(cudaMemcpy(cur.data(), ctx->d_tasks, cur.size() * sizeof(TaskDesc), cudaMemcpyDeviceToHost));
+        for (size_t t = 0; t < cur.size(); ++t) std::memcpy(p + 8 * t, &cur[t].neval, 8);
+    }
     return BEST_OK;
 }
 
@@ -1463,6 +1596,18 @@ best_status best_load_state(best_ctx* ctx, const void* host_buf, int64_t size) {
         // the allocation, then the items rebuilt from it
         CK(cudaMemcpy(ctx->d_strat_m, p, ctx->strat_total_h * sizeof(int32_t), cudaMemcpyHostToDevice));
         strat_init_kernel<<<ctx->geo.n_tasks, 256>>>(ctx->d_tasks, ctx->d_strat_m, ctx->d_item_h, 0);
+        CK(cudaGetLastError());
+        CK(cudaDeviceSynchronize());
+    }
+    p += ctx->strat_total_h * sizeof(int32_t);
+    if (ctx->any_budget) {
+        // the budgets, then the partition built from them
+        std::vector<TaskDesc> cur(ctx->geo.n_tasks);
+        CK(cudaMemcpy(cur.data(), ctx->d_tasks, cur.size() * sizeof(TaskDesc), cudaMemcpyDeviceToHost));
+        for (size_t t = 0; t < cur.size(); ++t) std::memcpy(&cur[t].neval, p + 8 * t, 8);
+        CK(cudaMemcpy(ctx->d_tasks, cur.data(), cur.size() * sizeof(TaskDesc), cudaMemcpyHostToDevice));
+        plan_kernel<<<1, 1024>>>(ctx->d_tasks, ctx->max_nitn, ctx->d_plandev, ctx->grid,
+                                 ctx->precision == BEST_FP32 ? 1 : 0, ctx->d_plan_scratch);
         CK(cudaGetLastError());
         CK(cudaDeviceSynchronize());
     }
@@ -1536,12 +1681,29 @@ int32_t best_last_launch_count(const best_ctx* ctx) { return ctx ? ctx->launches
 
 int64_t best_sweep_samples(const best_ctx* ctx, int32_t iteration) {
     if (!ctx) return 0;
+    std::vector<TaskDesc> cur;
+    if (ctx->any_budget) {
+        // the budgets of the next sweep, as the device holds them (synchronises)
+        cur.resize(ctx->tasks.size());
+        if (cudaMemcpy(cur.data(), ctx->d_tasks, cur.size() * sizeof(TaskDesc), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return -1;
+    }
+    const std::vector<TaskDesc>& ts = ctx->any_budget ? cur : ctx->tasks;
     int64_t tot = 0;
-    for (const TaskDesc& td : ctx->tasks) {
+    for (const TaskDesc& td : ts) {
         if (iteration < 0) tot += td.neval * td.nitn;
         else if (td.nitn > iteration) tot += td.neval;
     }
     return tot;
+}
+
+best_status best_get_budgets(best_ctx* ctx, int64_t* neval, void* stream) {
+    if (!ctx || !neval) return fail(ctx, BEST_ERR_INVALID, "NULL argument");
+    CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    std::vector<TaskDesc> cur(ctx->tasks.size());
+    CK(cudaMemcpy(cur.data(), ctx->d_tasks, cur.size() * sizeof(TaskDesc), cudaMemcpyDeviceToHost));
+    for (size_t t = 0; t < cur.size(); ++t) neval[t] = cur[t].neval;
+    return BEST_OK;
 }
 
 best_status best_get_task_results(best_ctx* ctx, double* mean, double* err, void* stream) {

@@ -6,13 +6,14 @@ template __global__ void eval_kernel<double, 4, 1>(EvalParams);
 template __global__ void eval_kernel<double, 5, 1>(EvalParams);
 template __global__ void eval_kernel<double, 6, 1>(EvalParams);
 
-int eval_variants_f64(int nmax, void** fn, int* mb) {
+int eval_variants_f64(int nmax, SampleVariant* v) {
+    void* fn;
     switch (nmax) {
-        case 3: case 4: fn[0] = reinterpret_cast<void*>(&eval_kernel<double, 4, 1>); break;
-        case 5: fn[0] = reinterpret_cast<void*>(&eval_kernel<double, 5, 1>); break;
-        default: fn[0] = reinterpret_cast<void*>(&eval_kernel<double, 6, 1>); break;
+        case 3: case 4: fn = reinterpret_cast<void*>(&eval_kernel<double, 4, 1>); break;
+        case 5: fn = reinterpret_cast<void*>(&eval_kernel<double, 5, 1>); break;
+        default: fn = reinterpret_cast<void*>(&eval_kernel<double, 6, 1>); break;
     }
-    mb[0] = 1;
+    v[0] = {fn, 1, 256, 1};
     return 1;
 }
 }  // namespace best

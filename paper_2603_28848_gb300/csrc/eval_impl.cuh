@@ -70,6 +70,30 @@ struct Acc {
     }
 };
 
+// Energy balance E_in - E_out of Eq. (11) accumulated without losing the
+// rounding of each addition: in FP32 an error-free transformation (Knuth's
+// TwoSum) keeps the running sum s and, in c, the sum of the exact rounding
+// errors of the additions, so that s + c is the sum of the terms to about
+// FP32 precision of the (small) result rather than of the (large) energies;
+// in FP64 a plain sum.
+template <typename R>
+struct EBal {
+    R s, c;
+    __device__ __forceinline__ explicit EBal(R x0) : s(x0), c(R(0)) {}
+    __device__ __forceinline__ void add(R x) {
+        if constexpr (sizeof(R) == 4) {
+            const R t = s + x;
+            const R xp = t - s;
+            const R sp = t - xp;
+            c += (s - sp) + (x - xp);
+            s = t;
+        } else {
+            s += x;
+        }
+    }
+    __device__ __forceinline__ R value() const { return s + c; }
+};
+
 // Spline lookup tables of one species in shared memory.
 template <typename R>
 struct SplineView {
@@ -158,7 +182,7 @@ template <typename R, int NLEG, bool EXT>
 __device__ __forceinline__ R kin_at(const SegConst<R, NLEG>& C, const R* y, R jac, R* r, R& qc, R& Ec) {
     constexpr int NI = NLEG - 2;
     R px = R(0), py = R(0), pz = C.pobs_sig;
-    R dE = C.sgn_obs_E;
+    EBal<R> bal(C.sgn_obs_E);
     R Esum = C.e_obs;                   // E_in + E_out (used when C.frac)
     R Qx = R(0), Qy = R(0), Qz = C.obs_in_p, Ein = C.obs_in_E;   // initial state (used when C.me_on)
     R meas = jac;
@@ -180,7 +204,7 @@ __device__ __forceinline__ R kin_at(const SegConst<R, NLEG>& C, const R* y, R ja
         const R rE = RMath<R>::rsqrt_(E2);
         const R E = E2 * rE;
         cut |= E < C.e_cut;
-        dE = fma(C.sgnE[j], E, dE);
+        bal.add(C.sgnE[j] * E);
         Esum += E;
         if (EXT && C.me_on) {
             const R iw = C.inw[j];
@@ -198,7 +222,8 @@ __device__ __forceinline__ R kin_at(const SegConst<R, NLEG>& C, const R* y, R ja
     const R rEc = RMath<R>::rsqrt_(Ec2 > R(0) ? Ec2 : R(1e-30));
     Ec = Ec2 * rEc;
     cut |= Ec < C.e_cut;
-    dE = fma(C.sgn_cons, Ec, dE);
+    bal.add(C.sgn_cons * Ec);
+    const R dE = bal.value();
     qc = pc2 * (pc2 > R(0) ? RMath<R>::rsqrt_(pc2) : R(0)) * C.a;
     R gauss;
     if (C.frac) {
@@ -222,6 +247,98 @@ __device__ __forceinline__ R kin_at(const SegConst<R, NLEG>& C, const R* y, R ja
         w *= fma(fma(fma(C.me[3], sv, C.me[2]), sv, C.me[1]), sv, C.me[0]);
     }
     return cut ? R(0) : w;
+}
+
+// Packed FP32x2 helpers (one instruction for both halves on sm_100+).
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
+// EBal for two samples, the TwoSum steps packed.
+struct EBal2 {
+    float2 s, c;
+    __device__ __forceinline__ explicit EBal2(float x0) : s(make_float2(x0, x0)), c(make_float2(0.0f, 0.0f)) {}
+    __device__ __forceinline__ void add(float2 x) {
+        const float2 t = add2(s, x);
+        const float2 xp = sub2(t, s);
+        const float2 sp = sub2(t, xp);
+        c = add2(c, add2(sub2(s, sp), sub2(x, xp)));
+        s = t;
+    }
+    __device__ __forceinline__ float2 value() const { return add2(s, c); }
+};
+// 2^x with denormal results flushed to zero (the bare special-function op)
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// kin_at for two samples at once (constant |M|^2), each FP32 operation
+// packed over the pair; the special-function operations stay per sample.
+template <int NLEG>
+__device__ __forceinline__ float2 kin_pair(const SegConst<float, NLEG>& C, const float2* y, float2 jac, float2* r,
+                                           float2& qc, float2& Ec) {
+    constexpr int NI = NLEG - 2;
+    float2 px = bc2(0.0f), py = bc2(0.0f), pz = bc2(C.pobs_sig);
+    EBal2 bal(C.sgn_obs_E);
+    float2 Esum = bc2(C.e_obs);
+    float2 meas = jac, rinv = bc2(1.0f);
+    float emin0 = 3.0e38f, emin1 = 3.0e38f;
+#pragma unroll
+    for (int j = 0; j < NI; ++j) {
+        r[j] = y[3 * j];
+        float2 st, ct, sp, cp;
+        __sincosf(y[3 * j + 1].x, &st.x, &ct.x);
+        __sincosf(y[3 * j + 1].y, &st.y, &ct.y);
+        __sincosf(y[3 * j + 2].x, &sp.x, &cp.x);      // angle phi - pi
+        __sincosf(y[3 * j + 2].y, &sp.y, &cp.y);
+        const float2 p = mul2(r[j], bc2(C.inv_a));
+        const float2 ps = mul2(p, st);
+        const float2 nps = mul2(ps, bc2(-C.sig[j]));   // cos(phi) = -cos(phi - pi)
+        px = fma2(nps, cp, px);
+        py = fma2(nps, sp, py);
+        pz = fma2(mul2(p, bc2(C.sig[j])), ct, pz);
+        const float2 E2 = fma2(p, p, bc2(C.m2[j]));
+        const float2 rE = make_float2(rsqrtf(E2.x), rsqrtf(E2.y));
+        const float2 E = mul2(E2, rE);
+        emin0 = fminf(emin0, E.x);
+        emin1 = fminf(emin1, E.y);
+        bal.add(mul2(bc2(C.sgnE[j]), E));
+        Esum = add2(Esum, E);
+        meas = mul2(meas, mul2(mul2(r[j], r[j]), st));
+        rinv = mul2(rinv, rE);
+    }
+    // conserved leg (Eq. (10), App. A)
+    const float2 pc2 = fma2(px, px, fma2(py, py, mul2(pz, pz)));
+    const float2 Ec2q = add2(pc2, bc2(C.m2c));
+    const float2 rEc = make_float2(rsqrtf(Ec2q.x > 0.0f ? Ec2q.x : 1e-30f), rsqrtf(Ec2q.y > 0.0f ? Ec2q.y : 1e-30f));
+    Ec = mul2(Ec2q, rEc);
+    emin0 = fminf(emin0, Ec.x);
+    emin1 = fminf(emin1, Ec.y);
+    bal.add(mul2(bc2(C.sgn_cons), Ec));
+    const float2 dE = bal.value();
+    const float2 rpc = make_float2(pc2.x > 0.0f ? rsqrtf(pc2.x) : 0.0f, pc2.y > 0.0f ? rsqrtf(pc2.y) : 0.0f);
+    qc = mul2(mul2(pc2, rpc), bc2(C.a));
+    float2 gauss;
+    if (C.frac) {
+        // sigma = w S / 2 with S = E_in + E_out: exponent -2 dE^2 / (w S)^2,
+        // normalisation sigma_ref / sigma = 2 E_obs / S
+        Esum = add2(Esum, Ec);
+        const float2 iS = make_float2(__fdividef(1.0f, Esum.x), __fdividef(1.0f, Esum.y));
+        const float2 x = mul2(dE, iS);
+        const float2 e = mul2(mul2(x, x), bc2(C.gauss_k));
+        gauss = mul2(make_float2(ex2_ftz(e.x), ex2_ftz(e.y)), mul2(bc2(2.0f * C.e_obs), iS));
+    } else {
+        const float2 e = mul2(mul2(dE, dE), bc2(C.gauss_k));
+        gauss = make_float2(ex2_ftz(e.x), ex2_ftz(e.y));
+    }
+    float2 w = mul2(mul2(meas, rinv), mul2(rEc, gauss));
+    w.x = emin0 < C.e_cut ? 0.0f : w.x;
+    w.y = emin1 < C.e_cut ? 0.0f : w.y;
+    return w;
 }
 
 // Statistical factor of Eq. (5) of one sample: the observed leg's factor
@@ -282,50 +399,23 @@ __device__ __forceinline__ R weight_at(const SegConst<R, NLEG>& C, const R* y, R
     return stat_at<R, NLEG>(C, r, qc, Ec, s_spline, knots, g, inv_step, q0, lq0_step, qN, ncoef) * kin;
 }
 
-// STRAT: the instantiation also handles stratified tasks and s-dependent
-// matrix elements (kept apart so that the plain kernel's register allocation
-// is not affected).
-template <typename R, int NLEG, bool STRAT>
-__device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& seg,
-                                            const SideDesc& sd, const TaskDesc& td,
-                                            const TaskConst& tc, R* s_spline,
-                                            Real2<R>* s_map, R* s_hist, double* s_red, float* s_queue) {
+// Per-segment constants of run_segment: the roles, signs, masses and
+// statistical-factor coefficients of the legs, the Gaussian's exponent and
+// the spline-index constants, rounded to R from values that the time-state,
+// spline and prepare kernels computed in FP64 once per sweep (so that the
+// threads here only select and convert: FP64 arithmetic runs at a small
+// fraction of the FP32 rate).
+template <typename R, int NLEG>
+struct SegSetup {
+    SegConst<R, NLEG> C;
+    R inv_step, q0, lq0_step, qN;
+};
+
+template <typename R, int NLEG>
+__device__ __forceinline__ void seg_setup(const EvalParams& P, const SideDesc& sd, const TaskDesc& td,
+                                          const TaskConst& tc, SegSetup<R, NLEG>* out) {
     constexpr int NI = NLEG - 2;
-    constexpr int D = 3 * NI;
-    constexpr bool F32 = RMath<R>::kF32;
-    using SS = StreamShape<D, F32>;
-    constexpr int G = SS::kGroup;
     const Geometry& g = P.geo;
-    const int nb = td.nbins;
-    const int tid = threadIdx.x;
-
-    // ---- map table of this task in shared memory ---------------------------
-    const double* edges = P.edges + static_cast<int64_t>(seg.task) * g.map_stride;
-    for (int k = tid; k < D * nb; k += blockDim.x) {
-        const int d = k / nb;
-        const int b = k - d * nb;
-        const double e0 = edges[d * (nb + 1) + b];
-        const double e1 = edges[d * (nb + 1) + b + 1];
-        double lo, sc;
-        switch (d % 3) {
-            case 0: lo = g.q_min; sc = g.q_max - g.q_min; break;   // r (comoving)
-            case 1: lo = 0.0; sc = kPi; break;                     // theta
-            default: lo = -kPi; sc = kTwoPi; break;                // phi - pi
-        }
-        Real2<R> v;
-        v.y0 = static_cast<R>(lo + sc * e0);
-        v.dy = static_cast<R>(sc * (e1 - e0));
-        s_map[k] = v;
-    }
-    // per-warp histograms: atomics from different warps never share an
-    // address, and the warps are summed in a fixed order at the end, so the
-    // training data do not depend on warp scheduling
-    const int map_elems = kMaxDim * g.nbins_max;
-    const int nwarps = blockDim.x >> 5;
-    for (int k = tid; k < nwarps * map_elems; k += blockDim.x) s_hist[k] = R(0);
-    R* w_hist = s_hist + (tid >> 5) * map_elems;
-
-    // ---- per-segment constants --------------------------------------------
     SegConst<R, NLEG> C;
     const TimeState& ts = *P.ts;
     const int cons = sd.cons;
@@ -373,12 +463,10 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
         C.thi_b = static_cast<R>(P.sconst[sp].tail_hi_b);
     }
     C.a = static_cast<R>(ts.a);
-    C.inv_a = static_cast<R>(1.0 / ts.a);
-    // the observed leg's own cut (App. A) removes the whole task
-    C.c0 = tc.E_obs < g.e_cut ? R(0) : static_cast<R>(tc.obs_factor / tc.scale);
+    C.inv_a = static_cast<R>(ts.inv_a);
+    C.c0 = static_cast<R>(tc.c0);
     C.frac = tc.wfrac > 0.0;
-    C.gauss_k = static_cast<R>(C.frac ? -2.0 * 1.4426950408889634 / (tc.wfrac * tc.wfrac)
-                                      : -1.4426950408889634 / (2.0 * sd.sigma * sd.sigma));
+    C.gauss_k = static_cast<R>(tc.gauss_k);
     C.e_obs = static_cast<R>(tc.E_obs);
     C.me_on = sd.me_on != 0;
     for (int k = 0; k < 4; ++k) C.me[k] = static_cast<R>(sd.me_coef[k]);
@@ -391,15 +479,66 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
         for (int j = 0; j < NI; ++j) C.inw[j] = ((sd.in_mask >> sd.integ[j]) & 1) ? R(1) : R(0);
     }
     C.e_cut = static_cast<R>(g.e_cut);
+    out->C = C;
+    out->q0 = static_cast<R>(g.q_min);
+    out->lq0_step = static_cast<R>(g.lq0_step);
+    out->qN = static_cast<R>(g.q_max);
+    out->inv_step = static_cast<R>(g.inv_step);
+}
+
+// STRAT: the instantiation also handles stratified tasks and s-dependent
+// matrix elements (kept apart so that the plain kernel's register allocation
+// is not affected).
+template <typename R, int NLEG, bool STRAT, int SPL>
+__device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& seg,
+                                            const SideDesc& sd, const TaskDesc& td,
+                                            const TaskConst& tc, R* s_spline,
+                                            Real2<R>* s_map, R* s_hist, double* s_red, float* s_queue) {
+    constexpr int NI = NLEG - 2;
+    constexpr int D = 3 * NI;
+    constexpr bool F32 = RMath<R>::kF32;
+    using SS = StreamShape<D, F32>;
+    constexpr int G = SS::kGroup;
+    const Geometry& g = P.geo;
+    const int nb = td.nbins;
+    const int tid = threadIdx.x;
+
+    // ---- map table of this task in shared memory ---------------------------
+    const double* edges = P.edges + static_cast<int64_t>(seg.task) * g.map_stride;
+    for (int k = tid; k < D * nb; k += blockDim.x) {
+        const int d = k / nb;
+        const int b = k - d * nb;
+        const double e0 = edges[d * (nb + 1) + b];
+        const double e1 = edges[d * (nb + 1) + b + 1];
+        double lo, sc;
+        switch (d % 3) {
+            case 0: lo = g.q_min; sc = g.q_max - g.q_min; break;   // r (comoving)
+            case 1: lo = 0.0; sc = kPi; break;                     // theta
+            default: lo = -kPi; sc = kTwoPi; break;                // phi - pi
+        }
+        Real2<R> v;
+        v.y0 = static_cast<R>(lo + sc * e0);
+        v.dy = static_cast<R>(sc * (e1 - e0));
+        s_map[k] = v;
+    }
+    // per-warp histograms: atomics from different warps never share an
+    // address, and the warps are summed in a fixed order at the end, so the
+    // training data do not depend on warp scheduling
+    const int map_elems = kMaxDim * g.nbins_max;
+    const int nwarps = blockDim.x >> 5;
+    for (int k = tid; k < nwarps * map_elems; k += blockDim.x) s_hist[k] = R(0);
+    R* w_hist = s_hist + (tid >> 5) * map_elems;
+
+    // ---- per-segment constants ----------------------------------------------
+    SegSetup<R, NLEG> setup;
+    seg_setup<R, NLEG>(P, sd, td, tc, &setup);
     const R nbR = static_cast<R>(nb);
-    const R q0 = static_cast<R>(g.q_min);
-    // for log grids: log2(q0) / step (the spline index offset); unused otherwise
-    const R lq0_step = static_cast<R>(g.log_spaced ? std::log2(g.q_min) / (g.log_step / 0.6931471805599453) : 0.0);
-    const R qN = static_cast<R>(g.q_max);
-    const R inv_step = static_cast<R>(1.0 / (g.log_spaced ? g.log_step / 0.6931471805599453 : g.log_step));
     const int ncoef = 4 * (g.n_grid - 1);
     const R* knots = s_spline + g.n_species * ncoef;
     __syncthreads();
+    const SegConst<R, NLEG>& C = setup.C;
+    const R q0 = setup.q0, lq0_step = setup.lq0_step, qN = setup.qN, inv_step = setup.inv_step;
+    const uint32_t call = P.ts->call;
 
     // ---- samples ------------------------------------------------------------
     Acc<R> acc_w, acc_w2;
@@ -443,57 +582,122 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
                     }
                 }
             };
-            for (int32_t gb = static_cast<int32_t>(seg.g0) + (tid & ~31); gb < g1; gb += blockDim.x) {
-                const int64_t grp = static_cast<int64_t>(gb) + lane;
-                uint32_t uw[SS::kUniforms];
-                group_words<D>(uw, grp, P.itn, ts.call, task, P.rk);
+            // 32-bit indices: neval * dim <= 2^33 keeps every group index and sample count below 2^32
+            const uint32_t g1u = static_cast<uint32_t>(seg.g1), Nu = static_cast<uint32_t>(N);
+            // appends one sample per lane (those with keep) to the warp's queue
+            // and, once 32 are queued, evaluates them
+            auto push = [&](bool keep, float kin, const float* r, float qc, float Ec, const uint32_t* pb) {
+                const uint32_t vote = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int slot = qn + __popc(vote & lanes_below);     // < 2 * 32
+                    q[slot] = kin;
 #pragma unroll
-                for (int sgi = 0; sgi < G; ++sgi) {
-                    // samples past the budget (only in a task's last group) and
-                    // past the segment are computed and not queued
-                    const bool valid = grp < g1 && grp * G + sgi < N;
-                    R y[D];
-                    uint32_t pb[NB];
+                    for (int j = 0; j < NI; ++j) q[(1 + j) * kQueueSlots + slot] = r[j];
+                    q[(1 + NI) * kQueueSlots + slot] = qc;
+                    q[(2 + NI) * kQueueSlots + slot] = Ec;
 #pragma unroll
-                    for (int k = 0; k < NB; ++k) pb[k] = 0u;
-                    R jac = R(1);
+                    for (int k = 0; k < NB; ++k) q[(3 + NI + k) * kQueueSlots + slot] = __uint_as_float(pb[k]);
+                }
+                qn += __popc(vote);
+                if (qn >= 32) {
+                    __syncwarp();
+                    drain(lane);
+                    __syncwarp();
+                    if (lane < qn - 32) {
 #pragma unroll
-                    for (int d = 0; d < D; ++d) {
-                        // x nb = (2k + 1) nb / 2^24 with k = word >> 9: increment
-                        // and fraction exactly, in integer arithmetic
-                        const uint32_t m = (uw[sgi * D + d] >> 9) * (2u * nb) + static_cast<uint32_t>(nb);
-                        const uint32_t b = m >> 24;
-                        const float fr = static_cast<float>(m & 0xFFFFFFu) * 5.9604644775390625e-08f;   // 2^-24
-                        const Real2<R> e = s_map[d * nb + b];
-                        y[d] = fma(e.dy, fr, e.y0);
-                        jac *= e.dy;
-                        pb[d >> 2] |= b << (8 * (d & 3));
+                        for (int f = 0; f < QW; ++f) q[f * kQueueSlots + lane] = q[f * kQueueSlots + 32 + lane];
                     }
-                    R r[NI], qc, Ec;
-                    const R kin = kin_at<R, NLEG, STRAT>(C, y, jac, r, qc, Ec);
-                    const bool keep = valid && kin != R(0);
-                    const uint32_t vote = __ballot_sync(0xffffffffu, keep);
-                    if (keep) {
-                        const int slot = qn + __popc(vote & lanes_below);     // < 2 * 32
-                        q[slot] = kin;
+                    __syncwarp();
+                    qn -= 32;
+                }
+            };
+            if constexpr (!STRAT && SPL == 2) {
+                // Two samples per step in packed FP32x2 arithmetic: the two
+                // samples of a group (G even) or of two consecutive groups
+                // (G = 1, a lane then takes groups 2k and 2k + 1).  The
+                // packed path holds more registers live, so whether it pays
+                // depends on the register budget: the autotuner decides.
+                constexpr int U = G % 2 == 0 ? 1 : 2;       // groups per lane per trip
+                constexpr int S = G * U;                    // samples per lane per trip (even)
+                for (uint32_t gb = static_cast<uint32_t>(seg.g0) + (tid & ~31) * U; gb < g1u;
+                     gb += blockDim.x * U) {
+                    const uint32_t grp0 = gb + lane * U;
+                    uint32_t uw[SS::kUniforms * U];
 #pragma unroll
-                        for (int j = 0; j < NI; ++j) q[(1 + j) * kQueueSlots + slot] = r[j];
-                        q[(1 + NI) * kQueueSlots + slot] = qc;
-                        q[(2 + NI) * kQueueSlots + slot] = Ec;
+                    for (int u = 0; u < U; ++u) group_words<D>(uw + u * SS::kUniforms, grp0 + u, P.itn, call, task, P.rk);
 #pragma unroll
-                        for (int k = 0; k < NB; ++k) q[(3 + NI + k) * kQueueSlots + slot] = __uint_as_float(pb[k]);
-                    }
-                    qn += __popc(vote);
-                    if (qn >= 32) {
-                        __syncwarp();
-                        drain(lane);
-                        __syncwarp();
-                        if (lane < qn - 32) {
+                    for (int sp = 0; sp < S; sp += 2) {
+                        bool valid[2];
+                        float2 y[D];
+                        float2 jac = make_float2(1.0f, 1.0f);
+                        uint32_t pb[2][NB];
 #pragma unroll
-                            for (int f = 0; f < QW; ++f) q[f * kQueueSlots + lane] = q[f * kQueueSlots + 32 + lane];
+                        for (int h = 0; h < 2; ++h) {
+                            const uint32_t grp = grp0 + (sp + h) / G;
+                            valid[h] = grp < g1u && grp * G + (sp + h) % G < Nu;
+#pragma unroll
+                            for (int k = 0; k < NB; ++k) pb[h][k] = 0u;
                         }
-                        __syncwarp();
-                        qn -= 32;
+#pragma unroll
+                        for (int d = 0; d < D; ++d) {
+                            // x nb = (2k + 1) nb / 2^24 with k = word >> 9: increment
+                            // and fraction exactly, in integer arithmetic
+                            Real2<float> e[2];
+                            float fr[2];
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const uint32_t m = (uw[(sp + h) * D + d] >> 9) * (2u * nb) + static_cast<uint32_t>(nb);
+                                const uint32_t b = m >> 24;
+                                fr[h] = static_cast<float>(m & 0xFFFFFFu);
+                                e[h] = s_map[d * nb + b];
+                                pb[h][d >> 2] |= b << (8 * (d & 3));
+                            }
+                            const float2 dy = make_float2(e[0].dy, e[1].dy);
+                            const float2 frac = __fmul2_rn(make_float2(fr[0], fr[1]),
+                                                           make_float2(5.9604644775390625e-08f, 5.9604644775390625e-08f));
+                            y[d] = __ffma2_rn(dy, frac, make_float2(e[0].y0, e[1].y0));
+                            jac = __fmul2_rn(jac, dy);
+                        }
+                        float2 r2[NI], qc2, Ec2;
+                        const float2 kin = kin_pair<NLEG>(C, y, jac, r2, qc2, Ec2);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            float r[NI];
+#pragma unroll
+                            for (int j = 0; j < NI; ++j) r[j] = h ? r2[j].y : r2[j].x;
+                            const float kh = h ? kin.y : kin.x;
+                            push(valid[h] && kh != 0.0f, kh, r, h ? qc2.y : qc2.x, h ? Ec2.y : Ec2.x, pb[h]);
+                        }
+                    }
+                }
+            } else {
+                for (uint32_t gb = static_cast<uint32_t>(seg.g0) + (tid & ~31); gb < g1u; gb += blockDim.x) {
+                    const uint32_t grp = gb + lane;
+                    uint32_t uw[SS::kUniforms];
+                    group_words<D>(uw, grp, P.itn, call, task, P.rk);
+#pragma unroll
+                    for (int sgi = 0; sgi < G; ++sgi) {
+                        // samples past the budget (only in a task's last group) and
+                        // past the segment are computed and not queued
+                        const bool valid = grp < g1u && grp * G + sgi < Nu;
+                        R y[D];
+                        uint32_t pb[NB];
+#pragma unroll
+                        for (int k = 0; k < NB; ++k) pb[k] = 0u;
+                        R jac = R(1);
+#pragma unroll
+                        for (int d = 0; d < D; ++d) {
+                            const uint32_t m = (uw[sgi * D + d] >> 9) * (2u * nb) + static_cast<uint32_t>(nb);
+                            const uint32_t b = m >> 24;
+                            const float fr = static_cast<float>(m & 0xFFFFFFu) * 5.9604644775390625e-08f;   // 2^-24
+                            const Real2<R> e = s_map[d * nb + b];
+                            y[d] = fma(e.dy, fr, e.y0);
+                            jac *= e.dy;
+                            pb[d >> 2] |= b << (8 * (d & 3));
+                        }
+                        R r[NI], qc, Ec;
+                        const R kin = kin_at<R, NLEG, STRAT>(C, y, jac, r, qc, Ec);
+                        push(valid && kin != R(0), kin, r, qc, Ec, pb);
                     }
                 }
             }
@@ -502,7 +706,7 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
         } else {
             for (int32_t grp = static_cast<int32_t>(seg.g0) + tid; grp < g1; grp += blockDim.x) {
                 R u[SS::kUniforms];                       // 52-bit uniforms
-                group_uniforms<D, F32, R>(u, grp, P.itn, ts.call, task, P.rk);
+                group_uniforms<D, F32, R>(u, grp, P.itn, call, task, P.rk);
 #pragma unroll
                 for (int sgi = 0; sgi < G; ++sgi) {
                     // samples past the budget (only in a task's last group) are
@@ -570,8 +774,8 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
                 const int32_t grp = item * GPI + gi;
                 uint32_t uw[F32 ? SS::kUniforms : 1];
                 R u[F32 ? 1 : SS::kUniforms];
-                if constexpr (F32) group_words<D>(uw, grp, P.itn, ts.call, task, P.rk);
-                else group_uniforms<D, F32, R>(u, grp, P.itn, ts.call, task, P.rk);
+                if constexpr (F32) group_words<D>(uw, grp, P.itn, call, task, P.rk);
+                else group_uniforms<D, F32, R>(u, grp, P.itn, call, task, P.rk);
 #pragma unroll
                 for (int sgi = 0; sgi < G; ++sgi) {
                     R y[D];
@@ -646,9 +850,11 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
 }
 
 // MB: CTAs per SM the kernel is register-limited to (__launch_bounds__);
-// several values are instantiated and the autotuner picks one at run time.
-template <typename R, int NMAX, int MB, bool STRAT = false>
-__global__ void __launch_bounds__(kThreads, MB)
+// THREADS: threads per CTA; SPL: samples a lane evaluates per step of the
+// FP32 loop (1, or 2 in packed FP32x2 arithmetic).  Several combinations are
+// instantiated and the autotuner picks one at run time.
+template <typename R, int NMAX, int MB, bool STRAT = false, int THREADS = kThreads, int SPL = 1>
+__global__ void __launch_bounds__(THREADS, MB)
 eval_kernel(EvalParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* s_spline = reinterpret_cast<R*>(smem_raw);
@@ -656,7 +862,7 @@ eval_kernel(EvalParams P) {
     Real2<R>* s_map = reinterpret_cast<Real2<R>*>(s_spline + ((nsp + 3) & ~3));
     const int map_elems = kMaxDim * P.geo.nbins_max;
     R* s_hist = reinterpret_cast<R*>(s_map + map_elems);      // [warps][map_elems]
-    double* s_red = reinterpret_cast<double*>(s_hist + (((kThreads / 32) * map_elems + 3) & ~3));
+    double* s_red = reinterpret_cast<double*>(s_hist + (((THREADS / 32) * map_elems + 3) & ~3));
     float* s_queue = reinterpret_cast<float*>(s_red + 2 * 32);   // FP32: [warps][queue_words][kQueueSlots]
 
     // spline tables of all species, once per CTA
@@ -675,10 +881,10 @@ eval_kernel(EvalParams P) {
         const TaskConst tc = P.tconst[seg.task];
         __syncthreads();
         switch (sd.n) {
-            case 3: if constexpr (NMAX >= 3) run_segment<R, 3, STRAT>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue); break;
-            case 4: if constexpr (NMAX >= 4) run_segment<R, 4, STRAT>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue); break;
-            case 5: if constexpr (NMAX >= 5) run_segment<R, 5, STRAT>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue); break;
-            case 6: if constexpr (NMAX >= 6) run_segment<R, 6, STRAT>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue); break;
+            case 3: if constexpr (NMAX >= 3) run_segment<R, 3, STRAT, SPL>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue); break;
+            case 4: if constexpr (NMAX >= 4) run_segment<R, 4, STRAT, SPL>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue); break;
+            case 5: if constexpr (NMAX >= 5) run_segment<R, 5, STRAT, SPL>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue); break;
+            case 6: if constexpr (NMAX >= 6) run_segment<R, 6, STRAT, SPL>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue); break;
             default: break;
         }
     }

@@ -86,6 +86,11 @@ struct TaskConst {
     double E_obs;           // energy of the observed leg
     double p_obs;           // physical momentum of the observed leg
     double wfrac;           // fractional width w of App. C this sweep (0: absolute sigma_E)
+    double c0;              // obs_factor / scale, 0 when the observed leg is cut (App. A)
+    double gauss_k;         // exponent factor of the Gaussian: -log2(e) / (2 sigma^2), or -2 log2(e) / w^2
+    double inv_sig2_abs;    // 1 / sigma_E^2
+    double four_over_w2;    // 4 / w^2 with a fractional width, else 0
+    double inv_E_obs;       // 1 / E_obs
 };
 
 // Mass law of one species: m(t) = m0 + m1 t, or with n >= 2 knots the
@@ -139,6 +144,7 @@ struct TimeState {
     double dt;              // step used by the current Euler / Heun step
     double t_step;          // time at the start of the current step
     double mass[BEST_MAX_SPECIES];
+    double inv_a;           // 1 / a(t)
     uint32_t call;          // evaluation counter (Philox counter word 2)
     int32_t error;          // sticky numeric-error flag (BEST_ERR_NUMERIC)
 };
@@ -170,6 +176,8 @@ struct Geometry {
     int32_t tail_points;
     int32_t precision;
     int32_t pt_lo, pt_hi;   // grid points of this context's tasks (a shard), [pt_lo, pt_hi)
+    double inv_step;        // spline interval index: 1 / (log2 step) (log grid) or 1 / step (linear grid)
+    double lq0_step;        // log grid: log2(q_min) * inv_step
 };
 
 // Arguments of the sample kernel.
@@ -202,6 +210,45 @@ struct VjpParams {
     const void* dcoef;          // JVP: tangent spline coefficients of u, [species][n-1][4] in R
     const double* dtail;        // JVP: tail tangents [species][4] = (da, db) low end, (da, db) high end
 };
+
+// Variance-driven budgets of one process: its tasks [first, first + count)
+// share the fixed total of their configured budgets.
+struct BudgetCtl {
+    int32_t first, count;
+    int64_t n_min, n_max;
+    double total;
+};
+constexpr int kBudgetQuantum = 256;     // budgets are multiples of this many samples (or a bound)
+constexpr int kBudgetBisections = 200;
+
+// The device's view of the work partition of one VEGAS iteration index
+// (rebuilt on the device when budgets change).
+struct PlanDev {
+    int32_t n_active;
+    int32_t pad_;
+    const int32_t* active;      // [n_active] task ids
+    int32_t* task_seg;          // [n_active + 1]
+    Segment* segs;              // capacity n_active + grid
+    int32_t* cta_seg;           // [grid + 1]
+};
+
+// One instantiation of the sample kernel the autotuner may pick.
+struct SampleVariant {
+    void* fn;
+    int32_t mb;             // CTAs per SM of its register budget (__launch_bounds__)
+    int32_t threads;        // threads per CTA
+    int32_t spl;            // samples a lane evaluates per step of the FP32 loop
+};
+constexpr int kMaxVariants = 12;
+
+// Samples per Philox group of a D-dimensional task stream (FP32: 4 uniforms
+// per block, FP64: 2).
+__host__ __device__ inline int stream_group(int D, bool f32) {
+    const int per = f32 ? 4 : 2;
+    int a = D, b = per;
+    while (b) { const int t = a % b; a = b; b = t; }
+    return per / a;
+}
 
 // Doubles per partial record: the sample kernel writes 2 + D nb, the adjoint
 // kernel up to 12 values.

@@ -20,6 +20,7 @@ __global__ void set_time_kernel(Geometry g, TimeState* ts, const double* t_dev, 
     if (mode == 2) t = *t_dev + ts->dt;
     ts->t = t;
     ts->a = g.expansion ? g.a0 * sqrt(t / g.t0) : 1.0;
+    ts->inv_a = 1.0 / ts->a;
     if (!(ts->a > 0.0) || !isfinite(ts->a)) ts->error = BEST_ERR_NUMERIC;
     for (int s = 0; s < g.n_species; ++s) ts->mass[s] = mass_at(law[s], t);
 }
@@ -242,6 +243,13 @@ __global__ void prepare_kernel(Geometry g, const SideDesc* __restrict__ sides,
     c.obs_factor = td.term == 1 ? c.f_obs : 1.0 + sd.eta_obs * c.f_obs;
     const double est = prev[t];
     c.scale = clamp_scale(est > 0.0 && c.K > 0.0 ? est / c.K : (c.f_obs > 0.0 ? c.f_obs : 1.0), c.obs_factor);
+    // the observed leg's own cut (App. A) removes the whole task
+    c.c0 = E < g.e_cut ? 0.0 : c.obs_factor / c.scale;
+    c.gauss_k = c.wfrac > 0.0 ? -2.0 * 1.4426950408889634 / (c.wfrac * c.wfrac)
+                              : -1.4426950408889634 / (2.0 * sd.sigma * sd.sigma);
+    c.inv_sig2_abs = 1.0 / (sd.sigma * sd.sigma);
+    c.four_over_w2 = c.wfrac > 0.0 ? 4.0 / (c.wfrac * c.wfrac) : 0.0;
+    c.inv_E_obs = 1.0 / E;
     tconst[t] = c;
     if (!reset_acc) return;
     TaskAcc z;
@@ -533,7 +541,11 @@ __global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
                 A.n_exact += 1.0;
             }
         }
-        if (mean_n != 0.0) tconst_next[t].scale = clamp_scale(fabs(mean_n) * c.scale, c.obs_factor);
+        if (mean_n != 0.0) {
+            const double scale = clamp_scale(fabs(mean_n) * c.scale, c.obs_factor);
+            tconst_next[t].scale = scale;
+            tconst_next[t].c0 = c.c0 == 0.0 ? 0.0 : c.obs_factor / scale;   // a cut observed leg stays cut
+        }
     }
     if (underflow) return;
     // refinement: smoothing and compression in parallel over (dimension,

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "internal.cuh"
 #include "philox.cuh"
@@ -58,9 +59,12 @@ constexpr size_t kOffCtaSeg = up(kOffSegs + sizeof(Segment) * kMaxCtas);
 constexpr size_t kOffPart = up(kOffCtaSeg + sizeof(int32_t) * (kMaxCtas + 1));
 constexpr size_t kScratchBytes = up(kOffPart + sizeof(double) * static_cast<size_t>(kMaxCtas) * kRecord);
 
-// Per-device set-up: the device address of g_scratch.
+// Per-device set-up: the device address of g_scratch (looked up under a
+// lock, so that two host threads making their first call on one device do
+// not both write the slot).
 constexpr int kMaxDevices = 64;
 unsigned char* g_base[kMaxDevices] = {};
+std::mutex g_base_lock;
 
 }  // namespace
 
@@ -76,13 +80,15 @@ struct SetupArgs {
     SideDesc sd;
     TaskDesc td;
     int32_t ctas;
-    int32_t task_id;
     int64_t groups;
 };
 
 // Writes the descriptors, the grid, the time state and the partition of the
 // task's sample groups over the CTAs into the scratch array, and clears the
-// previous-estimate slot (the adaptive scale starts from f_obs).
+// previous-estimate slot (the adaptive scale starts from f_obs).  The task's
+// descriptors sit at index 0 of the scratch arrays, so every segment names
+// task 0; the Philox stream is keyed by the descriptor's gid, which holds
+// the task's id in the whole grid's numbering.
 __global__ void noalloc_setup_kernel(SetupArgs A, unsigned char* base) {
     const int tid = threadIdx.x;
     const Geometry& g = A.g;
@@ -101,7 +107,7 @@ __global__ void noalloc_setup_kernel(SetupArgs A, unsigned char* base) {
     int32_t* cta_seg = reinterpret_cast<int32_t*>(base + kOffCtaSeg);
     for (int b = tid; b < A.ctas; b += blockDim.x) {
         Segment s{};
-        s.task = A.task_id;
+        s.task = 0;
         s.g0 = A.groups * b / A.ctas;
         s.g1 = A.groups * (b + 1) / A.ctas;
         s.part = static_cast<int64_t>(b) * kRecord;
@@ -121,15 +127,19 @@ __global__ void noalloc_setup_kernel(SetupArgs A, unsigned char* base) {
 
 // Sums the task's partial records in CTA order and scales them back to the
 // weight's units: out[0] = sum w, out[1] = sum w^2, out[2 + d*nb + b] =
-// sum of w^2 over the samples in increment b of dimension d.
+// sum of w^2 over the samples in increment b of dimension d.  When the
+// spline build flagged the grid values (a value <= 0 or not finite: the
+// time state's sticky error), every output is NaN instead.
 __global__ void noalloc_reduce_kernel(const unsigned char* base, int ctas, int L, double* out) {
     const TaskConst& c = *reinterpret_cast<const TaskConst*>(base + kOffTconst);
+    const TimeState& ts = *reinterpret_cast<const TimeState*>(base + kOffTs);
     const double* part = reinterpret_cast<const double*>(base + kOffPart);
     const double sc = c.K * c.scale;
+    const bool bad = ts.error != 0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L; k += gridDim.x * blockDim.x) {
         double v = 0.0;
         for (int b = 0; b < ctas; ++b) v += part[static_cast<int64_t>(b) * kRecord + k];
-        out[k] = k == 0 ? v * sc : v * sc * sc;
+        out[k] = bad ? __longlong_as_double(0x7FF8000000000000LL) : (k == 0 ? v * sc : v * sc * sc);
     }
 }
 
@@ -164,13 +174,17 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return report(BEST_ERR_CUDA, "noalloc: no usable CUDA device");
-    if (!g_base[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p) return report(BEST_ERR_CUDA, "noalloc: cudaGetSymbolAddress failed");
-        g_base[dev] = static_cast<unsigned char*>(p);
+    unsigned char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_base_lock);
+        if (!g_base[dev]) {
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+            if (e != cudaSuccess || !p) return report(BEST_ERR_CUDA, "noalloc: cudaGetSymbolAddress failed");
+            g_base[dev] = static_cast<unsigned char*>(p);
+        }
+        base = g_base[dev];
     }
-    unsigned char* base = g_base[dev];
 
     // Geometry of this single task.
     const int D = td.dim, nb = td.nbins, n = cfg->grid.n, S = cfg->n_species;
@@ -180,6 +194,8 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     g.q_min = cfg->grid.q_min;
     g.q_max = cfg->grid.q_max;
     g.log_step = g.log_spaced ? std::log(g.q_max / g.q_min) / (n - 1) : (g.q_max - g.q_min) / (n - 1);
+    g.inv_step = 1.0 / (g.log_spaced ? g.log_step / 0.6931471805599453 : g.log_step);
+    g.lq0_step = g.log_spaced ? std::log2(g.q_min) * g.inv_step : 0.0;
     g.n_species = S;
     g.n_tasks = 1;
     g.n_side = 1;
@@ -222,6 +238,7 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     A.ts.t = t;
     A.ts.a = cfg->expansion ? cfg->a0 * std::sqrt(t / cfg->t0) : 1.0;
     if (!(A.ts.a > 0.0)) return report(BEST_ERR_INVALID, "noalloc: a(t) must be positive");
+    A.ts.inv_a = 1.0 / A.ts.a;
     A.ts.call = call;
     for (int s = 0; s < S; ++s) {
         const best_species& sp = cfg->species[s];
@@ -240,7 +257,6 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     A.sd = sd;
     A.td = td;
     A.ctas = ctas;
-    A.task_id = task;
     const int G = group_size(D, f32);
     A.groups = (td.neval + G - 1) / G;
 
@@ -263,19 +279,18 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     spline_build_kernel<<<S, 256, spline_smem, st>>>(g, f_dev, 0, knots, ts, sc, fgrid, coef64, coef32);
     prepare_kernel<<<1, 32, 0, st>>>(g, dsd, dtd, knots, fgrid, ts, prev, dtc, dacc, 1, nullptr);
 
-    // The sample kernel indexes its descriptor arrays and the map by the task
-    // id that also enters the Philox counter; the single task's entries sit
-    // at index 0 of the scratch arrays, so the base pointers are shifted by
-    // -task (only the task's own element is ever read).
+    // The sample kernel indexes its descriptor arrays and the map by the
+    // segment's task index (0 here: the scratch arrays and the caller's map
+    // hold this one task); its Philox stream is keyed by td.gid = task.
     EvalParams P;
     std::memset(&P, 0, sizeof(P));
     P.geo = g;
     P.sides = dsd;
-    P.tasks = dtd - task;
-    P.tconst = dtc - task;
+    P.tasks = dtd;
+    P.tconst = dtc;
     P.sconst = sc;
     P.ts = ts;
-    P.edges = edges_dev - static_cast<int64_t>(task) * g.map_stride;
+    P.edges = edges_dev;
     P.segs = reinterpret_cast<const Segment*>(base + kOffSegs);
     P.cta_seg = reinterpret_cast<const int32_t*>(base + kOffCtaSeg);
     P.coef = f32 ? static_cast<const void*>(coef32) : static_cast<const void*>(coef64);

@@ -96,13 +96,13 @@ __device__ __forceinline__ void group_uniforms(R* u, int64_t g, uint32_t itn, ui
 
 // Raw 32-bit words of sample group g (FP32 stream: one word per uniform).
 template <int D, typename Keys>
-__device__ __forceinline__ void group_words(uint32_t* w, int64_t g, uint32_t itn, uint32_t call,
+__device__ __forceinline__ void group_words(uint32_t* w, uint32_t g, uint32_t itn, uint32_t call,
                                             uint32_t task, const Keys& rk) {
     using S = StreamShape<D, true>;
-    const uint64_t b0 = static_cast<uint64_t>(g) * S::kBlocks;
+    const uint32_t b0 = g * S::kBlocks;            // counter word 0 is the block index mod 2^32
 #pragma unroll
     for (int j = 0; j < S::kBlocks; ++j) {
-        uint32_t c0 = static_cast<uint32_t>(b0 + j), c1 = itn, c2 = call, c3 = task;
+        uint32_t c0 = b0 + j, c1 = itn, c2 = call, c3 = task;
         philox4x32_10(c0, c1, c2, c3, rk);
         w[4 * j + 0] = c0;
         w[4 * j + 1] = c1;

@@ -143,16 +143,17 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
     const R cbc = enh_c ? eta_c : R(1);
     const R tlo_a = static_cast<R>(P.sconst[spcn].tail_lo_a), tlo_b = static_cast<R>(P.sconst[spcn].tail_lo_b);
     const R thi_a = static_cast<R>(P.sconst[spcn].tail_hi_a), thi_b = static_cast<R>(P.sconst[spcn].tail_hi_b);
-    const R a = static_cast<R>(ts.a), inv_a = static_cast<R>(1.0 / ts.a);
+    // (the FP64 quotients below come from the time-state and prepare kernels,
+    // once per sweep: FP64 division runs at a small fraction of the FP32 rate)
+    const R a = static_cast<R>(ts.a), inv_a = static_cast<R>(ts.inv_a);
     const bool obs_cut = tc.E_obs < g.e_cut;       // every sample of the task is cut
-    const R c0 = obs_cut ? R(0) : static_cast<R>(tc.obs_factor / tc.scale);
+    const R c0 = static_cast<R>(tc.c0);
     // Gaussian of Eq. (11); fractional width (App. C): sigma = w S / 2 per
     // sample, S = E_in + E_out, with sigma_ref = w E_obs inside K
     const bool frac = tc.wfrac > 0.0;
-    const R gauss_k = static_cast<R>(frac ? -2.0 * 1.4426950408889634 / (tc.wfrac * tc.wfrac)
-                                          : -1.4426950408889634 / (2.0 * sd.sigma * sd.sigma));
-    const R inv_sig2_abs = static_cast<R>(1.0 / (sd.sigma * sd.sigma));
-    const R four_over_w2 = static_cast<R>(frac ? 4.0 / (tc.wfrac * tc.wfrac) : 0.0);
+    const R gauss_k = static_cast<R>(tc.gauss_k);
+    const R inv_sig2_abs = static_cast<R>(tc.inv_sig2_abs);
+    const R four_over_w2 = static_cast<R>(tc.four_over_w2);
     const R e_obs = static_cast<R>(tc.E_obs);
     // |M|^2 / coupling^2 = P(s), s of the initial state
     const bool me_on = ME && sd.me_on != 0;
@@ -168,7 +169,7 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
 #pragma unroll
     for (int j = 0; j < NI; ++j) inw[j] = ((sd.in_mask >> sd.integ[j]) & 1) ? R(1) : R(0);
     const R e_cut = static_cast<R>(g.e_cut);
-    const R inv_Eobs = static_cast<R>(1.0 / tc.E_obs);
+    const R inv_Eobs = static_cast<R>(tc.inv_E_obs);
     const R U = static_cast<R>(V.task_u[seg.task]);     // VJP: adjoint seed; JVP: obs tangent factor
     R dta_lo = R(0), dtb_lo = R(0), dta_hi = R(0), dtb_hi = R(0);
     if constexpr (JVP) {
@@ -179,8 +180,8 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
     }
     const R nbR = static_cast<R>(nb);
     const R q0 = static_cast<R>(g.q_min), qN = static_cast<R>(g.q_max);
-    const R lq0_step = static_cast<R>(g.log_spaced ? std::log2(g.q_min) / (g.log_step / 0.6931471805599453) : 0.0);
-    const R inv_step = static_cast<R>(1.0 / (g.log_spaced ? g.log_step / 0.6931471805599453 : g.log_step));
+    const R lq0_step = static_cast<R>(g.lq0_step);
+    const R inv_step = static_cast<R>(g.inv_step);
     const int ncoef = 4 * (g.n_grid - 1);
     const R* knots = s_spline + g.n_species * ncoef;
     __syncthreads();
@@ -348,7 +349,7 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
         const int64_t grp = static_cast<int64_t>(gb) + lane;
         uint32_t uw[F32 ? SS::kUniforms : 1];
         R u[F32 ? 1 : SS::kUniforms];
-        if constexpr (F32) group_words<D>(uw, grp, P.itn, ts.call, task, P.rk);
+        if constexpr (F32) group_words<D>(uw, static_cast<uint32_t>(grp), P.itn, ts.call, task, P.rk);
         else group_uniforms<D, F32, R>(u, grp, P.itn, ts.call, task, P.rk);
 #pragma unroll
         for (int sgi = 0; sgi < G; ++sgi) {
@@ -374,7 +375,7 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
                 jac *= e.dy;
             }
             R px = R(0), py = R(0), pz = pobs_sig;
-            R dE = sgn_obs_E;
+            EBal<R> bal(sgn_obs_E);
             R Esum = e_obs;
             R Qx = R(0), Qy = R(0), Qz = obs_in_p, Ein = obs_in_E;
             R meas = jac;
@@ -396,7 +397,7 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
                 const R rr = RMath<R>::rsqrt_(E2);
                 const R E = E2 * rr;
                 cut |= E < e_cut;
-                dE = fma(sgnE[j], E, dE);
+                bal.add(sgnE[j] * E);
                 Esum += E;
                 if (me_on) {
                     Qx = fma(-inw[j] * ps, cp, Qx);
@@ -413,7 +414,8 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
             const R rEc = RMath<R>::rsqrt_(Ec2 > R(0) ? Ec2 : R(1e-30));
             const R Ec = Ec2 * rEc;
             cut |= Ec < e_cut;
-            dE = fma(sgn_cons, Ec, dE);
+            bal.add(sgn_cons * Ec);
+            const R dE = bal.value();
             const R qc = pc2 * (pc2 > R(0) ? RMath<R>::rsqrt_(pc2) : R(0)) * a;
             // Gaussian and, for the adjoint, 1/sigma^2 and the derivative of
             // log(1/sigma) with exp(-dE^2 / 2 sigma^2) through sigma(E_k)

@@ -15,10 +15,35 @@ import sys
 import numpy as np
 
 
+def equilibrium_fit(problem, f, t):
+    """(T, mu) per species from the least-squares line of log(1/f + eta)
+    against E(q/a) over the grid points with f > 1e-12: an equilibrium
+    distribution 1/(exp((E - mu)/T) - eta) gives exactly y = (E - mu)/T.  A
+    number-changing process drives mu to 0 (chemical equilibrium, Sec. 5D)."""
+    g = problem.grid
+    q = (np.geomspace(g.q_min, g.q_max, g.n) if g.log_spaced else np.linspace(g.q_min, g.q_max, g.n))
+    a = 1.0 if problem.expansion is None else problem.expansion.a0 * np.sqrt(t / problem.expansion.t0)
+    out = []
+    for s, sp in enumerate(problem.species):
+        eta = {0: 0.0, 1: 1.0, 2: -1.0}[sp.stat]
+        if sp.mass_table is not None:
+            m = float(np.interp(t, [k[0] for k in sp.mass_table], [k[1] for k in sp.mass_table]))
+        else:
+            m = sp.mass0 + sp.mass1 * t
+        fs = np.asarray(f[s], dtype=np.float64)
+        ok = fs > 1e-12
+        E = np.sqrt((q[ok] / a) ** 2 + m * m)
+        y = np.log(1.0 / fs[ok] + eta)
+        slope, icpt = np.polyfit(E, y, 1)
+        out.append((1.0 / slope, -icpt / slope))
+    return out
+
+
 def run(problem, f0, steps, every, precision=1, method="heun", t0=1.0, dt=1.0, autotune=True):
     """Evolve log f from f0 for ``steps`` steps (dt requested per step,
     bounded by Eq. (16)); returns a dict of histories: t, n[S], rho[S],
-    the widths of App. C and the final log f."""
+    the fitted temperature and chemical potential of every species, the
+    widths of App. C and the final log f."""
     import torch
 
     from . import Collision
@@ -30,10 +55,13 @@ def run(problem, f0, steps, every, precision=1, method="heun", t0=1.0, dt=1.0, a
         logf = torch.log(f).contiguous()
         t = torch.tensor([t0], dtype=torch.float64, device="cuda")
         dtt = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        hist = {"t": [], "n": [], "rho": [], "width": [], "step": []}
+        hist = {"t": [], "n": [], "rho": [], "width": [], "step": [], "T": [], "mu": []}
 
         def record(k):
             n, rho = col.moments(torch.exp(logf), float(t.item()))
+            fit = equilibrium_fit(problem, torch.exp(logf).cpu().numpy(), float(t.item()))
+            hist["T"].append([x[0] for x in fit])
+            hist["mu"].append([x[1] for x in fit])
             hist["t"].append(float(t.item()))
             hist["n"].append(n.cpu().numpy().tolist())
             hist["rho"].append(rho.cpu().numpy().tolist())

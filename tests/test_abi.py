@@ -60,7 +60,7 @@ def test_struct_layout_matches_c(tmp_path):
         "best_process": ["n_in", "n_out", "species", "coupling", "sigma_E", "neval", "neval_per_point",
                          "nitn", "nbins", "alpha", "width_mode", "width", "width_rel_lo", "width_rel_hi",
                          "width_factor", "width_min", "width_max", "strat", "strat_max_hcubes", "strat_beta",
-                         "me_coef"],
+                         "me_coef", "budget", "sides", "neval_min", "neval_max"],
         "best_config": ["grid", "n_species", "n_processes", "species", "processes", "precision",
                         "tail_points", "seed", "e_cut", "expansion", "a0", "t0", "eps_dt", "point_lo",
                         "point_hi"],

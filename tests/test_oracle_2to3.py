@@ -54,3 +54,20 @@ def test_mc_matches_reduction_massive(side, i):
     red = (ref.loss_2to3_c2_mb if side == 0 else ref.loss_2to3_c3_mb)(q[i], m, A, T, sigma)
     assert err < 0.05 * mean
     assert abs(mean - red) < 3.5 * err
+
+
+def test_side_selection_keeps_roles_and_multiplicities():
+    """sides = 1 / 2 keep only the side integrals with the observed leg
+    initial / final (the paper's C_3 alone, Sec. 5D), with the roles and
+    multiplicities they have in the full decomposition; a process with equal
+    initial and final species has no final-side integral to keep."""
+    from dataclasses import replace
+    prob = Problem(Grid(8, 0.1, 10.0, True), (Species("phi", STAT_MB, 1.0),),
+                   (Process("p", (0, 0), (0, 0, 0), 1.0, 0.1, 100, 1),))
+    full = side_integrals(prob)
+    assert [s.side for s in full] == [0, 1] and [s.mult for s in full] == [2, 3]
+    for keep in (1, 2):
+        sel = side_integrals(replace(prob, processes=(replace(prob.processes[0], sides=keep),)))
+        assert sel == [s for s in full if s.side == keep - 1]
+    sym = replace(prob, processes=(Process("q", (0, 0), (0, 0), sides=2),))
+    assert side_integrals(sym) == []

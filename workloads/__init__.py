@@ -108,6 +108,10 @@ class Process:
     budget: int = 0
     neval_min: int = 0
     neval_max: int = 0
+    # Side integrals evaluated (Eq. (7)): 0 all of them; 1 only those with
+    # the observed leg initial; 2 only those with it final (e.g. C_3 alone of
+    # a 2 -> 3 process, the paper's negative case of Sec. 5D).
+    sides: int = 0
 
 
 @dataclass(frozen=True)
