@@ -64,6 +64,7 @@ def mufu_per_sample(n_legs):
 NEVAL = None      # per-task samples per iteration; None = the workload's own
 WORKLOAD_KEY = "c2"
 STRAT = False     # stratified sampling (VEGAS+) in every process
+VARB = False      # variance-driven per-task budgets (multi-species workload)
 # per workload: (builder, integrator, requested dt, start time, description)
 WORKLOADS = {
     "c1": ("c1_maxwell_2to2", "euler", 0.1, 0.0,
@@ -93,9 +94,12 @@ def _workload():
     import workloads as W
     name = WORKLOADS[WORKLOAD_KEY][0]
     fn = getattr(W, name)
+    if WORKLOAD_KEY == "c4":
+        kw = dict(variance_budgets=VARB)
+        if NEVAL is not None:
+            kw.update(nmin=NEVAL, nmax=NEVAL * 100)
+        return fn(**kw)
     if NEVAL is not None:
-        if WORKLOAD_KEY == "c4":
-            return fn(nmin=NEVAL, nmax=NEVAL * 100)
         if WORKLOAD_KEY == "c3":
             return fn(neval=NEVAL, with_2to2=True)
         return fn(neval=NEVAL)
@@ -213,9 +217,16 @@ def run_native(args, rank, world):
     dt = torch.full((1,), DT, dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        ctas_per_sm = col.autotune(torch.exp(logf), T0)
-        col.profile(True)
+        # warm-up steps train the maps (and the budgets); the launch shape is
+        # then tuned on the trained state, which the timed steps resemble (the
+        # autotuner restores the state after its trial sweeps), and one more
+        # untimed step captures the step graph with the chosen kernel
         col.evolve(logf, t, dt, args.warmup, DT, method, stream=stream)
+        torch.cuda.synchronize()
+        ctas_per_sm = col.autotune(torch.exp(logf), float(t.item()))
+        shape = col.launch_shape()
+        col.profile(True)
+        col.evolve(logf, t, dt, 1, DT, method, stream=stream)
         col.check(stream)
         clocks = Clocks(dev)
         torch.cuda.synchronize()
@@ -237,6 +248,10 @@ def run_native(args, rank, world):
         kern_ms, kern_n = col.profile_read()               # launches of the last timed step
         col.profile(False)
         col.check(stream)
+        if VARB:
+            # variance-driven budgets: the per-sweep samples as the timed steps set them
+            evals = col.sweep_samples()
+            samples_per_launch = col.sweep_samples(0)
     from paper_2603_28848_gb300.dist import aggregate
     ms, sweeps = aggregate(ms, sweeps_per_step * args.steps, device="cuda")   # max time, summed units
     sweeps_per_s = sweeps / (ms / 1e3)
@@ -350,7 +365,8 @@ def run_native(args, rank, world):
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the sample kernel "
                               "(profiles/eval_kernel_f32_c2_bose_2to2.md); the tables it reads do not "
                               "grow with the sample count",
-            "kernel": f"best::eval_kernel<float,{max(n_legs, 4)},{ctas_per_sm}> (persistent sample kernel)",
+            "kernel": f"best::eval_kernel<float,{max(n_legs, 4)},{ctas_per_sm},_,{shape[1]},{shape[2]}> (persistent "
+                      "sample kernel)",
             "flops_per_sample": fps,
             "samples_per_launch": samples_per_launch, "launch_ms": per_launch_ms,
             "share_of_step": kern_ms / (ms / args.steps) if ms > 0 else None,
@@ -367,7 +383,8 @@ def run_native(args, rank, world):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded; BE(T=1) + Gaussian bump, no dataset)",
-        "config": {"workload": f"{wl[0]}: {wl[4]}" + (" + stratified sampling (VEGAS+)" if STRAT else ""),
+        "config": {"workload": f"{wl[0]}: {wl[4]}" + (" + stratified sampling (VEGAS+)" if STRAT else "")
+                   + (" + variance-driven budgets" if VARB else ""),
                    "grid_points": prob.grid.n, "tasks": col_tasks, "neval": prob.processes[0].neval,
                    "nitn": prob.processes[0].nitn,
                    "step": f"one {method} step = {sweeps_per_step} sweep(s)", "l2": "flushed between steps "
@@ -386,12 +403,114 @@ def run_native(args, rank, world):
                 "h2d_bytes_per_step": logf.numel() * 8 + 8, "d2h_bytes_per_step": logf.numel() * 8 + 8},
         "graph": "Heun steps replayed from a CUDA graph (best_evolve)",
         "autotune_ctas_per_sm": ctas_per_sm,
+        "autotune_shape": dict(zip(("ctas_per_sm", "threads", "samples_per_lane"), shape)),
         "gpu_launches": launches,
         "clocks": clk,
     }
     if rank == 0 and not args.skip_cpu and WORKLOAD_KEY == "c2":
         with oracle_pool() as pool:
             out["cpu_baseline"] = cpu_baseline(prob, workload()[1], args.cpu_seconds, evals, pool)
+    return out
+
+
+def point_costs(prob):
+    """Per grid point: samples x (dimensions + 6) summed over its tasks (the
+    sample kernel's cost model), for balancing grid-point shards."""
+    n = prob.grid.n
+    cost = np.zeros(n)
+    for p in prob.processes:
+        legs = len(p.species_in) + len(p.species_out)
+        sym = sorted(p.species_in) == sorted(p.species_out)
+        sides = len(set(p.species_in)) + (0 if sym else len(set(p.species_out)))
+        per = np.asarray(p.neval_per_point if p.neval_per_point is not None else [p.neval] * n, dtype=np.float64)
+        cost += 2 * sides * per * (3 * (legs - 2) + 6)
+    return cost
+
+
+def run_sharded(args, rank, world):
+    """The paper's decomposition over ranks (Sec. 3D, Eq. (17)): one workload,
+    rank r evaluating the tasks of a contiguous, cost-balanced block of grid
+    points; one NCCL all-reduce of C per evaluation; every rank applies the
+    same step stages (strong scaling: the whole job is fixed as N grows)."""
+    import torch
+
+    import workloads as W
+    from paper_2603_28848_gb300 import Collision, build
+    from paper_2603_28848_gb300 import dist as bdist
+
+    build()
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    prob, f0 = workload()
+    wl = WORKLOADS[WORKLOAD_KEY]
+    method, DT, T0 = wl[1], wl[2], wl[3]
+    lo, hi = bdist.shard(point_costs(prob), rank, world)
+    col = Collision(prob, W.PREC_FP32, points=(lo, hi))
+    logf = torch.tensor(np.log(f0), dtype=torch.float64, device="cuda").contiguous()
+    t = torch.full((1,), T0, dtype=torch.float64, device="cuda")
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctas_per_sm = col.autotune(torch.exp(logf), T0)
+    ref = torch.cuda.Event(enable_timing=True)
+    ref.record()
+
+    def clock():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record()
+        e.synchronize()
+        return ref.elapsed_time(e)
+
+    barrier = torch.distributed.barrier
+    clocks = Clocks(dev)
+    clocks.start()
+    col.profile(True)
+    ms, sweeps = bdist.timed_sharded_steps(col, logf, t, dt, DT, method, args.steps, args.warmup, clock, barrier)
+    kern_ms, kern_n = col.profile_read()
+    col.profile(False)
+    clk = clocks.stop()
+    col.check()
+    tm = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    torch.distributed.all_reduce(tm, op=torch.distributed.ReduceOp.MAX)
+    ms = float(tm.item())
+    # end to end: the step's distribution from pinned host memory and back
+    h_logf = torch.tensor(np.log(f0), dtype=torch.float64).pin_memory()
+    h_out = torch.empty_like(h_logf).pin_memory()
+
+    def e2e_reduce(x):
+        return bdist.all_reduce_sum(x)
+
+    barrier()
+    e0 = clock()
+    for _ in range(args.steps):
+        logf.copy_(h_logf, non_blocking=True)
+        bdist.sharded_step(col, logf, t, dt, DT, method, reduce=e2e_reduce)
+        h_out.copy_(logf, non_blocking=True)
+    e1 = clock()
+    barrier()
+    te = torch.tensor([e1 - e0], dtype=torch.float64, device="cuda")
+    torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+    ev = torch.tensor([float(col.sweep_samples())], dtype=torch.float64, device="cuda")
+    torch.distributed.all_reduce(ev)                     # the shards' samples add up to one whole sweep
+    evals = float(ev.item())
+    per_launch_ms = kern_ms / max(kern_n, 1)
+    out = {
+        "metric": METRIC, "value": sweeps / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; no dataset)",
+        "config": {"workload": f"{wl[0]}: {wl[4]}", "grid_points": prob.grid.n,
+                   "step": f"one {method} step = {2 if method == 'heun' else 1} sweep(s) of the whole grid",
+                   "parallelism": f"grid points sharded over {world} ranks, one all-reduce of C per evaluation",
+                   "shard_of_rank0": [lo, hi] if rank == 0 else None,
+                   "l2": "inputs and maps per task are small; no flush (a host round trip per stage)"},
+        "sample_kernel_ms_per_launch_rank0": per_launch_ms,
+        "autotune_ctas_per_sm": ctas_per_sm,
+        "gpu_launches": None,
+        "e2e": {"value": sweeps / (float(te.item()) / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": logf.numel() * 8, "d2h_bytes_per_step": logf.numel() * 8},
+        "clocks": clk,
+        "evals_per_sweep": evals,
+        "evals_per_s": evals * sweeps / (ms / 1e3),
+    }
+    col.close()
     return out
 
 
@@ -520,8 +639,13 @@ def main():
     ap.add_argument("--vjp", action="store_true", help="also time the adjoint")
     ap.add_argument("--implicit", action="store_true", help="also time the tangent and one implicit Euler step")
     ap.add_argument("--strat", action="store_true", help="adaptive stratified sampling (VEGAS+) in every process")
+    ap.add_argument("--replicas", action="store_true",
+                    help="under torchrun: an independent replica per rank instead of the grid-point shards")
+    ap.add_argument("--variance-budgets", action="store_true",
+                    help="multi-species workload: per-task budgets re-set from the last sweep's variance")
     args = ap.parse_args()
-    global NEVAL, WORKLOAD_KEY, STRAT
+    global NEVAL, WORKLOAD_KEY, STRAT, VARB
+    VARB = args.variance_budgets
     NEVAL = args.neval
     STRAT = args.strat
     WORKLOAD_KEY = args.workload
@@ -534,9 +658,11 @@ def main():
         return
     if world > 1:
         import torch
+        os.environ.setdefault("NCCL_DEBUG", "INFO")          # communicator lines name the ranks of the run
+        os.environ.setdefault("NCCL_DEBUG_SUBSYS", "INIT")
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
-    out = run_native(args, rank, world)
+    out = run_sharded(args, rank, world) if world > 1 and not args.replicas else run_native(args, rank, world)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -1,13 +1,14 @@
 """Host logic of multi-process runs (one process per GPU, torchrun).
 
 The collision integral partitions by grid points (independent tasks, the
-paper's MPI design of Sec. 3D).  bench.py runs an independent replica of the
-workload on every rank (weak scaling) and only reduces its timing.  A sharded
-evolution gives each rank the tasks of a contiguous, budget-balanced block of
-grid points (`shard`, a context built with points=(lo, hi)); every C
-evaluation is followed by one exchange, a sum of the ranks' disjoint C slices
-(`sharded_step`), after which every rank applies the same step to its copy of
-the whole distribution.
+paper's MPI design of Sec. 3D).  A sharded evolution gives each rank the
+tasks of a contiguous, budget-balanced block of grid points (`shard`, a
+context built with points=(lo, hi)); every C evaluation is followed by one
+exchange, a sum of the ranks' disjoint C slices (`sharded_step`), after which
+every rank applies the same step to its copy of the whole distribution.
+bench.py times that design under torchrun (`timed_sharded_steps`: one
+workload split over the ranks, strong scaling); independent replicas per
+rank are its opt-in alternative.
 """
 import numpy as np
 
@@ -70,3 +71,30 @@ def sharded_step(col, logf, t_dev, dt_dev, dt_request, method="heun", reduce=all
         reduce(k2)
         col.step_stage(1, 1, logf, k1, t_dev, dt_dev, k2=k2, fstar=fstar)
     return dt
+
+
+def timed_sharded_steps(col, logf, t_dev, dt_dev, dt_request, method, steps, warmup, clock, barrier=None,
+                        reduce=all_reduce_sum):
+    """`warmup` untimed, then `steps` timed sharded steps on this rank.
+
+    ``clock()`` returns a time in ms after waiting for the device (the bench
+    passes a synchronising CUDA-event clock); ``barrier()`` lines the ranks up
+    on both sides of the timed region.  Returns (elapsed ms on this rank,
+    whole-grid sweeps done: every rank takes part in each of them)."""
+    buffers = None
+    try:
+        import torch
+        buffers = (torch.empty_like(logf), torch.empty_like(logf), torch.empty_like(logf))
+    except ImportError:
+        pass
+    for _ in range(warmup):
+        sharded_step(col, logf, t_dev, dt_dev, dt_request, method, reduce=reduce, buffers=buffers)
+    if barrier is not None:
+        barrier()
+    t0 = clock()
+    for _ in range(steps):
+        sharded_step(col, logf, t_dev, dt_dev, dt_request, method, reduce=reduce, buffers=buffers)
+    t1 = clock()
+    if barrier is not None:
+        barrier()
+    return t1 - t0, steps * (2 if method == "heun" else 1)

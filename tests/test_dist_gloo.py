@@ -141,3 +141,68 @@ def test_sharded_steps_on_two_ranks_equal_one_rank(method):
         assert np.allclose(lf, logf.tolist(), rtol=0, atol=1e-14)
         assert tt == pytest.approx(float(t), rel=1e-15)
     assert float(t) > 0.2            # the steps moved time (some were limited by Eq. (16))
+
+
+def _timed_worker(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    n = 12
+    lo, hi = bdist.shard([1.0] * n, rank, world)
+    col = _Relaxation(n, lo, hi)
+    logf = torch.linspace(-2.0, 0.5, n, dtype=torch.float64)
+    t = torch.tensor([0.0], dtype=torch.float64)
+    dt = torch.tensor([0.0], dtype=torch.float64)
+    import time
+    ms, sweeps = bdist.timed_sharded_steps(col, logf, t, dt, 0.2, "heun", 3, 1, lambda: time.perf_counter() * 1e3,
+                                           dist.barrier)
+    out[rank] = (logf.tolist(), float(t), sweeps, ms)
+    dist.destroy_process_group()
+
+
+def test_bench_sharded_mode_on_two_ranks_equals_one_rank():
+    """The timed loop bench.py runs under torchrun (grid-point shards, one C
+    exchange per evaluation): 1 warm-up + 3 timed Heun steps on two gloo ranks
+    end where one rank with the whole grid ends, and count 6 whole-grid sweeps."""
+    import torch
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_timed_worker, args=(r, 2, port, out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=120)
+            assert p.exitcode == 0
+        got = [out[0], out[1]]
+    n = 12
+    col = _Relaxation(n, 0, n)
+    logf = torch.linspace(-2.0, 0.5, n, dtype=torch.float64)
+    t = torch.tensor([0.0], dtype=torch.float64)
+    dt = torch.tensor([0.0], dtype=torch.float64)
+    import time
+    ms, sweeps = bdist.timed_sharded_steps(col, logf, t, dt, 0.2, "heun", 3, 1, lambda: time.perf_counter() * 1e3,
+                                           reduce=lambda x: x)
+    assert sweeps == 6 and ms >= 0.0
+    for lf, tt, sw, msr in got:
+        assert np.allclose(lf, logf.tolist(), rtol=0, atol=1e-14)
+        assert tt == pytest.approx(float(t), rel=1e-15) and sw == 6 and msr >= 0.0
+
+
+def test_bench_point_costs_match_the_kernel_cost_model():
+    """bench.py balances shards by samples x (D + 6) per grid point over its
+    tasks, the cost model of the sample kernel's static partition."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(os.path.dirname(os.path.dirname(
+        os.path.abspath(__file__))), "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    import workloads as W
+    prob, _ = W.c4_multi_species(n=16, nmin=1000, nmax=100_000)
+    c = bench.point_costs(prob)
+    sched = np.asarray(prob.processes[0].neval_per_point, dtype=np.float64)
+    # AB->AB: 2 sides (one per species), D = 6; AA->AAA: 2 sides, D = 9; AAA->BB: 2 sides, D = 9
+    assert np.allclose(c, 2 * sched * (2 * 12 + 2 * 15 + 2 * 15))
