@@ -19,13 +19,14 @@ and this oracle consume identical samples.  Stream definition (a reading):
 For a task evaluated with N samples in D dimensions, uniform number
 u = s*D + d (sample s, dimension d) is taken from
 
-  * mode "f32": block u div 4, 32-bit word u mod 4, value ((x >> 9) + 1/2) 2^-23
+  * mode "f32": block u div 4, 32-bit word u mod 4, value x 2^-32 in [0, 1)
+    (so that the VEGAS increment floor(x nb / 2^32) and its fraction are the
+    high and low halves of the integer product x nb)
   * mode "f64": block u div 2, words (2(u mod 2), 2(u mod 2)+1) = (x0, x1),
-                value (((x0 >> 6) 2^26 + (x1 >> 6)) + 1/2) 2^-52
+                value (((x0 >> 6) 2^26 + (x1 >> 6)) + 1/2) 2^-52 in (0, 1)
 
-Both lie strictly inside (0, 1) and are exactly representable in their
-precision (23 + 1 and 52 + 1 significant bits), so every order of evaluation
-gives the same number on every machine.
+Both are exact in FP64, so every order of evaluation gives the same number on
+every machine.
 """
 import numpy as np
 
@@ -79,8 +80,7 @@ def uniforms(seed, task, iteration, call, n_samples, dim, mode="f64", first_samp
         b1 = (u0 + n_u - 1) // 4 + 1
         w = _words(seed, task, iteration, call, b0, b1 - b0)
         x = w[u0 - 4 * b0: u0 - 4 * b0 + n_u].astype(np.float64)
-        x = np.floor(x / 512.0)                     # x >> 9
-        v = (x + 0.5) * 2.0 ** -23
+        v = x * 2.0 ** -32
     elif mode == "f64":
         b0 = u0 // 2
         b1 = (u0 + n_u - 1) // 2 + 1

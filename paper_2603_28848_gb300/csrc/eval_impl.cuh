@@ -640,21 +640,21 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
                         }
 #pragma unroll
                         for (int d = 0; d < D; ++d) {
-                            // x nb = (2k + 1) nb / 2^24 with k = word >> 9: increment
-                            // and fraction exactly, in integer arithmetic
+                            // x nb = word nb / 2^32: the increment is the high and the
+                            // fraction the low half of one 32 x 32 -> 64-bit product
                             Real2<float> e[2];
                             float fr[2];
 #pragma unroll
                             for (int h = 0; h < 2; ++h) {
-                                const uint32_t m = (uw[(sp + h) * D + d] >> 9) * (2u * nb) + static_cast<uint32_t>(nb);
-                                const uint32_t b = m >> 24;
-                                fr[h] = static_cast<float>(m & 0xFFFFFFu);
+                                const uint64_t m = static_cast<uint64_t>(uw[(sp + h) * D + d]) * static_cast<uint32_t>(nb);
+                                const uint32_t b = static_cast<uint32_t>(m >> 32);
+                                fr[h] = static_cast<float>(static_cast<uint32_t>(m));
                                 e[h] = s_map[d * nb + b];
                                 pb[h][d >> 2] |= b << (8 * (d & 3));
                             }
                             const float2 dy = make_float2(e[0].dy, e[1].dy);
                             const float2 frac = __fmul2_rn(make_float2(fr[0], fr[1]),
-                                                           make_float2(5.9604644775390625e-08f, 5.9604644775390625e-08f));
+                                                           make_float2(2.3283064365386963e-10f, 2.3283064365386963e-10f));
                             y[d] = __ffma2_rn(dy, frac, make_float2(e[0].y0, e[1].y0));
                             jac = __fmul2_rn(jac, dy);
                         }
@@ -687,9 +687,9 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
                         R jac = R(1);
 #pragma unroll
                         for (int d = 0; d < D; ++d) {
-                            const uint32_t m = (uw[sgi * D + d] >> 9) * (2u * nb) + static_cast<uint32_t>(nb);
-                            const uint32_t b = m >> 24;
-                            const float fr = static_cast<float>(m & 0xFFFFFFu) * 5.9604644775390625e-08f;   // 2^-24
+                            const uint64_t m = static_cast<uint64_t>(uw[sgi * D + d]) * static_cast<uint32_t>(nb);
+                            const uint32_t b = static_cast<uint32_t>(m >> 32);
+                            const float fr = static_cast<float>(static_cast<uint32_t>(m)) * 2.3283064365386963e-10f;   // 2^-32
                             const Real2<R> e = s_map[d * nb + b];
                             y[d] = fma(e.dy, fr, e.y0);
                             jac *= e.dy;
@@ -785,8 +785,7 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
                     for (int d = 0; d < D; ++d) {
                         R x;
                         if constexpr (F32) {
-                            const float uf = static_cast<float>(((uw[sgi * D + d] >> 9) << 1) | 1u) *
-                                             5.9604644775390625e-08f;          // (2k + 1) 2^-24
+                            const float uf = static_cast<float>(uw[sgi * D + d]) * 2.3283064365386963e-10f;   // word 2^-32
                             x = fmaf(uf, invM, xi[d] * invM);
                         } else {
                             x = (xi[d] + u[sgi * D + d]) / static_cast<R>(M);

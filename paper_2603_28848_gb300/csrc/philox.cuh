@@ -2,11 +2,12 @@
 //
 // Stream of one task: key = (seed mod 2^32, seed div 2^32), counter =
 // (block, iteration, evaluation counter, task).  Uniform number u = s*D + d
-// (sample s, dimension d) is word u mod 4 of block u div 4 in FP32, mapped to
-// ((x >> 9) + 1/2) 2^-23, and words 2(u mod 2), 2(u mod 2)+1 of block u div 2
-// in FP64, mapped to (((x0 >> 6) 2^26 + (x1 >> 6)) + 1/2) 2^-52.  Both values
-// are exactly representable, so the FP32 and FP64 paths and any other
-// implementation of the same definition agree bit for bit.
+// (sample s, dimension d) is word u mod 4 of block u div 4 in FP32, the value
+// x 2^-32 in [0, 1) (its VEGAS increment and fraction follow exactly from the
+// 64-bit product x nb), and words 2(u mod 2), 2(u mod 2)+1 of block u div 2
+// in FP64, mapped to (((x0 >> 6) 2^26 + (x1 >> 6)) + 1/2) 2^-52 (exactly
+// representable), so any implementation of the same definition draws the
+// same points.
 #pragma once
 
 #include <cstdint>
@@ -51,7 +52,7 @@ __device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32
 }
 
 __device__ __forceinline__ float uniform_f32(uint32_t x) {
-    return (static_cast<float>(x >> 9) + 0.5f) * 1.1920928955078125e-07f;   // 2^-23
+    return static_cast<float>(x) * 2.3283064365386963e-10f;                  // x 2^-32 (rounded to FP32)
 }
 
 __device__ __forceinline__ double uniform_f64(uint32_t x0, uint32_t x1) {

@@ -361,9 +361,9 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
                 int b;
                 R fr;
                 if constexpr (F32) {
-                    const uint32_t m = (uw[sgi * D + d] >> 9) * (2u * nb) + static_cast<uint32_t>(nb);
-                    b = static_cast<int>(m >> 24);
-                    fr = static_cast<float>(m & 0xFFFFFFu) * 5.9604644775390625e-08f;
+                    const uint64_t m = static_cast<uint64_t>(uw[sgi * D + d]) * static_cast<uint32_t>(nb);
+                    b = static_cast<int>(m >> 32);
+                    fr = static_cast<float>(static_cast<uint32_t>(m)) * 2.3283064365386963e-10f;
                 } else {
                     const R t = u[sgi * D + d] * nbR;
                     b = static_cast<int>(t);
