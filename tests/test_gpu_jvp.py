@@ -98,8 +98,12 @@ def test_jvp_and_vjp_are_transposes(kind, precision, rtol):
     rhs = float(np.sum(gf.cpu().numpy() * u0))
     scale = float(np.sum(np.abs(v0 * JU.cpu().numpy())))
     assert abs(lhs - rhs) <= rtol * scale, (lhs, rhs, scale)
+    # the two kernels sum the same samples in different orders: C~ agrees to
+    # rounding relative to its largest value (a point where gain and loss
+    # nearly cancel has no relative precision of its own in FP32)
     crtol = 1e-12 if precision == W.PREC_FP64 else 1e-6
-    assert np.allclose(C1.cpu().numpy(), C2.cpu().numpy(), rtol=crtol, atol=0)
+    c1, c2 = C1.cpu().numpy(), C2.cpu().numpy()
+    assert np.max(np.abs(c1 - c2)) <= crtol * np.max(np.abs(c2)), np.max(np.abs(c1 - c2)) / np.max(np.abs(c2))
     col.close()
 
 
