@@ -7,6 +7,8 @@ how well N and E are conserved.  Every step of the path runs in libbest; this
 module only sequences the calls and copies the small histories to the host.
 
     python -m paper_2603_28848_gb300.evolve --workload c2_bose_2to2 --steps 200 --every 20
+    python -m paper_2603_28848_gb300.evolve --workload c3_cannibal_2to3 --n 64 --neval 1000000 \
+        --nitn 4 --method euler --dt 1e9 --t0 0 --steps 300 --every 30
 """
 import argparse
 import json
@@ -101,9 +103,18 @@ def main(argv=None):
     ap.add_argument("--t0", type=float, default=1.0)
     ap.add_argument("--method", default="heun", choices=["heun", "euler"])
     ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="grid points (default: the workload's)")
+    ap.add_argument("--neval", type=int, default=None, help="samples per task per iteration")
+    ap.add_argument("--nitn", type=int, default=None, help="VEGAS iterations per evaluation")
+    ap.add_argument("--sides", type=int, default=0, choices=[0, 1, 2],
+                    help="side integrals of every process: 0 all, 1 observed leg initial, 2 final")
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
-    prob, f0 = W.WORKLOADS[args.workload]()
+    kw = {k: v for k, v in (("n", args.n), ("neval", args.neval), ("nitn", args.nitn)) if v is not None}
+    prob, f0 = W.WORKLOADS[args.workload](**kw)
+    if args.sides:
+        from dataclasses import replace
+        prob = replace(prob, processes=tuple(replace(p, sides=args.sides) for p in prob.processes))
     hist = run(prob, f0, args.steps, args.every, W.PREC_FP64 if args.fp64 else W.PREC_FP32, args.method,
                args.t0, args.dt)
     summary = {k: v for k, v in hist.items() if k != "logf"}
@@ -112,7 +123,8 @@ def main(argv=None):
         with open(args.out, "w") as fh:
             fh.write(text + "\n")
     print(json.dumps({k: hist[k] for k in ("max_rel_change_n", "max_rel_change_rho", "final_rel_change_n",
-                                           "final_rel_change_rho", "max_abs_dlogf")} | {"t_final": hist["t"][-1]}))
+                                           "final_rel_change_rho", "max_abs_dlogf")}
+                     | {"t_final": hist["t"][-1], "T_final": hist["T"][-1], "mu_final": hist["mu"][-1]}))
     return 0
 
 
