@@ -82,7 +82,7 @@ struct IterPlan {
     int32_t* d_active = nullptr;     // [n_active] task ids
     int32_t* d_task_seg = nullptr;   // [n_active + 1]
     Segment* d_segs = nullptr;       // [n_segs]
-    int32_t* d_cta_seg = nullptr;    // [grid + 1]
+    int32_t* d_cta_seg = nullptr;    // [chunks + 1]
 };
 
 template <typename T>
@@ -100,6 +100,8 @@ struct best_ctx {
     int precision = 0;
     int nmax_legs = 0;
     int grid = 0;                   // CTAs of the persistent sample kernel
+    int n_chunks = 0;               // chunks of the work partition (kChunkStages x grid)
+    int32_t* d_chunk_ctr = nullptr; // [max_nitn + 1] chunk counters: sample kernel per iteration, adjoint / tangent
     size_t eval_smem = 0;
     size_t spline_smem = 0;
     size_t refine_smem = 0;
@@ -246,6 +248,7 @@ void free_all(best_ctx* c) {
     c->graph = nullptr;
     for (void* b : bufs) cudaFree(b);
     cudaFree(c->d_bctl); cudaFree(c->d_bv); cudaFree(c->d_plan_scratch); cudaFree(c->d_plandev);
+    cudaFree(c->d_chunk_ctr);
 }
 
 best_status validate(const best_config* cfg) {
@@ -372,10 +375,10 @@ size_t sample_smem(const best_ctx* ctx, int threads) {
            (f32 ? sizeof(float) * (threads / 32) * kQueueSlots * queue_words(ctx->nmax_legs) : 0);
 }
 
-// Static partition of the active tasks of one iteration over `grid` CTAs,
-// balanced by an estimate of the cost of a sample group (its samples times
-// the number of dimensions plus a constant).  Segments come out ordered by
-// task, so each task's segment records are contiguous.
+// Partition of the active tasks of one iteration into n_chunks chunks cut at
+// chunk_bound() of an estimate of the cost of a sample group (its samples
+// times the number of dimensions plus a constant).  Segments come out
+// ordered by task, so each task's segment records are contiguous.
 best_status build_plan(best_ctx* ctx, int it, IterPlan& plan) {
     const bool f32 = ctx->precision == BEST_FP32;
     std::vector<int32_t> active;
@@ -395,14 +398,14 @@ best_status build_plan(best_ctx* ctx, int it, IterPlan& plan) {
         cum[a + 1] = cum[a] + groups[a] * cost[a];
     }
     const int64_t W = cum[A];
-    const int B = ctx->grid;
+    const int B = ctx->grid, K = ctx->n_chunks;
     std::vector<Segment> segs;
-    std::vector<int32_t> cta_seg(B + 1, 0);
+    std::vector<int32_t> cta_seg(K + 1, 0);
     std::vector<int32_t> seg_active;
     int a0 = 0;
-    for (int b = 0; b < B; ++b) {
+    for (int b = 0; b < K; ++b) {
         cta_seg[b] = static_cast<int32_t>(segs.size());
-        const int64_t lo = W * b / B, hi = W * (b + 1) / B;
+        const int64_t lo = chunk_bound(W, b, B), hi = chunk_bound(W, b + 1, B);
         while (a0 < A && cum[a0 + 1] <= lo) ++a0;
         for (int a = a0; a < A && cum[a] < hi; ++a) {
             const int64_t c = cost[a];
@@ -417,7 +420,7 @@ best_status build_plan(best_ctx* ctx, int it, IterPlan& plan) {
             seg_active.push_back(a);
         }
     }
-    cta_seg[B] = static_cast<int32_t>(segs.size());
+    cta_seg[K] = static_cast<int32_t>(segs.size());
     // partial records and per-task segment ranges
     std::vector<int32_t> task_seg(A + 1, 0);
     int64_t off = 0;
@@ -440,23 +443,23 @@ best_status build_plan(best_ctx* ctx, int it, IterPlan& plan) {
     plan.partial_doubles = off;
     if (ctx->any_budget) {
         // the device rebuilds this partition when the budgets change: room for
-        // the largest one (each CTA boundary splits at most one task)
+        // the largest one (each chunk boundary splits at most one task)
         int64_t cap = 0, rmax = 0;
         for (int a = 0; a < A; ++a) {
             const TaskDesc& td = ctx->tasks[active[a]];
             cap += record_doubles(td.dim, td.nbins);
             rmax = std::max(rmax, record_doubles(td.dim, td.nbins));
         }
-        plan.partial_doubles = std::max(off, cap + static_cast<int64_t>(B) * rmax);
+        plan.partial_doubles = std::max(off, cap + static_cast<int64_t>(K) * rmax);
     }
     CK(dalloc(&plan.d_active, A));
     CK(dalloc(&plan.d_task_seg, A + 1));
-    CK(dalloc(&plan.d_segs, ctx->any_budget ? static_cast<size_t>(A) + B : segs.size()));
-    CK(dalloc(&plan.d_cta_seg, B + 1));
+    CK(dalloc(&plan.d_segs, ctx->any_budget ? static_cast<size_t>(A) + K : segs.size()));
+    CK(dalloc(&plan.d_cta_seg, K + 1));
     CK(cudaMemcpy(plan.d_active, active.data(), A * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(plan.d_task_seg, task_seg.data(), (A + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(plan.d_segs, segs.data(), segs.size() * sizeof(Segment), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(plan.d_cta_seg, cta_seg.data(), (B + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(plan.d_cta_seg, cta_seg.data(), (K + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
     return BEST_OK;
 }
 
@@ -485,6 +488,7 @@ best_status set_variant(best_ctx* ctx, int v) {
     ctx->variant = v;
     ctx->eval_threads = threads;
     ctx->grid = nsm * occ;
+    ctx->n_chunks = kChunkStages * ctx->grid;
     for (auto& pl : ctx->plans) {
         cudaFree(pl.d_active); cudaFree(pl.d_task_seg); cudaFree(pl.d_segs); cudaFree(pl.d_cta_seg);
     }
@@ -522,7 +526,7 @@ best_status set_variant(best_ctx* ctx, int v) {
         ctx->d_plan_scratch = nullptr;
         CK(dalloc(&ctx->d_plandev, pd.size()));
         CK(cudaMemcpy(ctx->d_plandev, pd.data(), pd.size() * sizeof(PlanDev), cudaMemcpyHostToDevice));
-        CK(dalloc(&ctx->d_plan_scratch, static_cast<size_t>(amax) + 1 + 2 * static_cast<size_t>(ctx->grid)));
+        CK(dalloc(&ctx->d_plan_scratch, static_cast<size_t>(amax) + 1 + 2 * static_cast<size_t>(ctx->n_chunks)));
     }
     return BEST_OK;
 }
@@ -539,6 +543,7 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
                                                             ctx->d_acc, 1, ctx->d_width);
     ctx->launches += 2;
     const bool f32 = ctx->precision == BEST_FP32;
+    CK(cudaMemsetAsync(ctx->d_chunk_ctr, 0, sizeof(int32_t) * ctx->max_nitn, st));
     for (int it = 0; it < ctx->max_nitn; ++it) {
         const IterPlan& pl = ctx->plans[it];
         if (pl.n_active == 0) continue;
@@ -552,6 +557,8 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
         P.edges = ctx->d_edges;
         P.segs = pl.d_segs;
         P.cta_seg = pl.d_cta_seg;
+        P.n_chunks = ctx->n_chunks;
+        P.chunk_counter = ctx->d_chunk_ctr + it;
         P.coef = f32 ? static_cast<const void*>(ctx->d_coef32) : static_cast<const void*>(ctx->d_coef64);
         P.knots = f32 ? static_cast<const void*>(ctx->d_knots32) : static_cast<const void*>(ctx->d_knots);
         P.partials = ctx->d_partials;
@@ -927,6 +934,7 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     CKI(dalloc(&ctx->d_tasks, T));
     CKI(dalloc(&ctx->d_tconst, T));
     CKI(dalloc(&ctx->d_acc, T));
+    CKI(dalloc(&ctx->d_chunk_ctr, static_cast<size_t>(ctx->max_nitn) + 1));
     CKI(dalloc(&ctx->d_sconst, S));
     CKI(dalloc(&ctx->d_ts, 1));
     CKI(dalloc(&ctx->d_edges, static_cast<size_t>(T) * g.map_stride));
@@ -1221,6 +1229,18 @@ best_status best_autotune(best_ctx* ctx, const double* f_dev, double t, int32_t*
     return s;
 }
 
+// CTAs of the persistent adjoint / tangent sample kernel fn: as many as fit
+// on the device at once (the kernel takes the partition's chunks from a
+// counter, so its grid need not match the sample kernel's).
+static cudaError_t adjoint_grid(const best_ctx* ctx, const void* fn, size_t smem, int* grid) {
+    int dev = 0, nsm = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, smem);
+    *grid = std::max(1, std::min(nsm * std::max(occ, 1), ctx->n_chunks));
+    return e;
+}
+
 best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, const double* v_dev, double* C_dev,
                                double* gf_dev, double* gm_dev, double* gcoupling_dev, void* stream) {
     if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
@@ -1262,6 +1282,8 @@ best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, con
     P.edges = ctx->d_edges;
     P.segs = pl.d_segs;
     P.cta_seg = pl.d_cta_seg;
+    P.n_chunks = ctx->n_chunks;
+    P.chunk_counter = ctx->d_chunk_ctr + ctx->max_nitn;
     P.coef = f32 ? static_cast<const void*>(ctx->d_coef32) : static_cast<const void*>(ctx->d_coef64);
     P.knots = f32 ? static_cast<const void*>(ctx->d_knots32) : static_cast<const void*>(ctx->d_knots);
     P.partials = ctx->d_partials;
@@ -1274,7 +1296,10 @@ best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, con
     V.dcoef = nullptr;
     V.dtail = nullptr;
     void* args[] = {&V};
-    CK(cudaLaunchKernel(fn, dim3(ctx->grid), dim3(kThreads), args, ctx->vjp_smem, st));
+    int vgrid = 0;
+    CK(adjoint_grid(ctx, fn, ctx->vjp_smem, &vgrid));
+    CK(cudaMemsetAsync(P.chunk_counter, 0, sizeof(int32_t), st));
+    CK(cudaLaunchKernel(fn, dim3(vgrid), dim3(kThreads), args, ctx->vjp_smem, st));
     vjp_task_kernel<<<(pl.n_active + 127) / 128, 128, 0, st>>>(g, pl.d_active, pl.d_task_seg, pl.d_segs,
                                                                ctx->d_partials, pl.n_active, ctx->d_vjp_tot);
     vjp_finish_kernel<<<1, 32, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_tconst, ctx->d_sconst, ctx->d_ts, v_dev,
@@ -1364,6 +1389,8 @@ static best_status enqueue_jvp(best_ctx* ctx, const double* f_dev, double t, con
     P.edges = ctx->d_edges;
     P.segs = pl.d_segs;
     P.cta_seg = pl.d_cta_seg;
+    P.n_chunks = ctx->n_chunks;
+    P.chunk_counter = ctx->d_chunk_ctr + ctx->max_nitn;
     P.coef = f32 ? static_cast<const void*>(ctx->d_coef32) : static_cast<const void*>(ctx->d_coef64);
     P.knots = f32 ? static_cast<const void*>(ctx->d_knots32) : static_cast<const void*>(ctx->d_knots);
     P.partials = ctx->d_partials;
@@ -1376,7 +1403,10 @@ static best_status enqueue_jvp(best_ctx* ctx, const double* f_dev, double t, con
     V.dcoef = f32 ? static_cast<const void*>(ctx->d_dcoef32) : static_cast<const void*>(ctx->d_dcoef64);
     V.dtail = ctx->d_dtail;
     void* args[] = {&V};
-    CK(cudaLaunchKernel(fn, dim3(ctx->grid), dim3(kThreads), args, ctx->jvp_smem, st));
+    int vgrid = 0;
+    CK(adjoint_grid(ctx, fn, ctx->jvp_smem, &vgrid));
+    CK(cudaMemsetAsync(P.chunk_counter, 0, sizeof(int32_t), st));
+    CK(cudaLaunchKernel(fn, dim3(vgrid), dim3(kThreads), args, ctx->jvp_smem, st));
     vjp_task_kernel<<<(pl.n_active + 127) / 128, 128, 0, st>>>(g, pl.d_active, pl.d_task_seg, pl.d_segs,
                                                                ctx->d_partials, pl.n_active, ctx->d_vjp_tot);
     jvp_finish_kernel<<<1, 32, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_tconst, ctx->d_vjp_tot, C_dev, JU_dev);

@@ -108,20 +108,21 @@ __global__ void budget_kernel(const BudgetCtl* __restrict__ ctl, const TaskAcc* 
 
 // Rebuilds the partition of every iteration index (one CTA, blockDim a
 // power of two): plan p's active tasks are split into segments of sample
-// groups, each CTA b of the persistent grid taking the cost range
-// [W b / B, W (b + 1) / B) with cost (groups x group size x unit) x (D + 6)
-// per task, as the host-built partition does; segments are ordered by task,
-// the partial records laid out in segment order.  scratch: int64 of
-// max(n_active) + 1 + 2 grid.
+// groups, chunk c of the K = kChunkStages B chunks (B: the persistent grid)
+// taking the cost range [chunk_bound(W, c, B), chunk_bound(W, c + 1, B)) with
+// cost (groups x group size x unit) x (D + 6) per task, as the host-built
+// partition does; segments are ordered by task, the partial records laid out
+// in segment order.  scratch: int64 of max(n_active) + 1 + 2 K.
 __global__ void plan_kernel(const TaskDesc* __restrict__ tasks, int n_plans, const PlanDev* __restrict__ plans,
                             int B, int f32, int64_t* scratch) {
     __shared__ int64_t s[1024];
+    const int K = kChunkStages * B;
     for (int p = 0; p < n_plans; ++p) {
         const PlanDev pl = plans[p];
         const int A = pl.n_active;
         int64_t* cum = scratch;                 // [A + 1]
-        int64_t* cnt = scratch + A + 1;         // [B] segments of CTA b, then their first index
-        int64_t* rec = cnt + B;                 // [B] record doubles of CTA b, then their offset
+        int64_t* cnt = scratch + A + 1;         // [K] segments of chunk b, then their first index
+        int64_t* rec = cnt + K;                 // [K] record doubles of chunk b, then their offset
         // cost prefix of the active tasks
         int64_t carry = 0;
         for (int a0 = 0; a0 < A; a0 += blockDim.x) {
@@ -142,10 +143,10 @@ __global__ void plan_kernel(const TaskDesc* __restrict__ tasks, int n_plans, con
         if (threadIdx.x == 0) cum[A] = carry;
         __syncthreads();
         const int64_t W = carry;
-        // pass 1: segments and record doubles per CTA; pass 2: write them
+        // pass 1: segments and record doubles per chunk; pass 2: write them
         for (int pass = 0; pass < 2; ++pass) {
-            for (int b = threadIdx.x; b < B; b += blockDim.x) {
-                const int64_t lo = W * b / B, hi = W * (b + 1) / B;
+            for (int b = threadIdx.x; b < K; b += blockDim.x) {
+                const int64_t lo = chunk_bound(W, b, B), hi = chunk_bound(W, b + 1, B);
                 int a = 0, top = A;             // first a with cum[a + 1] > lo
                 while (a < top) {
                     const int mid = (a + top) >> 1;
@@ -181,14 +182,14 @@ __global__ void plan_kernel(const TaskDesc* __restrict__ tasks, int n_plans, con
             }
             __syncthreads();
             if (!pass) {
-                // exclusive prefixes over the CTAs
+                // exclusive prefixes over the chunks
                 int64_t c1 = 0, c2 = 0;
-                for (int b0 = 0; b0 < B; b0 += blockDim.x) {
+                for (int b0 = 0; b0 < K; b0 += blockDim.x) {
                     const int b = b0 + threadIdx.x;
                     int64_t t1, t2;
-                    const int64_t e1 = cta_scan(b < B ? cnt[b] : 0, s, &t1);
-                    const int64_t e2 = cta_scan(b < B ? rec[b] : 0, s, &t2);
-                    if (b < B) {
+                    const int64_t e1 = cta_scan(b < K ? cnt[b] : 0, s, &t1);
+                    const int64_t e2 = cta_scan(b < K ? rec[b] : 0, s, &t2);
+                    if (b < K) {
                         cnt[b] = c1 + e1;
                         rec[b] = c2 + e2;
                         pl.cta_seg[b] = static_cast<int32_t>(c1 + e1);
@@ -197,7 +198,7 @@ __global__ void plan_kernel(const TaskDesc* __restrict__ tasks, int n_plans, con
                     c2 += t2;
                 }
                 if (threadIdx.x == 0) {
-                    pl.cta_seg[B] = static_cast<int32_t>(c1);
+                    pl.cta_seg[K] = static_cast<int32_t>(c1);
                     pl.task_seg[A] = static_cast<int32_t>(c1);
                 }
                 __syncthreads();

@@ -190,7 +190,10 @@ struct EvalParams {
     const TimeState* ts;
     const double* edges;        // [task][map_stride]
     const Segment* segs;
-    const int32_t* cta_seg;     // segments of CTA b: [cta_seg[b], cta_seg[b+1])
+    const int32_t* cta_seg;     // segments of chunk c: [cta_seg[c], cta_seg[c+1])
+    int32_t n_chunks;           // chunks of the partition
+    int32_t pad_chunks_;
+    int32_t* chunk_counter;     // next chunk to take (reset to 0 before the launch); NULL: CTA b takes chunk b
     const void* coef;           // [species][n-1][4] in R
     const void* knots;          // [n] in R
     double* partials;
@@ -222,15 +225,37 @@ constexpr int kBudgetQuantum = 256;     // budgets are multiples of this many sa
 constexpr int kBudgetBisections = 200;
 
 // The device's view of the work partition of one VEGAS iteration index
-// (rebuilt on the device when budgets change).
+// (rebuilt on the device when budgets change).  The partition cuts the
+// iteration's sample groups into chunks of equal estimated cost; CTAs of the
+// persistent grid take chunks from an atomic counter until none is left, so
+// that CTAs whose chunks ran faster take more of them.
 struct PlanDev {
     int32_t n_active;
     int32_t pad_;
     const int32_t* active;      // [n_active] task ids
     int32_t* task_seg;          // [n_active + 1]
     Segment* segs;              // capacity n_active + grid
-    int32_t* cta_seg;           // [grid + 1]
+    int32_t* cta_seg;           // [chunks + 1]
 };
+
+// Chunks of the dynamic partition: kChunkStages stages of `grid` chunks
+// each, the stages covering 1/2, 1/4, ... of the iteration's estimated cost
+// and the last stage the remainder, so that the chunks taken last (when CTAs
+// run out of work at different times) are small.  chunk_bound(W, c, B, K) is
+// the cost at which chunk c of K = kChunkStages B starts; chunk_bound(W, K,
+// B, K) = W.  Integer arithmetic: the host and the device cut identically.
+#ifndef BEST_CHUNK_STAGES
+#define BEST_CHUNK_STAGES 8
+#endif
+constexpr int kChunkStages = BEST_CHUNK_STAGES;
+__host__ __device__ inline int64_t stage_start(int64_t W, int s) {
+    return s >= kChunkStages ? W : W - (W >> s);
+}
+__host__ __device__ inline int64_t chunk_bound(int64_t W, int c, int B) {
+    const int s = c / B, j = c - s * B;
+    const int64_t lo = stage_start(W, s);
+    return s >= kChunkStages ? W : lo + (stage_start(W, s + 1) - lo) * j / B;
+}
 
 // One instantiation of the sample kernel the autotuner may pick.
 struct SampleVariant {

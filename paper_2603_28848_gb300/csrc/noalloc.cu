@@ -293,6 +293,8 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     P.edges = edges_dev;
     P.segs = reinterpret_cast<const Segment*>(base + kOffSegs);
     P.cta_seg = reinterpret_cast<const int32_t*>(base + kOffCtaSeg);
+    P.n_chunks = ctas;                  // one chunk (segment) per CTA, no counter
+    P.chunk_counter = nullptr;
     P.coef = f32 ? static_cast<const void*>(coef32) : static_cast<const void*>(coef64);
     P.knots = f32 ? static_cast<const void*>(knots32) : static_cast<const void*>(knots);
     P.partials = reinterpret_cast<double*>(base + kOffPart);

@@ -560,20 +560,32 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) vjp_kernel(V
         const R* gk = static_cast<const R*>(P.knots);
         for (int k = threadIdx.x; k < P.geo.n_grid; k += blockDim.x) s_spline[ngc + k] = gk[k];
     }
-    const int s0 = P.cta_seg[blockIdx.x], s1 = P.cta_seg[blockIdx.x + 1];
-    for (int si = s0; si < s1; ++si) {
-        const Segment seg = P.segs[si];
-        const TaskDesc td = P.tasks[seg.task];
-        const SideDesc& sd = P.sides[td.si];
-        const TaskConst tc = P.tconst[seg.task];
-        __syncthreads();
-        switch (sd.n) {
-            case 3: if constexpr (NMAX >= 3) vjp_segment<R, 3, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp, s_queue); break;
-            case 4: if constexpr (NMAX >= 4) vjp_segment<R, 4, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp, s_queue); break;
-            case 5: if constexpr (NMAX >= 5) vjp_segment<R, 5, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp, s_queue); break;
-            case 6: if constexpr (NMAX >= 6) vjp_segment<R, 6, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp, s_queue); break;
-            default: break;
+    // chunks of the partition, as in the sample kernel
+    __shared__ int s_chunk;
+    for (int c = P.chunk_counter ? -1 : static_cast<int>(blockIdx.x);;) {
+        if (P.chunk_counter) {
+            __syncthreads();
+            if (threadIdx.x == 0) s_chunk = atomicAdd(P.chunk_counter, 1);
+            __syncthreads();
+            c = s_chunk;
         }
+        if (c >= P.n_chunks) break;
+        const int s0 = P.cta_seg[c], s1 = P.cta_seg[c + 1];
+        for (int si = s0; si < s1; ++si) {
+            const Segment seg = P.segs[si];
+            const TaskDesc td = P.tasks[seg.task];
+            const SideDesc& sd = P.sides[td.si];
+            const TaskConst tc = P.tconst[seg.task];
+            __syncthreads();
+            switch (sd.n) {
+                case 3: if constexpr (NMAX >= 3) vjp_segment<R, 3, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp, s_queue); break;
+                case 4: if constexpr (NMAX >= 4) vjp_segment<R, 4, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp, s_queue); break;
+                case 5: if constexpr (NMAX >= 5) vjp_segment<R, 5, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp, s_queue); break;
+                case 6: if constexpr (NMAX >= 6) vjp_segment<R, 6, JVP, ME>(V, seg, sd, td, tc, s_spline, s_map, s_gc, s_red, s_dsp, s_queue); break;
+                default: break;
+            }
+        }
+        if (!P.chunk_counter) break;
     }
     if constexpr (!JVP) {
         __syncthreads();
