@@ -407,6 +407,8 @@ def run_native(args, rank, world):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if rank == 0 and not args.skip_cpu:
+        out["fp32_parity"] = fp32_parity(prob, workload()[1], T0)
     if rank == 0 and not args.skip_cpu and WORKLOAD_KEY == "c2":
         with oracle_pool() as pool:
             out["cpu_baseline"] = cpu_baseline(prob, workload()[1], args.cpu_seconds, evals, pool)
@@ -578,6 +580,57 @@ def cpu_baseline(prob, f0, seconds, evals, pool=None, single=True):
                          f"evals/s summed over the processes; sweeps/s = evals/s / evals per sweep ({evals:.3g})",
                "single_core": out}
     return out
+
+
+PARITY_TASKS = 24   # tasks of the FP32-vs-oracle check in the CPU-baseline leg
+
+
+def fp32_parity(prob, f0, t):
+    """FP32 rounding of the sample kernel on this workload: one iteration from
+    uniform maps at the oracle's reduced budget (CPU_NEVAL samples per task),
+    so that the FP32 kernel and the oracle (FP64 arithmetic on the same
+    FP32-form uniforms) see identical samples and differ by rounding only.
+    PARITY_TASKS tasks spread over side integrals, grid points and terms;
+    tasks below 1e-8 of the largest checked value of their side integral and
+    term are left out (FP32 underflow of negligible tasks).  Runs with the
+    CPU baseline (the oracle executes on the host)."""
+    import torch
+
+    import workloads as W
+    from oracle import collision as ocol
+    from oracle import vegas
+    from oracle.tasks import side_integrals
+
+    from paper_2603_28848_gb300 import Collision
+    one = prob.with_budget(neval=CPU_NEVAL, nitn=1)
+    col = Collision(one, W.PREC_FP32)
+    try:
+        col.eval(torch.tensor(np.ascontiguousarray(f0), dtype=torch.float64, device="cuda"), t)
+        col.check()
+        mean, _ = col.task_results()
+    finally:
+        col.close()
+    sis = side_integrals(one)
+    dists = ocol.distributions(one, f0, t)
+    n = one.grid.n
+    rows = []
+    for k in range(PARITY_TASKS):
+        si_idx = k % len(sis)
+        term = (k // len(sis)) % 2
+        i = (7 + 37 * k) % n
+        si = sis[si_idx]
+        p = one.processes[si.process]
+        om = ocol.evaluate_task(one, si_idx, si, i, term, f0, t, vegas.uniform_edges(si.dim, p.nbins), 0, "f32",
+                                dists)[0]
+        rows.append((si_idx, term, om, mean[(si_idx * n + i) * 2 + term]))
+    big = {}
+    for si_idx, term, om, _ in rows:
+        big[(si_idx, term)] = max(big.get((si_idx, term), 0.0), abs(om))
+    rel = [abs(g - om) / abs(om) for si_idx, term, om, g in rows if om != 0 and abs(om) > 1e-8 * big[(si_idx, term)]]
+    return {"tasks": len(rel), "max_rel": float(max(rel)) if rel else None,
+            "median_rel": float(np.median(rel)) if rel else None,
+            "what": f"FP32 sample kernel vs the FP64 oracle on identical samples (one iteration, uniform maps, "
+                    f"{CPU_NEVAL} samples per task): relative difference of the task estimates"}
 
 
 def oracle_pool():

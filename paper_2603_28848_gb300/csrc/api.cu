@@ -100,7 +100,7 @@ struct best_ctx {
     int precision = 0;
     int nmax_legs = 0;
     int grid = 0;                   // CTAs of the persistent sample kernel
-    int n_chunks = 0;               // chunks of the work partition (kChunkStages x grid)
+    int n_chunks = 0;               // chunks of the work partition (chunk_count(grid))
     int32_t* d_chunk_ctr = nullptr; // [max_nitn + 1] chunk counters: sample kernel per iteration, adjoint / tangent
     size_t eval_smem = 0;
     size_t spline_smem = 0;
@@ -488,7 +488,7 @@ best_status set_variant(best_ctx* ctx, int v) {
     ctx->variant = v;
     ctx->eval_threads = threads;
     ctx->grid = nsm * occ;
-    ctx->n_chunks = kChunkStages * ctx->grid;
+    ctx->n_chunks = chunk_count(ctx->grid);
     for (auto& pl : ctx->plans) {
         cudaFree(pl.d_active); cudaFree(pl.d_task_seg); cudaFree(pl.d_segs); cudaFree(pl.d_cta_seg);
     }

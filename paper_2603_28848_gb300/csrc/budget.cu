@@ -108,7 +108,7 @@ __global__ void budget_kernel(const BudgetCtl* __restrict__ ctl, const TaskAcc* 
 
 // Rebuilds the partition of every iteration index (one CTA, blockDim a
 // power of two): plan p's active tasks are split into segments of sample
-// groups, chunk c of the K = kChunkStages B chunks (B: the persistent grid)
+// groups, chunk c of the K = chunk_count(B) chunks (B: the persistent grid)
 // taking the cost range [chunk_bound(W, c, B), chunk_bound(W, c + 1, B)) with
 // cost (groups x group size x unit) x (D + 6) per task, as the host-built
 // partition does; segments are ordered by task, the partial records laid out
@@ -116,7 +116,7 @@ __global__ void budget_kernel(const BudgetCtl* __restrict__ ctl, const TaskAcc* 
 __global__ void plan_kernel(const TaskDesc* __restrict__ tasks, int n_plans, const PlanDev* __restrict__ plans,
                             int B, int f32, int64_t* scratch) {
     __shared__ int64_t s[1024];
-    const int K = kChunkStages * B;
+    const int K = chunk_count(B);
     for (int p = 0; p < n_plans; ++p) {
         const PlanDev pl = plans[p];
         const int A = pl.n_active;

@@ -238,23 +238,30 @@ struct PlanDev {
     int32_t* cta_seg;           // [chunks + 1]
 };
 
-// Chunks of the dynamic partition: kChunkStages stages of `grid` chunks
-// each, the stages covering 1/2, 1/4, ... of the iteration's estimated cost
-// and the last stage the remainder, so that the chunks taken last (when CTAs
-// run out of work at different times) are small.  chunk_bound(W, c, B, K) is
-// the cost at which chunk c of K = kChunkStages B starts; chunk_bound(W, K,
-// B, K) = W.  Integer arithmetic: the host and the device cut identically.
+// Chunks of the dynamic partition: kChunkStages stages of kChunkSplit x
+// `grid` chunks each, the stages covering 1/2, 1/4, ... of the iteration's
+// estimated cost and the last stage the remainder, so that the chunks taken
+// last (when CTAs run out of work at different times) are small.
+// chunk_bound(W, c, B) is the cost at which chunk c of chunk_count(B) starts;
+// chunk_bound(W, chunk_count(B), B) = W.  Integer arithmetic: the host and
+// the device cut identically.
 #ifndef BEST_CHUNK_STAGES
 #define BEST_CHUNK_STAGES 8
 #endif
+#ifndef BEST_CHUNK_SPLIT
+#define BEST_CHUNK_SPLIT 2
+#endif
 constexpr int kChunkStages = BEST_CHUNK_STAGES;
+constexpr int kChunkSplit = BEST_CHUNK_SPLIT;
+__host__ __device__ inline int chunk_count(int B) { return kChunkStages * kChunkSplit * B; }
 __host__ __device__ inline int64_t stage_start(int64_t W, int s) {
     return s >= kChunkStages ? W : W - (W >> s);
 }
 __host__ __device__ inline int64_t chunk_bound(int64_t W, int c, int B) {
-    const int s = c / B, j = c - s * B;
+    const int per = kChunkSplit * B;
+    const int s = c / per, j = c - s * per;
     const int64_t lo = stage_start(W, s);
-    return s >= kChunkStages ? W : lo + (stage_start(W, s + 1) - lo) * j / B;
+    return s >= kChunkStages ? W : lo + (stage_start(W, s + 1) - lo) * j / per;
 }
 
 // One instantiation of the sample kernel the autotuner may pick.

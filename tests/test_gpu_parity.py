@@ -127,11 +127,14 @@ def test_linear_grid_minimal_fp64():
     _compare_fp64(prob, f0)
 
 
-def _compare_fp32(problem, f0, t=0.0):
+def _compare_fp32(problem, f0, t=0.0, rtol_max=5e-3, rtol_median=5e-4):
     """FP32 path against the oracle on the same (FP32-form) uniform stream.
 
     One iteration: the samples are identical, so the tasks differ by FP32
-    rounding only (checked to 5e-3 relative).  Several iterations: the FP32
+    rounding only: the largest and the median relative difference over the
+    significant tasks are held to per-workload bounds (2-4x what the
+    workloads show; the largest come from tasks whose positive and negative
+    energy-balance contributions nearly cancel).  Several iterations: the FP32
     and FP64 training data refine the maps slightly differently and the maps
     drift apart on high-variance tasks, so the later iterations are only
     partly correlated; the check is then statistical: at least 95% of the
@@ -144,7 +147,8 @@ def _compare_fp32(problem, f0, t=0.0):
     om, _ = task_arrays(detail, col.n_tasks)
     sig = _significance(one, om)
     keep = np.abs(om) > 1e-8 * sig
-    assert np.max(rel_diff(mean[keep], om[keep])) < 5e-3
+    r = rel_diff(mean[keep], om[keep])
+    assert np.max(r) < rtol_max and np.median(r) < rtol_median, (np.max(r), np.median(r))
     col.close()
 
     col = _gpu(problem, W.PREC_FP32)
@@ -164,17 +168,17 @@ def _compare_fp32(problem, f0, t=0.0):
 
 def test_c1_fp32_within_three_sigma():
     prob, f0 = W.c1_maxwell_2to2()
-    _compare_fp32(prob, f0)
+    _compare_fp32(prob, f0, rtol_max=2e-3, rtol_median=5e-5)
 
 
 def test_2to3_fp32_within_three_sigma():
     prob, f0 = W.c3_cannibal_2to3(n=8, neval=4001, nitn=2)
-    _compare_fp32(prob, f0)
+    _compare_fp32(prob, f0, rtol_max=6e-3, rtol_median=6e-4)
 
 
 def test_multi_species_fp32_within_three_sigma():
     prob, f0 = W.c4_multi_species(n=8, nmin=1000, nmax=4000, nitn=2)
-    _compare_fp32(prob, f0, t=2.0)
+    _compare_fp32(prob, f0, t=2.0, rtol_max=4e-3, rtol_median=6e-4)
 
 
 @pytest.mark.parametrize("sigma", [50.0, 5e-3])
