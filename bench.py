@@ -34,12 +34,14 @@ UNIT = "sweeps/s"
 WORKLOAD = "c2_bose_2to2"
 DT = 0.5          # requested Heun step (bounded by Eq. (16) inside each step)
 CPU_NEVAL = 20_000  # samples per iteration of the oracle tasks timed on the host
-# DRAM bytes per sample-kernel launch from the last ncu capture of this kernel version
-TRAFFIC_BYTES_PER_LAUNCH = 1.529088e6
-# Thread instructions per sample of the 2->2 Bose sample kernel, from the same ncu capture
-# (smsp__inst_executed.sum x 32 / samples: issue slots in thread units): the kernel is issue-bound, so its
-# instruction issue rate against the SMs' issue peak says how close it is to the hardware limit.
-INSTR_PER_SAMPLE_C2 = 346.4
+# DRAM bytes per sample-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum) and thread
+# instructions per sample (smsp__inst_executed.sum x 32 / samples: issue slots in thread units) of the
+# 2->2 Bose sample kernel, from one ncu capture of a timed-step launch of this kernel version at
+# 5e5 samples per task (summarised under profiles/); the tables it reads do not grow with
+# the sample count.  The kernel is issue-bound, so its instruction issue rate against the SMs' issue peak
+# says how close it is to the hardware limit.
+TRAFFIC_BYTES_PER_LAUNCH = 1.865984e6
+INSTR_PER_SAMPLE_C2 = 337.2
 ISSUE_PEAK_TINSTR = 152 * 4 * 32 * 2.07e9 / 1e12     # 4 schedulers x 1 warp instruction / clock
 FP32_PEAK_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 

@@ -578,7 +578,16 @@ __global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
             const double v = sm[k] / t;
             if (v < 1e-30) o = 0.0;            // numerically empty increment
             else if (v >= 1.0) o = 1.0;
-            else o = pow((1.0 - v) / -log(v), td.alpha);
+            else if (g.precision == BEST_FP32) {
+                // the FP32 path's training data carry FP32 rounding: its
+                // compression is evaluated in FP32 too (FP64 log and pow run
+                // at a small fraction of the FP32 rate on this GPU)
+                const float vf = static_cast<float>(v);
+                o = vf < 1.0f ? static_cast<double>(powf((1.0f - vf) / -logf(vf), static_cast<float>(td.alpha)))
+                              : 1.0;
+            } else {
+                o = pow((1.0 - v) / -log(v), td.alpha);
+            }
         }
         sm[k] = o;
     }
