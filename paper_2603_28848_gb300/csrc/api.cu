@@ -376,9 +376,10 @@ size_t sample_smem(const best_ctx* ctx, int threads) {
 }
 
 // Partition of the active tasks of one iteration into n_chunks chunks cut at
-// chunk_bound() of an estimate of the cost of a sample group (its samples
-// times the number of dimensions plus a constant).  Segments come out
-// ordered by task, so each task's segment records are contiguous.
+// chunk_bound() (shape from chunk_shape()) of an estimate of the cost of a
+// sample group (its samples times the number of dimensions plus a constant).
+// Segments come out ordered by task, so each task's segment records are
+// contiguous.
 best_status build_plan(best_ctx* ctx, int it, IterPlan& plan) {
     const bool f32 = ctx->precision == BEST_FP32;
     std::vector<int32_t> active;
@@ -399,13 +400,14 @@ best_status build_plan(best_ctx* ctx, int it, IterPlan& plan) {
     }
     const int64_t W = cum[A];
     const int B = ctx->grid, K = ctx->n_chunks;
+    const ChunkShape sh = chunk_shape(W, B);
     std::vector<Segment> segs;
     std::vector<int32_t> cta_seg(K + 1, 0);
     std::vector<int32_t> seg_active;
     int a0 = 0;
     for (int b = 0; b < K; ++b) {
         cta_seg[b] = static_cast<int32_t>(segs.size());
-        const int64_t lo = chunk_bound(W, b, B), hi = chunk_bound(W, b + 1, B);
+        const int64_t lo = chunk_bound(W, b, sh), hi = chunk_bound(W, b + 1, sh);
         while (a0 < A && cum[a0 + 1] <= lo) ++a0;
         for (int a = a0; a < A && cum[a] < hi; ++a) {
             const int64_t c = cost[a];

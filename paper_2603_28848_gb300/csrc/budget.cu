@@ -109,7 +109,8 @@ __global__ void budget_kernel(const BudgetCtl* __restrict__ ctl, const TaskAcc* 
 // Rebuilds the partition of every iteration index (one CTA, blockDim a
 // power of two): plan p's active tasks are split into segments of sample
 // groups, chunk c of the K = chunk_count(B) chunks (B: the persistent grid)
-// taking the cost range [chunk_bound(W, c, B), chunk_bound(W, c + 1, B)) with
+// taking the cost range [chunk_bound(W, c, sh), chunk_bound(W, c + 1, sh)),
+// sh = chunk_shape(W, B), with
 // cost (groups x group size x unit) x (D + 6) per task, as the host-built
 // partition does; segments are ordered by task, the partial records laid out
 // in segment order.  scratch: int64 of max(n_active) + 1 + 2 K.
@@ -143,10 +144,11 @@ __global__ void plan_kernel(const TaskDesc* __restrict__ tasks, int n_plans, con
         if (threadIdx.x == 0) cum[A] = carry;
         __syncthreads();
         const int64_t W = carry;
+        const ChunkShape sh = chunk_shape(W, B);
         // pass 1: segments and record doubles per chunk; pass 2: write them
         for (int pass = 0; pass < 2; ++pass) {
             for (int b = threadIdx.x; b < K; b += blockDim.x) {
-                const int64_t lo = chunk_bound(W, b, B), hi = chunk_bound(W, b + 1, B);
+                const int64_t lo = chunk_bound(W, b, sh), hi = chunk_bound(W, b + 1, sh);
                 int a = 0, top = A;             // first a with cum[a + 1] > lo
                 while (a < top) {
                     const int mid = (a + top) >> 1;

@@ -238,13 +238,16 @@ struct PlanDev {
     int32_t* cta_seg;           // [chunks + 1]
 };
 
-// Chunks of the dynamic partition: kChunkStages stages of kChunkSplit x
-// `grid` chunks each, the stages covering 1/2, 1/4, ... of the iteration's
-// estimated cost and the last stage the remainder, so that the chunks taken
-// last (when CTAs run out of work at different times) are small.
-// chunk_bound(W, c, B) is the cost at which chunk c of chunk_count(B) starts;
-// chunk_bound(W, chunk_count(B), B) = W.  Integer arithmetic: the host and
-// the device cut identically.
+// Chunks of the dynamic partition.  With enough work (W, the iteration's
+// estimated cost, at least chunk_count(B) x kMinChunkCost) the partition has
+// kChunkStages stages of kChunkSplit x B chunks (B: the persistent grid), the
+// stages covering 1/2, 1/4, ... of W and the last stage the remainder, so
+// that the chunks taken last (when CTAs run out of work at different times)
+// are small.  With less work it has max(B, W / kMinChunkCost) equal chunks,
+// so that no chunk is so small that the per-segment set-up (map table,
+// histograms, record) outweighs its samples.  Chunks past the last one are
+// empty: the kernels always see chunk_count(B) chunks.  Integer arithmetic:
+// the host and the device cut identically.
 #ifndef BEST_CHUNK_STAGES
 #define BEST_CHUNK_STAGES 8
 #endif
@@ -253,15 +256,26 @@ struct PlanDev {
 #endif
 constexpr int kChunkStages = BEST_CHUNK_STAGES;
 constexpr int kChunkSplit = BEST_CHUNK_SPLIT;
+constexpr int64_t kMinChunkCost = 8192LL * 12;   // cost of 8192 samples of a 2 -> 2 task
 __host__ __device__ inline int chunk_count(int B) { return kChunkStages * kChunkSplit * B; }
-__host__ __device__ inline int64_t stage_start(int64_t W, int s) {
-    return s >= kChunkStages ? W : W - (W >> s);
+struct ChunkShape {
+    int stages;             // stages of the partition
+    int per;                // chunks per stage
+};
+__host__ __device__ inline ChunkShape chunk_shape(int64_t W, int B) {
+    const int kmax = chunk_count(B);
+    const int64_t want = W / kMinChunkCost;
+    if (want >= kmax) return ChunkShape{kChunkStages, kChunkSplit * B};
+    return ChunkShape{1, want < B ? B : static_cast<int>(want)};
 }
-__host__ __device__ inline int64_t chunk_bound(int64_t W, int c, int B) {
-    const int per = kChunkSplit * B;
-    const int s = c / per, j = c - s * per;
-    const int64_t lo = stage_start(W, s);
-    return s >= kChunkStages ? W : lo + (stage_start(W, s + 1) - lo) * j / per;
+__host__ __device__ inline int64_t stage_start(int64_t W, int s, int stages) {
+    return s >= stages ? W : W - (W >> s);
+}
+__host__ __device__ inline int64_t chunk_bound(int64_t W, int c, const ChunkShape& sh) {
+    const int s = c / sh.per, j = c - s * sh.per;
+    if (s >= sh.stages) return W;
+    const int64_t lo = stage_start(W, s, sh.stages);
+    return lo + (stage_start(W, s + 1, sh.stages) - lo) * j / sh.per;
 }
 
 // One instantiation of the sample kernel the autotuner may pick.

