@@ -879,14 +879,18 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
             return bail(fail(ctx, BEST_ERR_INVALID, "spline and map tables need %zu B of shared memory (max %d)",
                              sample_smem(ctx, kThreads), max_optin));
         cudaFuncAttributes fa{};
-        ctx->spline_smem = 3 * sizeof(double) * g.n_grid;
-        if (cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(&spline_build_kernel)) != cudaSuccess)
-            return bail(fail(ctx, BEST_ERR_CUDA, "cannot query the spline kernel"));
-        if (static_cast<size_t>(fa.maxDynamicSharedSizeBytes) < ctx->spline_smem &&
-            cudaFuncSetAttribute(reinterpret_cast<const void*>(&spline_build_kernel),
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(ctx->spline_smem)) != cudaSuccess)
-            return bail(fail(ctx, BEST_ERR_CUDA, "cannot set shared memory of the spline kernel"));
-        ctx->refine_smem = sizeof(double) * (3 * static_cast<size_t>(kMaxDim) * nb_max + 2 * kMaxDim + 2);
+        ctx->spline_smem = 5 * sizeof(double) * g.n_grid;
+        for (const void* fn : {reinterpret_cast<const void*>(&spline_build_kernel),
+                               reinterpret_cast<const void*>(&spline_tangent_kernel),
+                               reinterpret_cast<const void*>(&spline_adjoint_kernel)}) {
+            if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess)
+                return bail(fail(ctx, BEST_ERR_CUDA, "cannot query the spline kernels"));
+            if (static_cast<size_t>(fa.maxDynamicSharedSizeBytes) < ctx->spline_smem &&
+                cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(ctx->spline_smem)) != cudaSuccess)
+                return bail(fail(ctx, BEST_ERR_CUDA, "cannot set shared memory of the spline kernels"));
+        }
+        ctx->refine_smem = sizeof(double) * (4 * static_cast<size_t>(kMaxDim) * nb_max + 2 * kMaxDim + 2);
         if (cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(&refine_kernel)) != cudaSuccess)
             return bail(fail(ctx, BEST_ERR_CUDA, "cannot query the refinement kernel"));
         if (static_cast<size_t>(fa.maxDynamicSharedSizeBytes) < ctx->refine_smem &&

@@ -29,14 +29,18 @@ __global__ void set_time_kernel(Geometry g, TimeState* ts, const double* t_dev, 
 // the tridiagonal system for M_1 .. M_{n-2} with the not-a-knot conditions
 // (third derivative continuous at q_1 and q_{n-2}) eliminated into its first
 // and last rows, solved by the Thomas algorithm; then M_0 and M_{n-1}.
-// cp: scratch of n doubles.  Single thread.
-__device__ void notaknot_moments(int n, const double* __restrict__ knots, const double* f, double* cp, double* M) {
+// Called by every thread of the CTA: the rows (sub-, main and
+// super-diagonal, right-hand side) are formed in parallel in shared memory,
+// then one thread runs the recurrence (one division per row, no global
+// loads in the dependent chain).  cp, A, Bd: scratch of n doubles each.
+__device__ void notaknot_moments(int n, const double* __restrict__ knots, const double* f, double* cp,
+                                 double* M, double* A, double* Bd) {
     const int m = n - 2;    // unknowns M_1 .. M_{n-2}
     auto h = [&](int i) { return knots[i + 1] - knots[i]; };
-    auto rhs = [&](int i) { return 6.0 * ((f[i + 1] - f[i]) / h(i) - (f[i] - f[i - 1]) / h(i - 1)); };
-    for (int k = 0; k < m; ++k) {
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
         const int i = k + 1;
-        double a = h(i - 1), b = 2.0 * (h(i - 1) + h(i)), c = h(i), d = rhs(i);
+        double a = h(i - 1), b = 2.0 * (h(i - 1) + h(i)), c = h(i);
+        const double d = 6.0 * ((f[i + 1] - f[i]) / h(i) - (f[i] - f[i - 1]) / h(i - 1));
         if (k == 0) {
             const double h0 = h(0), h1 = h(1);
             b += h0 * (h0 + h1) / h1;
@@ -49,20 +53,48 @@ __device__ void notaknot_moments(int n, const double* __restrict__ knots, const 
             b += hl * (hl + hp) / hp;
             c = 0.0;
         }
-        if (k > 0) {
-            const double den = b - a * cp[k - 1];
-            cp[k] = c / den;
-            M[k + 1] = (d - a * M[k]) / den;
-        } else {
-            cp[k] = c / b;
-            M[k + 1] = d / b;
-        }
+        A[k] = a;
+        Bd[k] = b;
+        cp[k] = c;
+        M[k + 1] = d;
     }
-    for (int k = m - 2; k >= 0; --k) M[k + 1] -= cp[k] * M[k + 2];
-    const double h0 = h(0), h1 = h(1);
-    M[0] = ((h0 + h1) * M[1] - h0 * M[2]) / h1;
-    const double hl = h(n - 2), hp = h(n - 3);
-    M[n - 1] = ((hl + hp) * M[n - 2] - hl * M[n - 3]) / hp;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < m; ++k) {
+            const double den = k > 0 ? Bd[k] - A[k] * cp[k - 1] : Bd[k];
+            const double r = 1.0 / den;
+            cp[k] *= r;
+            M[k + 1] = (k > 0 ? M[k + 1] - A[k] * M[k] : M[k + 1]) * r;
+        }
+        for (int k = m - 2; k >= 0; --k) M[k + 1] -= cp[k] * M[k + 2];
+        const double h0 = h(0), h1 = h(1);
+        M[0] = ((h0 + h1) * M[1] - h0 * M[2]) / h1;
+        const double hl = h(n - 2), hp = h(n - 3);
+        M[n - 1] = ((hl + hp) * M[n - 2] - hl * M[n - 3]) / hp;
+    }
+    __syncthreads();
+}
+
+// Least-squares line y = a + b x through the K end points of one end of
+// the grid (end 0: j < K; end 1: j >= n - K), x and y given per grid point.
+__device__ inline void end_fit(int n, int K, int end, const double* x, const double* y, double* a0, double* b) {
+    double xm = 0.0, ym = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const int j = end == 0 ? k : n - K + k;
+        xm += x[j];
+        ym += y[j];
+    }
+    xm /= K;
+    ym /= K;
+    double sxy = 0.0, sxx = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const int j = end == 0 ? k : n - K + k;
+        const double xc = x[j] - xm;
+        sxy += xc * (y[j] - ym);
+        sxx += xc * xc;
+    }
+    *b = sxy / sxx;
+    *a0 = ym - *b * xm;
 }
 
 // ---------------------------------------------------------------------------
@@ -72,7 +104,7 @@ __device__ void notaknot_moments(int n, const double* __restrict__ knots, const 
 // eliminated into the first and last rows; then the interval coefficients
 // and the least-squares end fits of log(1/f + eta) against E(q/a) (Eq. (13)).
 // src_mode 0: f given; 1: f = exp(src) (log f).
-// Dynamic shared memory: 3 n doubles.
+// Dynamic shared memory: 5 n doubles.
 // ---------------------------------------------------------------------------
 __global__ void spline_build_kernel(Geometry g, const double* __restrict__ src, int src_mode,
                                     const double* __restrict__ knots, TimeState* ts,
@@ -84,6 +116,8 @@ __global__ void spline_build_kernel(Geometry g, const double* __restrict__ src, 
     double* f = sh;
     double* cp = sh + n;
     double* M = sh + 2 * n;
+    double* X = sh + 3 * n;            // row scratch, then the end fits' abscissae
+    double* Y = sh + 4 * n;            // row scratch, then the end fits' ordinates
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         double v = src[static_cast<int64_t>(s) * n + j];
         if (src_mode == 1) v = exp(v);
@@ -92,8 +126,7 @@ __global__ void spline_build_kernel(Geometry g, const double* __restrict__ src, 
         fgrid[static_cast<int64_t>(s) * n + j] = v;
     }
     __syncthreads();
-    if (threadIdx.x == 0) notaknot_moments(n, knots, f, cp, M);
-    __syncthreads();
+    notaknot_moments(n, knots, f, cp, M, X, Y);
     for (int j = threadIdx.x; j < n - 1; j += blockDim.x) {
         const double hj = knots[j + 1] - knots[j];
         const double c0 = f[j];
@@ -105,34 +138,24 @@ __global__ void spline_build_kernel(Geometry g, const double* __restrict__ src, 
         coef32[o + 0] = static_cast<float>(c0); coef32[o + 1] = static_cast<float>(c1);
         coef32[o + 2] = static_cast<float>(c2); coef32[o + 3] = static_cast<float>(c3);
     }
-    if (threadIdx.x == 0) {
-        const double eta = sc[s].eta;
-        const double m = ts->mass[s];
-        const double a = ts->a;
-        const int K = g.tail_points;
-        for (int end = 0; end < 2; ++end) {
-            double xm = 0.0, ym = 0.0;
-            for (int k = 0; k < K; ++k) {
-                const int j = end == 0 ? k : n - K + k;
-                const double p = knots[j] / a;
-                xm += sqrt(p * p + m * m);
-                ym += log(1.0 / f[j] + eta);
-            }
-            xm /= K;
-            ym /= K;
-            double sxy = 0.0, sxx = 0.0;
-            for (int k = 0; k < K; ++k) {
-                const int j = end == 0 ? k : n - K + k;
-                const double p = knots[j] / a;
-                const double x = sqrt(p * p + m * m) - xm;
-                sxy += x * (log(1.0 / f[j] + eta) - ym);
-                sxx += x * x;
-            }
-            const double b = sxy / sxx;
-            const double a0 = ym - b * xm;
-            if (end == 0) { sc[s].tail_lo_a = a0; sc[s].tail_lo_b = b; }
-            else { sc[s].tail_hi_a = a0; sc[s].tail_hi_b = b; }
-        }
+    // end fits: E(q_j / a) and log(1/f_j + eta) of the 2K end points in
+    // parallel, then one line per end
+    const double eta = sc[s].eta;
+    const double mass = ts->mass[s];
+    const double a = ts->a;
+    const int K = g.tail_points;
+    for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) {
+        const int j = t < K ? t : n - 2 * K + t;
+        const double p = knots[j] / a;
+        X[j] = sqrt(p * p + mass * mass);
+        Y[j] = log(1.0 / f[j] + eta);
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double a0, b;
+        end_fit(n, K, threadIdx.x, X, Y, &a0, &b);
+        if (threadIdx.x == 0) { sc[s].tail_lo_a = a0; sc[s].tail_lo_b = b; }
+        else { sc[s].tail_hi_a = a0; sc[s].tail_hi_b = b; }
     }
 }
 
@@ -141,7 +164,7 @@ __global__ void spline_build_kernel(Geometry g, const double* __restrict__ src, 
 // CTA): the interval coefficients are linear in f, so the tangent spline is
 // the spline of u (no clamping); the end fits y = log(1/f + eta) = a + b E
 // move by da, db from dy_j = -u_j / (f_j (1 + eta f_j)).  Dynamic shared
-// memory: 3 n doubles.
+// memory: 5 n doubles.
 // ---------------------------------------------------------------------------
 __global__ void spline_tangent_kernel(Geometry g, const double* __restrict__ u, const double* __restrict__ knots,
                                       const double* __restrict__ fgrid, const SpeciesConst* __restrict__ sc,
@@ -152,10 +175,11 @@ __global__ void spline_tangent_kernel(Geometry g, const double* __restrict__ u, 
     double* du = sh;
     double* cp = sh + n;
     double* M = sh + 2 * n;
+    double* X = sh + 3 * n;
+    double* Y = sh + 4 * n;
     for (int j = threadIdx.x; j < n; j += blockDim.x) du[j] = u[static_cast<int64_t>(s) * n + j];
     __syncthreads();
-    if (threadIdx.x == 0) notaknot_moments(n, knots, du, cp, M);
-    __syncthreads();
+    notaknot_moments(n, knots, du, cp, M, X, Y);
     for (int j = threadIdx.x; j < n - 1; j += blockDim.x) {
         const double hj = knots[j + 1] - knots[j];
         const double c0 = du[j];
@@ -167,34 +191,23 @@ __global__ void spline_tangent_kernel(Geometry g, const double* __restrict__ u, 
         dcoef32[o + 0] = static_cast<float>(c0); dcoef32[o + 1] = static_cast<float>(c1);
         dcoef32[o + 2] = static_cast<float>(c2); dcoef32[o + 3] = static_cast<float>(c3);
     }
-    if (threadIdx.x == 0) {
-        const double eta = sc[s].eta;
-        const double m = ts->mass[s];
-        const double a = ts->a;
-        const int K = g.tail_points;
-        const double* f = fgrid + static_cast<int64_t>(s) * n;
-        for (int end = 0; end < 2; ++end) {
-            double xm = 0.0, dym = 0.0;
-            for (int q = 0; q < K; ++q) {
-                const int j = end == 0 ? q : n - K + q;
-                const double p = knots[j] / a;
-                xm += sqrt(p * p + m * m);
-                dym += -du[j] / (f[j] * (1.0 + eta * f[j]));
-            }
-            xm /= K;
-            dym /= K;
-            double sxy = 0.0, sxx = 0.0;
-            for (int q = 0; q < K; ++q) {
-                const int j = end == 0 ? q : n - K + q;
-                const double p = knots[j] / a;
-                const double x = sqrt(p * p + m * m) - xm;
-                sxy += x * (-du[j] / (f[j] * (1.0 + eta * f[j])) - dym);
-                sxx += x * x;
-            }
-            const double db = sxy / sxx;
-            dtail[s * 4 + 2 * end] = dym - db * xm;
-            dtail[s * 4 + 2 * end + 1] = db;
-        }
+    const double eta = sc[s].eta;
+    const double mass = ts->mass[s];
+    const double a = ts->a;
+    const int K = g.tail_points;
+    const double* f = fgrid + static_cast<int64_t>(s) * n;
+    for (int t = threadIdx.x; t < 2 * K; t += blockDim.x) {
+        const int j = t < K ? t : n - 2 * K + t;
+        const double p = knots[j] / a;
+        X[j] = sqrt(p * p + mass * mass);
+        Y[j] = -du[j] / (f[j] * (1.0 + eta * f[j]));
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double da, db;
+        end_fit(n, K, threadIdx.x, X, Y, &da, &db);
+        dtail[s * 4 + 2 * threadIdx.x] = da;
+        dtail[s * 4 + 2 * threadIdx.x + 1] = db;
     }
 }
 
@@ -563,6 +576,7 @@ __global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
     double* sm = hist + 2 + D * nb;            // smoothed, then compressed weights [D][nb]
     double* tot = sm + D * nb;                 // per-dimension sums [D]
     double* newe = tot + D;                    // new edges [D][nb + 1]
+    double* rom = newe + D * (nb + 1);         // reciprocals of the compressed weights [D][nb]
     for (int k = threadIdx.x; k < D * nb; k += blockDim.x) {
         const int d = k / nb, b = k - d * nb;
         const double* dd = hist + 2 + d * nb;
@@ -600,11 +614,16 @@ __global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
             }
         }
         sm[k] = o;
+        // the walk below multiplies by these reciprocals (o is 0 or at least
+        // (1 / ln 1e30)^alpha): FP64 division is a long dependent sequence
+        // on this GPU, and the walk is serial per dimension
+        rom[k] = o > 0.0 ? 1.0 / o : 0.0;
     }
     __syncthreads();
     if (threadIdx.x < D) {
         const int d = threadIdx.x;
         const double* om = sm + d * nb;
+        const double* rm = rom + d * nb;
         double* e = edges + static_cast<int64_t>(t) * g.map_stride + d * (nb + 1);
         if (tot[d] > 0.0) {
             double otot = 0.0;
@@ -623,7 +642,7 @@ __global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
                     lo_i = e[i];
                     hi_i = e[i + 1];
                 }
-                double fr = om[i] > 0.0 ? (goal - accw) / om[i] : 0.0;
+                double fr = (goal - accw) * rm[i];
                 fr = fr < 0.0 ? 0.0 : (fr > 1.0 ? 1.0 : fr);
                 ne[k] = lo_i + fr * (hi_i - lo_i);
             }

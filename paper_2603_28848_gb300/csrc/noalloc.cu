@@ -275,7 +275,7 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     float* coef32 = reinterpret_cast<float*>(base + kOffCoef32);
 
     noalloc_setup_kernel<<<1, 512, 0, st>>>(A, base);
-    const size_t spline_smem = 3 * sizeof(double) * n;
+    const size_t spline_smem = 5 * sizeof(double) * n;
     spline_build_kernel<<<S, 256, spline_smem, st>>>(g, f_dev, 0, knots, ts, sc, fgrid, coef64, coef32);
     prepare_kernel<<<1, 32, 0, st>>>(g, dsd, dtd, knots, fgrid, ts, prev, dtc, dacc, 1, nullptr);
 
