@@ -572,11 +572,17 @@ __global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
     }
     if (underflow) return;
     // refinement: smoothing and compression in parallel over (dimension,
-    // increment), the cumulative re-partition by one thread per dimension
+    // increment); the running sums of the compressed weights per dimension
+    // (one thread each, in increment order); then every new edge in
+    // parallel: the increment where the running sum reaches k / nb of the
+    // total, and the linear interpolation inside it
     double* sm = hist + 2 + D * nb;            // smoothed, then compressed weights [D][nb]
     double* tot = sm + D * nb;                 // per-dimension sums [D]
-    double* newe = tot + D;                    // new edges [D][nb + 1]
-    double* rom = newe + D * (nb + 1);         // reciprocals of the compressed weights [D][nb]
+    double* olde = tot + D;                    // old edges [D][nb + 1]
+    double* rom = olde + D * (nb + 1);         // reciprocals of the compressed weights [D][nb]
+    double* cum = rom + D * nb;                // running sums of the compressed weights [D][nb + 1]
+    const double* e_task = edges + static_cast<int64_t>(t) * g.map_stride;
+    for (int k = threadIdx.x; k < D * (nb + 1); k += blockDim.x) olde[k] = e_task[k];
     for (int k = threadIdx.x; k < D * nb; k += blockDim.x) {
         const int d = k / nb, b = k - d * nb;
         const double* dd = hist + 2 + d * nb;
@@ -614,42 +620,50 @@ __global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
             }
         }
         sm[k] = o;
-        // the walk below multiplies by these reciprocals (o is 0 or at least
-        // (1 / ln 1e30)^alpha): FP64 division is a long dependent sequence
-        // on this GPU, and the walk is serial per dimension
+        // the interpolation below multiplies by these reciprocals (o is 0 or
+        // at least (1 / ln 1e30)^alpha): FP64 division is a long dependent
+        // sequence on this GPU
         rom[k] = o > 0.0 ? 1.0 / o : 0.0;
     }
     __syncthreads();
     if (threadIdx.x < D) {
         const int d = threadIdx.x;
         const double* om = sm + d * nb;
-        const double* rm = rom + d * nb;
-        double* e = edges + static_cast<int64_t>(t) * g.map_stride + d * (nb + 1);
-        if (tot[d] > 0.0) {
-            double otot = 0.0;
-            for (int b = 0; b < nb; ++b) otot += om[b];
-            const double target = otot / nb;
-            // new edges depend on the old ones: collect them, then write
-            double accw = 0.0;
-            int i = 0;
-            double lo_i = e[0], hi_i = e[1];      // old edges of increment i
-            double* ne = newe + d * (nb + 1);
-            for (int k = 1; k < nb; ++k) {
-                const double goal = k * target;
-                while (i < nb - 1 && accw + om[i] < goal) {
-                    accw += om[i];
-                    ++i;
-                    lo_i = e[i];
-                    hi_i = e[i + 1];
-                }
-                double fr = (goal - accw) * rm[i];
-                fr = fr < 0.0 ? 0.0 : (fr > 1.0 ? 1.0 : fr);
-                ne[k] = lo_i + fr * (hi_i - lo_i);
-            }
-            for (int k = 1; k < nb; ++k) e[k] = ne[k];
-            e[0] = 0.0;
-            e[nb] = 1.0;
+        double* c = cum + d * (nb + 1);
+        double acc = 0.0;
+        c[0] = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            acc += om[b];
+            c[b + 1] = acc;
         }
+    }
+    __syncthreads();
+    // new edge k of dimension d: starting from increment 0, step to the next
+    // increment while the running sum after it stays below the goal k T / nb
+    // (and an increment is left); the running sums are non-decreasing, so the
+    // increment reached is the number of j in [1, nb - 1] with cum[j] < goal
+    double* e = edges + static_cast<int64_t>(t) * g.map_stride;
+    for (int q = threadIdx.x; q < D * (nb + 1); q += blockDim.x) {
+        const int d = q / (nb + 1), k = q - d * (nb + 1);
+        if (!(tot[d] > 0.0)) continue;                   // no training data: the map is kept
+        if (k == 0 || k == nb) {
+            e[q] = k == 0 ? 0.0 : 1.0;
+            continue;
+        }
+        const double* c = cum + d * (nb + 1);
+        const double target = c[nb] / nb;
+        const double goal = k * target;
+        int lo = 0, hi = nb - 1;                         // first i in [0, nb - 1] with !(c[i + 1] < goal), else nb - 1
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (c[mid + 1] < goal) lo = mid + 1;
+            else hi = mid;
+        }
+        const int i = lo;
+        double fr = (goal - c[i]) * rom[d * nb + i];
+        fr = fr < 0.0 ? 0.0 : (fr > 1.0 ? 1.0 : fr);
+        const double* oe = olde + d * (nb + 1);
+        e[q] = oe[i] + fr * (oe[i + 1] - oe[i]);
     }
 }
 
