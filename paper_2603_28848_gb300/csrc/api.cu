@@ -20,13 +20,14 @@ __global__ void set_time_kernel(Geometry, TimeState*, const double*, double, int
 __global__ void spline_build_kernel(Geometry, const double*, int, const double*, TimeState*, SpeciesConst*,
                                     double*, double*, float*);
 __global__ void prepare_kernel(Geometry, const SideDesc*, const TaskDesc*, const double*, const double*,
-                               const TimeState*, const double*, TaskConst*, TaskAcc*, int, const double*);
+                               const TimeState*, const double*, TaskConst*, TaskAcc*, int, const double*,
+                               const SpeciesConst*, SegConst32*);
 __global__ void moments_kernel(Geometry, const double*, const double*, const TimeState*, double*, double*);
 __global__ void width_control_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskAcc*, const WidthCtl*,
                                      double*, double*);
 __global__ void refine_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskConst*, const int32_t*,
                               const int32_t*, const Segment*, const double*, double*, TaskAcc*, TaskConst*,
-                              const double*);
+                              const double*, SegConst32*);
 __global__ void strat_init_kernel(const TaskDesc*, int32_t*, uint32_t*, int);
 __global__ void strat_refine_kernel(const TaskDesc*, const int32_t*, const double*, int32_t*, double*, double*,
                                     uint32_t*, double*);
@@ -120,6 +121,7 @@ struct best_ctx {
     SideDesc* d_sides = nullptr;
     TaskDesc* d_tasks = nullptr;
     TaskConst* d_tconst = nullptr;
+    SegConst32* d_tconst32 = nullptr;  // FP32 segment constants per task (FP32 sample kernel)
     TaskAcc* d_acc = nullptr;
     SpeciesConst* d_sconst = nullptr;
     TimeState* d_ts = nullptr;
@@ -238,7 +240,7 @@ void free_all(best_ctx* c) {
         cudaFree(p.d_active); cudaFree(p.d_task_seg); cudaFree(p.d_segs); cudaFree(p.d_cta_seg);
     }
     c->plans.clear();
-    void* bufs[] = {c->d_sides, c->d_tasks, c->d_tconst, c->d_acc, c->d_sconst, c->d_ts, c->d_edges,
+    void* bufs[] = {c->d_sides, c->d_tasks, c->d_tconst, c->d_tconst32, c->d_acc, c->d_sconst, c->d_ts, c->d_edges,
                     c->d_knots, c->d_knots32, c->d_coef64, c->d_coef32, c->d_fgrid, c->d_mass_law,
                     c->d_partials, c->d_k1, c->d_k2, c->d_fstar, c->d_prev, c->d_dtreq,
                     c->d_gcoef, c->d_vjp_tot, c->d_u, c->d_gtail, c->d_coupling, c->d_dcoef64,
@@ -542,7 +544,8 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
         g, src, src_mode, ctx->d_knots, ctx->d_ts, ctx->d_sconst, ctx->d_fgrid, ctx->d_coef64, ctx->d_coef32);
     prepare_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_knots,
                                                             ctx->d_fgrid, ctx->d_ts, ctx->d_prev, ctx->d_tconst,
-                                                            ctx->d_acc, 1, ctx->d_width);
+                                                            ctx->d_acc, 1, ctx->d_width, ctx->d_sconst,
+                                                            ctx->d_tconst32);
     ctx->launches += 2;
     const bool f32 = ctx->precision == BEST_FP32;
     CK(cudaMemsetAsync(ctx->d_chunk_ctr, 0, sizeof(int32_t) * ctx->max_nitn, st));
@@ -554,6 +557,7 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
         P.sides = ctx->d_sides;
         P.tasks = ctx->d_tasks;
         P.tconst = ctx->d_tconst;
+        P.tconst32 = ctx->d_tconst32;
         P.sconst = ctx->d_sconst;
         P.ts = ctx->d_ts;
         P.edges = ctx->d_edges;
@@ -598,7 +602,7 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
         }
         refine_kernel<<<pl.n_active, 128, ctx->refine_smem, st>>>(
             g, ctx->d_sides, ctx->d_tasks, ctx->d_tconst, pl.d_active, pl.d_task_seg, pl.d_segs,
-            ctx->d_partials, ctx->d_edges, ctx->d_acc, ctx->d_tconst, ctx->d_strat_est);
+            ctx->d_partials, ctx->d_edges, ctx->d_acc, ctx->d_tconst, ctx->d_strat_est, ctx->d_tconst32);
         ctx->launches += 2;
     }
     const int total = g.n_species * g.n_grid;
@@ -939,6 +943,7 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     CKI(dalloc(&ctx->d_sides, g.n_side));
     CKI(dalloc(&ctx->d_tasks, T));
     CKI(dalloc(&ctx->d_tconst, T));
+    CKI(dalloc(&ctx->d_tconst32, T));
     CKI(dalloc(&ctx->d_acc, T));
     CKI(dalloc(&ctx->d_chunk_ctr, static_cast<size_t>(ctx->max_nitn) + 1));
     CKI(dalloc(&ctx->d_sconst, S));
@@ -1272,7 +1277,7 @@ best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, con
         g, f_dev, 0, ctx->d_knots, ctx->d_ts, ctx->d_sconst, ctx->d_fgrid, ctx->d_coef64, ctx->d_coef32);
     prepare_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_knots, ctx->d_fgrid,
                                                             ctx->d_ts, ctx->d_prev, ctx->d_tconst, ctx->d_acc, 0,
-                                                            ctx->d_width);
+                                                            ctx->d_width, ctx->d_sconst, ctx->d_tconst32);
     vjp_seed_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_tconst, v_dev,
                                                              ctx->d_u);
     CK(cudaMemsetAsync(ctx->d_gcoef, 0, sizeof(double) * g.n_species * (g.n_grid - 1) * 4, st));
@@ -1283,6 +1288,7 @@ best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, con
     P.sides = ctx->d_sides;
     P.tasks = ctx->d_tasks;
     P.tconst = ctx->d_tconst;
+    P.tconst32 = ctx->d_tconst32;
     P.sconst = ctx->d_sconst;
     P.ts = ctx->d_ts;
     P.edges = ctx->d_edges;
@@ -1375,7 +1381,8 @@ static best_status enqueue_jvp(best_ctx* ctx, const double* f_dev, double t, con
             g, f_dev, 0, ctx->d_knots, ctx->d_ts, ctx->d_sconst, ctx->d_fgrid, ctx->d_coef64, ctx->d_coef32);
         prepare_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_knots,
                                                                 ctx->d_fgrid, ctx->d_ts, ctx->d_prev, ctx->d_tconst,
-                                                                ctx->d_acc, 0, ctx->d_width);
+                                                                ctx->d_acc, 0, ctx->d_width, ctx->d_sconst,
+                                                                ctx->d_tconst32);
         ctx->launches += 3;
     }
     jvp_seed_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_tconst,
@@ -1390,6 +1397,7 @@ static best_status enqueue_jvp(best_ctx* ctx, const double* f_dev, double t, con
     P.sides = ctx->d_sides;
     P.tasks = ctx->d_tasks;
     P.tconst = ctx->d_tconst;
+    P.tconst32 = ctx->d_tconst32;
     P.sconst = ctx->d_sconst;
     P.ts = ctx->d_ts;
     P.edges = ctx->d_edges;

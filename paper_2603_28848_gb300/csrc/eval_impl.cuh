@@ -486,6 +486,56 @@ __device__ __forceinline__ void seg_setup(const EvalParams& P, const SideDesc& s
     out->inv_step = static_cast<R>(g.inv_step);
 }
 
+// The same for the FP32 kernel from the task's SegConst32 (rounded once per
+// sweep by the prepare kernel): loads only.
+template <int NLEG>
+__device__ __forceinline__ void seg_setup32(const SegConst32& S, SegSetup<float, NLEG>* out) {
+    constexpr int NI = NLEG - 2;
+    SegConst<float, NLEG> C;
+    C.pobs_sig = S.pobs_sig;
+    C.sgn_obs_E = S.sgn_obs_E;
+#pragma unroll
+    for (int j = 0; j < NI; ++j) {
+        C.sig[j] = S.sig[j];
+        C.sgnE[j] = S.sgnE[j];
+        C.m2[j] = S.m2[j];
+        C.ca[j] = S.ca[j];
+        C.cb[j] = S.cb[j];
+        C.spc[j] = S.spc[j];
+        C.fd[j] = S.fd[j];
+        C.inw[j] = S.inw[j];
+    }
+    C.sgn_cons = S.sgn_cons;
+    C.m2c = S.m2c;
+    C.cac = S.cac;
+    C.cbc = S.cbc;
+    C.sp_cons = S.sp_cons;
+    C.eta_c = S.eta_c;
+    C.fd_c = S.fd_c;
+    C.tlo_a = S.tlo_a;
+    C.tlo_b = S.tlo_b;
+    C.thi_a = S.thi_a;
+    C.thi_b = S.thi_b;
+    C.a = S.a;
+    C.inv_a = S.inv_a;
+    C.c0 = S.c0;
+    C.frac = S.frac != 0;
+    C.gauss_k = S.gauss_k;
+    C.e_obs = S.e_obs;
+    C.me_on = S.me_on != 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) C.me[k] = S.me[k];
+    C.obs_in_p = S.obs_in_p;
+    C.obs_in_E = S.obs_in_E;
+    C.cons_inw = S.cons_inw;
+    C.e_cut = S.e_cut;
+    out->C = C;
+    out->q0 = S.q0;
+    out->lq0_step = S.lq0_step;
+    out->qN = S.qN;
+    out->inv_step = S.inv_step;
+}
+
 // STRAT: the instantiation also handles stratified tasks and s-dependent
 // matrix elements (kept apart so that the plain kernel's register allocation
 // is not affected).
@@ -531,7 +581,8 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
 
     // ---- per-segment constants ----------------------------------------------
     SegSetup<R, NLEG> setup;
-    seg_setup<R, NLEG>(P, sd, td, tc, &setup);
+    if constexpr (F32) seg_setup32<NLEG>(P.tconst32[seg.task], &setup);
+    else seg_setup<R, NLEG>(P, sd, td, tc, &setup);
     const R nbR = static_cast<R>(nb);
     const int ncoef = 4 * (g.n_grid - 1);
     const R* knots = s_spline + g.n_species * ncoef;

@@ -93,6 +93,25 @@ struct TaskConst {
     double inv_E_obs;       // 1 / E_obs
 };
 
+// FP32 constants of one task's segment set-up in the FP32 sample kernel,
+// rounded once per sweep from the FP64 values (seg_const32, in the prepare
+// kernel; c0 again when the refinement rescales the task), so that the
+// sample kernel's threads only load them: FP64 arithmetic and conversions
+// run at a small fraction of the FP32 rate.  Leg arrays hold the
+// integrated legs in dimension order (entries past n - 2 unused).
+struct SegConst32 {
+    float pobs_sig, sgn_obs_E, sgn_cons, m2c, cac, cbc;
+    float inv_a, a, c0, gauss_k, e_obs;
+    float cons_inw, obs_in_p, obs_in_E, e_cut, eta_c;
+    float tlo_a, tlo_b, thi_a, thi_b;
+    float q0, lq0_step, qN, inv_step;
+    float me[4];
+    float sig[kMaxLegs - 2], sgnE[kMaxLegs - 2], m2[kMaxLegs - 2], ca[kMaxLegs - 2], cb[kMaxLegs - 2],
+        inw[kMaxLegs - 2];
+    int32_t spc[kMaxLegs - 2], fd[kMaxLegs - 2];
+    int32_t sp_cons, fd_c, frac, me_on;
+};
+
 // Mass law of one species: m(t) = m0 + m1 t, or with n >= 2 knots the
 // piecewise-linear interpolation of (t[k], m[k]) (t increasing), constant
 // beyond the first and last knot.
@@ -180,12 +199,89 @@ struct Geometry {
     double lq0_step;        // log grid: log2(q_min) * inv_step
 };
 
+// The FP32 segment constants of task td (side sd, constants tc) at the
+// sweep's time state: the roles and signs of the legs (App. A), masses,
+// statistical-factor coefficients of Eq. (5), the Gaussian's exponent
+// factor of Eq. (11), the conserved leg's Eq. (13) end fits and the spline
+// index constants, each rounded to FP32 from FP64 exactly as the sample
+// kernel needs them.
+__device__ inline SegConst32 seg_const32(const SideDesc& sd, const TaskDesc& td, const TaskConst& tc,
+                                         const TimeState& ts, const SpeciesConst* sconst, const Geometry& g) {
+    SegConst32 C{};
+    const int NI = sd.n - 2;
+    const int cons = sd.cons;
+    const bool cons_in = (sd.in_mask >> cons) & 1;
+    const float flip = cons_in ? -1.0f : 1.0f;     // p_cons = flip * sum_{k != c} s_k p_k
+    const bool is_loss = td.term == 1;
+    {
+        const float s_obs = ((sd.in_mask >> sd.obs) & 1) ? 1.0f : -1.0f;
+        C.pobs_sig = flip * s_obs * static_cast<float>(tc.p_obs);
+        C.sgn_obs_E = s_obs * static_cast<float>(tc.E_obs);
+    }
+    for (int j = 0; j < NI; ++j) {
+        const int k = sd.integ[j];
+        const bool kin = (sd.in_mask >> k) & 1;
+        const bool own = (sd.own_mask >> k) & 1;
+        const int sp = sd.leg_species[k];
+        const double eta = sconst[sp].eta;
+        C.sig[j] = flip * (kin ? 1.0f : -1.0f);
+        C.sgnE[j] = kin ? 1.0f : -1.0f;
+        const double m = ts.mass[sp];
+        C.m2[j] = static_cast<float>(m * m);
+        const bool enh = own != is_loss;
+        C.ca[j] = enh ? 1.0f : 0.0f;
+        C.cb[j] = enh ? static_cast<float>(eta) : 1.0f;
+        C.spc[j] = sp;
+        C.fd[j] = sconst[sp].stat == BEST_FD;
+        C.inw[j] = ((sd.in_mask >> sd.integ[j]) & 1) ? 1.0f : 0.0f;
+    }
+    {
+        const int sp = sd.leg_species[cons];
+        const bool own = (sd.own_mask >> cons) & 1;
+        const double eta = sconst[sp].eta;
+        const double m = ts.mass[sp];
+        C.sgn_cons = cons_in ? 1.0f : -1.0f;
+        C.m2c = static_cast<float>(m * m);
+        const bool enh = own != is_loss;
+        C.cac = enh ? 1.0f : 0.0f;
+        C.cbc = enh ? static_cast<float>(eta) : 1.0f;
+        C.sp_cons = sp;
+        C.eta_c = static_cast<float>(eta);
+        C.fd_c = sconst[sp].stat == BEST_FD;
+        C.tlo_a = static_cast<float>(sconst[sp].tail_lo_a);
+        C.tlo_b = static_cast<float>(sconst[sp].tail_lo_b);
+        C.thi_a = static_cast<float>(sconst[sp].tail_hi_a);
+        C.thi_b = static_cast<float>(sconst[sp].tail_hi_b);
+    }
+    C.a = static_cast<float>(ts.a);
+    C.inv_a = static_cast<float>(ts.inv_a);
+    C.c0 = static_cast<float>(tc.c0);
+    C.frac = tc.wfrac > 0.0;
+    C.gauss_k = static_cast<float>(tc.gauss_k);
+    C.e_obs = static_cast<float>(tc.E_obs);
+    C.me_on = sd.me_on != 0;
+    for (int k = 0; k < 4; ++k) C.me[k] = static_cast<float>(sd.me_coef[k]);
+    {
+        const bool obs_in = (sd.in_mask >> sd.obs) & 1;
+        C.obs_in_p = obs_in ? static_cast<float>(tc.p_obs) : 0.0f;
+        C.obs_in_E = obs_in ? static_cast<float>(tc.E_obs) : 0.0f;
+        C.cons_inw = cons_in ? 1.0f : 0.0f;
+    }
+    C.e_cut = static_cast<float>(g.e_cut);
+    C.q0 = static_cast<float>(g.q_min);
+    C.lq0_step = static_cast<float>(g.lq0_step);
+    C.qN = static_cast<float>(g.q_max);
+    C.inv_step = static_cast<float>(g.inv_step);
+    return C;
+}
+
 // Arguments of the sample kernel.
 struct EvalParams {
     Geometry geo;
     const SideDesc* sides;
     const TaskDesc* tasks;
     const TaskConst* tconst;
+    const SegConst32* tconst32; // FP32 segment constants per task (FP32 sample kernel)
     const SpeciesConst* sconst;
     const TimeState* ts;
     const double* edges;        // [task][map_stride]

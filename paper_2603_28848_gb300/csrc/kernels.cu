@@ -229,7 +229,8 @@ __global__ void prepare_kernel(Geometry g, const SideDesc* __restrict__ sides,
                                const TaskDesc* __restrict__ tasks, const double* __restrict__ knots,
                                const double* __restrict__ fgrid, const TimeState* ts,
                                const double* __restrict__ prev, TaskConst* tconst, TaskAcc* acc, int reset_acc,
-                               const double* __restrict__ width) {
+                               const double* __restrict__ width, const SpeciesConst* __restrict__ sconst,
+                               SegConst32* tconst32) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.n_tasks) return;
     const TaskDesc td = tasks[t];
@@ -264,6 +265,7 @@ __global__ void prepare_kernel(Geometry g, const SideDesc* __restrict__ sides,
     c.four_over_w2 = c.wfrac > 0.0 ? 4.0 / (c.wfrac * c.wfrac) : 0.0;
     c.inv_E_obs = 1.0 / E;
     tconst[t] = c;
+    if (tconst32) tconst32[t] = seg_const32(sd, td, c, *ts, sconst, g);
     if (!reset_acc) return;
     TaskAcc z;
     z.sum_inv_var = 0.0; z.sum_mean_inv_var = 0.0; z.sum_exact = 0.0; z.n_exact = 0.0;
@@ -507,7 +509,7 @@ __global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
                               const int32_t* __restrict__ active, const int32_t* __restrict__ task_seg,
                               const Segment* __restrict__ segs, const double* __restrict__ partials,
                               double* edges, TaskAcc* acc, TaskConst* tconst_next,
-                              const double* __restrict__ strat_est) {
+                              const double* __restrict__ strat_est, SegConst32* tconst32) {
     extern __shared__ double hist[];
     const int t = active[blockIdx.x];
     const TaskDesc td = tasks[t];
@@ -568,6 +570,7 @@ __global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
             const double scale = clamp_scale(fabs(mean_n) * c.scale, c.obs_factor);
             tconst_next[t].scale = scale;
             tconst_next[t].c0 = c.c0 == 0.0 ? 0.0 : c.obs_factor / scale;   // a cut observed leg stays cut
+            if (tconst32) tconst32[t].c0 = static_cast<float>(tconst_next[t].c0);
         }
     }
     if (underflow) return;

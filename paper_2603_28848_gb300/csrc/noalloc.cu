@@ -20,7 +20,8 @@ namespace best {
 __global__ void spline_build_kernel(Geometry, const double*, int, const double*, TimeState*, SpeciesConst*,
                                     double*, double*, float*);
 __global__ void prepare_kernel(Geometry, const SideDesc*, const TaskDesc*, const double*, const double*,
-                               const TimeState*, const double*, TaskConst*, TaskAcc*, int, const double*);
+                               const TimeState*, const double*, TaskConst*, TaskAcc*, int, const double*,
+                               const SpeciesConst*, SegConst32*);
 void* eval_kernel_ptr_f32(int nmax);
 void* eval_kernel_ptr_f64(int nmax);
 best_status check_config(const best_config* cfg);
@@ -47,7 +48,8 @@ constexpr size_t kOffSc = up(kOffTs + sizeof(TimeState));
 constexpr size_t kOffSide = up(kOffSc + sizeof(SpeciesConst) * BEST_MAX_SPECIES);
 constexpr size_t kOffTask = up(kOffSide + sizeof(SideDesc));
 constexpr size_t kOffTconst = up(kOffTask + sizeof(TaskDesc));
-constexpr size_t kOffAcc = up(kOffTconst + sizeof(TaskConst));
+constexpr size_t kOffTc32 = up(kOffTconst + sizeof(TaskConst));
+constexpr size_t kOffAcc = up(kOffTc32 + sizeof(SegConst32));
 constexpr size_t kOffPrev = up(kOffAcc + sizeof(TaskAcc));
 constexpr size_t kOffKnots = up(kOffPrev + sizeof(double));
 constexpr size_t kOffKnots32 = up(kOffKnots + sizeof(double) * kMaxGrid);
@@ -266,6 +268,7 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     SideDesc* dsd = reinterpret_cast<SideDesc*>(base + kOffSide);
     TaskDesc* dtd = reinterpret_cast<TaskDesc*>(base + kOffTask);
     TaskConst* dtc = reinterpret_cast<TaskConst*>(base + kOffTconst);
+    SegConst32* dtc32 = reinterpret_cast<SegConst32*>(base + kOffTc32);
     TaskAcc* dacc = reinterpret_cast<TaskAcc*>(base + kOffAcc);
     double* prev = reinterpret_cast<double*>(base + kOffPrev);
     double* knots = reinterpret_cast<double*>(base + kOffKnots);
@@ -277,7 +280,7 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     noalloc_setup_kernel<<<1, 512, 0, st>>>(A, base);
     const size_t spline_smem = 5 * sizeof(double) * n;
     spline_build_kernel<<<S, 256, spline_smem, st>>>(g, f_dev, 0, knots, ts, sc, fgrid, coef64, coef32);
-    prepare_kernel<<<1, 32, 0, st>>>(g, dsd, dtd, knots, fgrid, ts, prev, dtc, dacc, 1, nullptr);
+    prepare_kernel<<<1, 32, 0, st>>>(g, dsd, dtd, knots, fgrid, ts, prev, dtc, dacc, 1, nullptr, sc, dtc32);
 
     // The sample kernel indexes its descriptor arrays and the map by the
     // segment's task index (0 here: the scratch arrays and the caller's map
@@ -288,6 +291,7 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     P.sides = dsd;
     P.tasks = dtd;
     P.tconst = dtc;
+    P.tconst32 = dtc32;
     P.sconst = sc;
     P.ts = ts;
     P.edges = edges_dev;
