@@ -892,9 +892,11 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
         part[1] = a1;
     }
     for (int k = tid; k < D * nb; k += blockDim.x) {
-        double v = 0.0;
-        for (int w = 0; w < nwarps; ++w) v += static_cast<double>(s_hist[w * map_elems + k]);
-        part[2 + k] = v;
+        // the per-warp histograms summed in their own precision (FP32 for
+        // the FP32 kernel: one conversion per entry instead of one per warp)
+        R v = R(0);
+        for (int w = 0; w < nwarps; ++w) v += s_hist[w * map_elems + k];
+        part[2 + k] = static_cast<double>(v);
     }
     __syncthreads();
 }
