@@ -105,11 +105,12 @@ struct SegConst32 {
     float cons_inw, obs_in_p, obs_in_E, e_cut, eta_c;
     float tlo_a, tlo_b, thi_a, thi_b;
     float q0, lq0_step, qN, inv_step;
+    float mass_c, inv_sig2_abs, four_over_w2, inv_E_obs, obs_inw;   // (adjoint and tangent kernels)
     float me[4];
     float sig[kMaxLegs - 2], sgnE[kMaxLegs - 2], m2[kMaxLegs - 2], ca[kMaxLegs - 2], cb[kMaxLegs - 2],
-        inw[kMaxLegs - 2];
+        inw[kMaxLegs - 2], mass[kMaxLegs - 2];
     int32_t spc[kMaxLegs - 2], fd[kMaxLegs - 2];
-    int32_t sp_cons, fd_c, frac, me_on;
+    int32_t sp_cons, fd_c, frac, me_on, obs_cut;
 };
 
 // Mass law of one species: m(t) = m0 + m1 t, or with n >= 2 knots the
@@ -228,6 +229,7 @@ __device__ inline SegConst32 seg_const32(const SideDesc& sd, const TaskDesc& td,
         C.sgnE[j] = kin ? 1.0f : -1.0f;
         const double m = ts.mass[sp];
         C.m2[j] = static_cast<float>(m * m);
+        C.mass[j] = static_cast<float>(m);
         const bool enh = own != is_loss;
         C.ca[j] = enh ? 1.0f : 0.0f;
         C.cb[j] = enh ? static_cast<float>(eta) : 1.0f;
@@ -242,6 +244,7 @@ __device__ inline SegConst32 seg_const32(const SideDesc& sd, const TaskDesc& td,
         const double m = ts.mass[sp];
         C.sgn_cons = cons_in ? 1.0f : -1.0f;
         C.m2c = static_cast<float>(m * m);
+        C.mass_c = static_cast<float>(m);
         const bool enh = own != is_loss;
         C.cac = enh ? 1.0f : 0.0f;
         C.cbc = enh ? static_cast<float>(eta) : 1.0f;
@@ -266,7 +269,12 @@ __device__ inline SegConst32 seg_const32(const SideDesc& sd, const TaskDesc& td,
         C.obs_in_p = obs_in ? static_cast<float>(tc.p_obs) : 0.0f;
         C.obs_in_E = obs_in ? static_cast<float>(tc.E_obs) : 0.0f;
         C.cons_inw = cons_in ? 1.0f : 0.0f;
+        C.obs_inw = obs_in ? 1.0f : 0.0f;
     }
+    C.obs_cut = tc.E_obs < g.e_cut;
+    C.inv_sig2_abs = static_cast<float>(tc.inv_sig2_abs);
+    C.four_over_w2 = static_cast<float>(tc.four_over_w2);
+    C.inv_E_obs = static_cast<float>(tc.inv_E_obs);
     C.e_cut = static_cast<float>(g.e_cut);
     C.q0 = static_cast<float>(g.q_min);
     C.lq0_step = static_cast<float>(g.lq0_step);

@@ -101,75 +101,90 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
         s_map[k] = v;
     }
 
-    // per-segment constants (as in the sample kernel)
+    // per-segment constants (as in the sample kernel; the FP32 kernel loads
+    // them from the task's SegConst32, rounded once per sweep)
     const TimeState& ts = *P.ts;
+    const SegConst32* S = F32 ? P.tconst32 + seg.task : nullptr;
     const int cons = sd.cons;
     const bool cons_in = (sd.in_mask >> cons) & 1;
     const R flip = cons_in ? R(-1) : R(1);
     const bool is_loss = td.term == 1;
     const R s_obs = ((sd.in_mask >> sd.obs) & 1) ? R(1) : R(-1);
-    const R pobs_sig = flip * s_obs * static_cast<R>(tc.p_obs);
-    const R sgn_obs_E = s_obs * static_cast<R>(tc.E_obs);
+    const R pobs_sig = F32 ? R(S->pobs_sig) : flip * s_obs * static_cast<R>(tc.p_obs);
+    const R sgn_obs_E = F32 ? R(S->sgn_obs_E) : s_obs * static_cast<R>(tc.E_obs);
     R sig[NI], sgnE[NI], m2[NI], ca[NI], cb[NI], mass[NI];
     int spc[NI], fdj[NI];
 #pragma unroll
     for (int j = 0; j < NI; ++j) {
-        const int k = sd.integ[j];
-        const bool kin = (sd.in_mask >> k) & 1;
-        const bool own = (sd.own_mask >> k) & 1;
-        const int sp = sd.leg_species[k];
-        const double eta = P.sconst[sp].eta;
-        sig[j] = flip * (kin ? R(1) : R(-1));
-        sgnE[j] = kin ? R(1) : R(-1);
-        const double m = ts.mass[sp];
-        mass[j] = static_cast<R>(m);
-        m2[j] = static_cast<R>(m * m);
-        const bool enh = own != is_loss;
-        ca[j] = enh ? R(1) : R(0);
-        cb[j] = enh ? static_cast<R>(eta) : R(1);
-        spc[j] = sp;
-        fdj[j] = P.sconst[sp].stat == BEST_FD;
+        if constexpr (F32) {
+            sig[j] = S->sig[j];
+            sgnE[j] = S->sgnE[j];
+            mass[j] = S->mass[j];
+            m2[j] = S->m2[j];
+            ca[j] = S->ca[j];
+            cb[j] = S->cb[j];
+            spc[j] = S->spc[j];
+            fdj[j] = S->fd[j];
+        } else {
+            const int k = sd.integ[j];
+            const bool kin = (sd.in_mask >> k) & 1;
+            const bool own = (sd.own_mask >> k) & 1;
+            const int sp = sd.leg_species[k];
+            const double eta = P.sconst[sp].eta;
+            sig[j] = flip * (kin ? R(1) : R(-1));
+            sgnE[j] = kin ? R(1) : R(-1);
+            const double m = ts.mass[sp];
+            mass[j] = static_cast<R>(m);
+            m2[j] = static_cast<R>(m * m);
+            const bool enh = own != is_loss;
+            ca[j] = enh ? R(1) : R(0);
+            cb[j] = enh ? static_cast<R>(eta) : R(1);
+            spc[j] = sp;
+            fdj[j] = P.sconst[sp].stat == BEST_FD;
+        }
     }
     const int spcn = sd.leg_species[cons];
-    const double eta_cd = P.sconst[spcn].eta;
-    const R eta_c = static_cast<R>(eta_cd);
-    const bool fd_c = P.sconst[spcn].stat == BEST_FD;
+    const R eta_c = F32 ? R(S->eta_c) : static_cast<R>(P.sconst[spcn].eta);
+    const bool fd_c = F32 ? S->fd_c != 0 : P.sconst[spcn].stat == BEST_FD;
     const R sgn_cons = cons_in ? R(1) : R(-1);
-    const R mass_c = static_cast<R>(ts.mass[spcn]);
+    const R mass_c = F32 ? R(S->mass_c) : static_cast<R>(ts.mass[spcn]);
     const R m2c = mass_c * mass_c;
     const bool own_c = (sd.own_mask >> cons) & 1;
     const bool enh_c = own_c != is_loss;
     const R cac = enh_c ? R(1) : R(0);
     const R cbc = enh_c ? eta_c : R(1);
-    const R tlo_a = static_cast<R>(P.sconst[spcn].tail_lo_a), tlo_b = static_cast<R>(P.sconst[spcn].tail_lo_b);
-    const R thi_a = static_cast<R>(P.sconst[spcn].tail_hi_a), thi_b = static_cast<R>(P.sconst[spcn].tail_hi_b);
+    const R tlo_a = F32 ? R(S->tlo_a) : static_cast<R>(P.sconst[spcn].tail_lo_a);
+    const R tlo_b = F32 ? R(S->tlo_b) : static_cast<R>(P.sconst[spcn].tail_lo_b);
+    const R thi_a = F32 ? R(S->thi_a) : static_cast<R>(P.sconst[spcn].tail_hi_a);
+    const R thi_b = F32 ? R(S->thi_b) : static_cast<R>(P.sconst[spcn].tail_hi_b);
     // (the FP64 quotients below come from the time-state and prepare kernels,
     // once per sweep: FP64 division runs at a small fraction of the FP32 rate)
-    const R a = static_cast<R>(ts.a), inv_a = static_cast<R>(ts.inv_a);
-    const bool obs_cut = tc.E_obs < g.e_cut;       // every sample of the task is cut
-    const R c0 = static_cast<R>(tc.c0);
+    const R a = F32 ? R(S->a) : static_cast<R>(ts.a);
+    const R inv_a = F32 ? R(S->inv_a) : static_cast<R>(ts.inv_a);
+    const bool obs_cut = F32 ? S->obs_cut != 0 : tc.E_obs < g.e_cut;   // every sample of the task is cut
+    const R c0 = F32 ? R(S->c0) : static_cast<R>(tc.c0);
     // Gaussian of Eq. (11); fractional width (App. C): sigma = w S / 2 per
     // sample, S = E_in + E_out, with sigma_ref = w E_obs inside K
     const bool frac = tc.wfrac > 0.0;
-    const R gauss_k = static_cast<R>(tc.gauss_k);
-    const R inv_sig2_abs = static_cast<R>(tc.inv_sig2_abs);
-    const R four_over_w2 = static_cast<R>(tc.four_over_w2);
-    const R e_obs = static_cast<R>(tc.E_obs);
+    const R gauss_k = F32 ? R(S->gauss_k) : static_cast<R>(tc.gauss_k);
+    const R inv_sig2_abs = F32 ? R(S->inv_sig2_abs) : static_cast<R>(tc.inv_sig2_abs);
+    const R four_over_w2 = F32 ? R(S->four_over_w2) : static_cast<R>(tc.four_over_w2);
+    const R e_obs = F32 ? R(S->e_obs) : static_cast<R>(tc.E_obs);
     // |M|^2 / coupling^2 = P(s), s of the initial state
     const bool me_on = ME && sd.me_on != 0;
     R mec[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) mec[k] = static_cast<R>(sd.me_coef[k]);
+    for (int k = 0; k < 4; ++k) mec[k] = F32 ? R(S->me[k]) : static_cast<R>(sd.me_coef[k]);
     const bool obs_in = (sd.in_mask >> sd.obs) & 1;
-    const R obs_in_p = obs_in ? static_cast<R>(tc.p_obs) : R(0);
-    const R obs_in_E = obs_in ? static_cast<R>(tc.E_obs) : R(0);
+    const R obs_in_p = F32 ? R(S->obs_in_p) : (obs_in ? static_cast<R>(tc.p_obs) : R(0));
+    const R obs_in_E = F32 ? R(S->obs_in_E) : (obs_in ? static_cast<R>(tc.E_obs) : R(0));
     const R obs_inw = obs_in ? R(1) : R(0);
     const R cons_inw = cons_in ? R(1) : R(0);
     R inw[NI];
 #pragma unroll
     for (int j = 0; j < NI; ++j) inw[j] = ((sd.in_mask >> sd.integ[j]) & 1) ? R(1) : R(0);
-    const R e_cut = static_cast<R>(g.e_cut);
-    const R inv_Eobs = static_cast<R>(tc.inv_E_obs);
+    const R e_cut = F32 ? R(S->e_cut) : static_cast<R>(g.e_cut);
+    const R inv_Eobs = F32 ? R(S->inv_E_obs) : static_cast<R>(tc.inv_E_obs);
     const R U = static_cast<R>(V.task_u[seg.task]);     // VJP: adjoint seed; JVP: obs tangent factor
     R dta_lo = R(0), dtb_lo = R(0), dta_hi = R(0), dtb_hi = R(0);
     if constexpr (JVP) {
@@ -179,9 +194,9 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
         dtb_hi = static_cast<R>(V.dtail[spcn * 4 + 3]);
     }
     const R nbR = static_cast<R>(nb);
-    const R q0 = static_cast<R>(g.q_min), qN = static_cast<R>(g.q_max);
-    const R lq0_step = static_cast<R>(g.lq0_step);
-    const R inv_step = static_cast<R>(g.inv_step);
+    const R q0 = F32 ? R(S->q0) : static_cast<R>(g.q_min), qN = F32 ? R(S->qN) : static_cast<R>(g.q_max);
+    const R lq0_step = F32 ? R(S->lq0_step) : static_cast<R>(g.lq0_step);
+    const R inv_step = F32 ? R(S->inv_step) : static_cast<R>(g.inv_step);
     const int ncoef = 4 * (g.n_grid - 1);
     const R* knots = s_spline + g.n_species * ncoef;
     __syncthreads();
