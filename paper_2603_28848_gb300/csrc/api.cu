@@ -27,7 +27,8 @@ __global__ void width_control_kernel(Geometry, const SideDesc*, const TaskDesc*,
                                      double*, double*);
 __global__ void refine_kernel(Geometry, const SideDesc*, const TaskDesc*, const TaskConst*, const int32_t*,
                               const int32_t*, const Segment*, const double*, double*, TaskAcc*, TaskConst*,
-                              const double*, SegConst32*);
+                              const double*, SegConst32*, float2*);
+__global__ void map32_kernel(Geometry, const TaskDesc*, int, const double*, float2*);
 __global__ void strat_init_kernel(const TaskDesc*, int32_t*, uint32_t*, int);
 __global__ void strat_refine_kernel(const TaskDesc*, const int32_t*, const double*, int32_t*, double*, double*,
                                     uint32_t*, double*);
@@ -122,6 +123,7 @@ struct best_ctx {
     TaskDesc* d_tasks = nullptr;
     TaskConst* d_tconst = nullptr;
     SegConst32* d_tconst32 = nullptr;  // FP32 segment constants per task (FP32 sample kernel)
+    float2* d_map32 = nullptr;      // FP32 kernels' map tables [task][map32_stride] (FP32 contexts)
     TaskAcc* d_acc = nullptr;
     SpeciesConst* d_sconst = nullptr;
     TimeState* d_ts = nullptr;
@@ -240,7 +242,7 @@ void free_all(best_ctx* c) {
         cudaFree(p.d_active); cudaFree(p.d_task_seg); cudaFree(p.d_segs); cudaFree(p.d_cta_seg);
     }
     c->plans.clear();
-    void* bufs[] = {c->d_sides, c->d_tasks, c->d_tconst, c->d_tconst32, c->d_acc, c->d_sconst, c->d_ts, c->d_edges,
+    void* bufs[] = {c->d_sides, c->d_tasks, c->d_tconst, c->d_tconst32, c->d_map32, c->d_acc, c->d_sconst, c->d_ts, c->d_edges,
                     c->d_knots, c->d_knots32, c->d_coef64, c->d_coef32, c->d_fgrid, c->d_mass_law,
                     c->d_partials, c->d_k1, c->d_k2, c->d_fstar, c->d_prev, c->d_dtreq,
                     c->d_gcoef, c->d_vjp_tot, c->d_u, c->d_gtail, c->d_coupling, c->d_dcoef64,
@@ -547,6 +549,10 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
                                                             ctx->d_acc, 1, ctx->d_width, ctx->d_sconst,
                                                             ctx->d_tconst32);
     ctx->launches += 2;
+    if (ctx->d_map32) {
+        map32_kernel<<<2 * 152, 256, 0, st>>>(g, ctx->d_tasks, g.n_tasks, ctx->d_edges, ctx->d_map32);
+        ctx->launches += 1;
+    }
     const bool f32 = ctx->precision == BEST_FP32;
     CK(cudaMemsetAsync(ctx->d_chunk_ctr, 0, sizeof(int32_t) * ctx->max_nitn, st));
     for (int it = 0; it < ctx->max_nitn; ++it) {
@@ -561,6 +567,7 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
         P.sconst = ctx->d_sconst;
         P.ts = ctx->d_ts;
         P.edges = ctx->d_edges;
+        P.map32 = ctx->d_map32;
         P.segs = pl.d_segs;
         P.cta_seg = pl.d_cta_seg;
         P.n_chunks = ctx->n_chunks;
@@ -602,7 +609,8 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
         }
         refine_kernel<<<pl.n_active, 128, ctx->refine_smem, st>>>(
             g, ctx->d_sides, ctx->d_tasks, ctx->d_tconst, pl.d_active, pl.d_task_seg, pl.d_segs,
-            ctx->d_partials, ctx->d_edges, ctx->d_acc, ctx->d_tconst, ctx->d_strat_est, ctx->d_tconst32);
+            ctx->d_partials, ctx->d_edges, ctx->d_acc, ctx->d_tconst, ctx->d_strat_est, ctx->d_tconst32,
+            ctx->d_map32);
         ctx->launches += 2;
     }
     const int total = g.n_species * g.n_grid;
@@ -944,6 +952,7 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
     CKI(dalloc(&ctx->d_tasks, T));
     CKI(dalloc(&ctx->d_tconst, T));
     CKI(dalloc(&ctx->d_tconst32, T));
+    if (ctx->precision == BEST_FP32) CKI(dalloc(&ctx->d_map32, static_cast<size_t>(T) * map32_stride(g)));
     CKI(dalloc(&ctx->d_acc, T));
     CKI(dalloc(&ctx->d_chunk_ctr, static_cast<size_t>(ctx->max_nitn) + 1));
     CKI(dalloc(&ctx->d_sconst, S));
@@ -1278,6 +1287,8 @@ best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, con
     prepare_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_knots, ctx->d_fgrid,
                                                             ctx->d_ts, ctx->d_prev, ctx->d_tconst, ctx->d_acc, 0,
                                                             ctx->d_width, ctx->d_sconst, ctx->d_tconst32);
+    if (ctx->d_map32)
+        map32_kernel<<<2 * 152, 256, 0, st>>>(g, ctx->d_tasks, g.n_tasks, ctx->d_edges, ctx->d_map32);
     vjp_seed_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_tconst, v_dev,
                                                              ctx->d_u);
     CK(cudaMemsetAsync(ctx->d_gcoef, 0, sizeof(double) * g.n_species * (g.n_grid - 1) * 4, st));
@@ -1292,6 +1303,7 @@ best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, con
     P.sconst = ctx->d_sconst;
     P.ts = ctx->d_ts;
     P.edges = ctx->d_edges;
+    P.map32 = ctx->d_map32;
     P.segs = pl.d_segs;
     P.cta_seg = pl.d_cta_seg;
     P.n_chunks = ctx->n_chunks;
@@ -1320,7 +1332,7 @@ best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, con
     spline_adjoint_kernel<<<g.n_species, 32, ctx->spline_smem, st>>>(g, ctx->d_knots, ctx->d_fgrid, ctx->d_sconst,
                                                                      ctx->d_ts, ctx->d_gcoef, ctx->d_gtail, gf_dev,
                                                                      gm_dev);
-    ctx->launches = 9;
+    ctx->launches = ctx->d_map32 ? 10 : 9;
     CK(cudaGetLastError());
     return BEST_OK;
 }
@@ -1383,6 +1395,10 @@ static best_status enqueue_jvp(best_ctx* ctx, const double* f_dev, double t, con
                                                                 ctx->d_fgrid, ctx->d_ts, ctx->d_prev, ctx->d_tconst,
                                                                 ctx->d_acc, 0, ctx->d_width, ctx->d_sconst,
                                                                 ctx->d_tconst32);
+        if (ctx->d_map32) {
+            map32_kernel<<<2 * 152, 256, 0, st>>>(g, ctx->d_tasks, g.n_tasks, ctx->d_edges, ctx->d_map32);
+            ctx->launches += 1;
+        }
         ctx->launches += 3;
     }
     jvp_seed_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_tconst,
@@ -1401,6 +1417,7 @@ static best_status enqueue_jvp(best_ctx* ctx, const double* f_dev, double t, con
     P.sconst = ctx->d_sconst;
     P.ts = ctx->d_ts;
     P.edges = ctx->d_edges;
+    P.map32 = ctx->d_map32;
     P.segs = pl.d_segs;
     P.cta_seg = pl.d_cta_seg;
     P.n_chunks = ctx->n_chunks;

@@ -554,22 +554,34 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
     const int tid = threadIdx.x;
 
     // ---- map table of this task in shared memory ---------------------------
-    const double* edges = P.edges + static_cast<int64_t>(seg.task) * g.map_stride;
-    for (int k = tid; k < D * nb; k += blockDim.x) {
-        const int d = k / nb;
-        const int b = k - d * nb;
-        const double e0 = edges[d * (nb + 1) + b];
-        const double e1 = edges[d * (nb + 1) + b + 1];
-        double lo, sc;
-        switch (d % 3) {
-            case 0: lo = g.q_min; sc = g.q_max - g.q_min; break;   // r (comoving)
-            case 1: lo = 0.0; sc = kPi; break;                     // theta
-            default: lo = -kPi; sc = kTwoPi; break;                // phi - pi
+    if constexpr (F32) {
+        // rounded to FP32 once per refinement (map32_kernel, refine_kernel)
+        const float2* m32 = P.map32 + static_cast<int64_t>(seg.task) * map32_stride(g);
+        for (int k = tid; k < D * nb; k += blockDim.x) {
+            const float2 m = m32[k];
+            Real2<R> v;
+            v.y0 = m.x;
+            v.dy = m.y;
+            s_map[k] = v;
         }
-        Real2<R> v;
-        v.y0 = static_cast<R>(lo + sc * e0);
-        v.dy = static_cast<R>(sc * (e1 - e0));
-        s_map[k] = v;
+    } else {
+        const double* edges = P.edges + static_cast<int64_t>(seg.task) * g.map_stride;
+        for (int k = tid; k < D * nb; k += blockDim.x) {
+            const int d = k / nb;
+            const int b = k - d * nb;
+            const double e0 = edges[d * (nb + 1) + b];
+            const double e1 = edges[d * (nb + 1) + b + 1];
+            double lo, sc;
+            switch (d % 3) {
+                case 0: lo = g.q_min; sc = g.q_max - g.q_min; break;   // r (comoving)
+                case 1: lo = 0.0; sc = kPi; break;                     // theta
+                default: lo = -kPi; sc = kTwoPi; break;                // phi - pi
+            }
+            Real2<R> v;
+            v.y0 = static_cast<R>(lo + sc * e0);
+            v.dy = static_cast<R>(sc * (e1 - e0));
+            s_map[k] = v;
+        }
     }
     // per-warp histograms: atomics from different warps never share an
     // address, and the warps are summed in a fixed order at the end, so the

@@ -283,6 +283,24 @@ __device__ inline SegConst32 seg_const32(const SideDesc& sd, const TaskDesc& td,
     return C;
 }
 
+// The FP32 kernels' map table of one task: for dimension d and increment b,
+// the left end and the width of increment b in the physical variable (r
+// comoving, theta, phi - pi), from the FP64 edges in [0, 1] rounded to FP32;
+// entry d * nb + b of the task's kMaxDim * nbins_max entries.  Written by
+// map32_kernel (every sweep) and by the refinement for the tasks it refines.
+__host__ __device__ inline int map32_stride(const Geometry& g) { return kMaxDim * g.nbins_max; }
+__device__ inline float2 map32_entry(const double* e_task, int d, int b, int nb, const Geometry& g) {
+    const double e0 = e_task[d * (nb + 1) + b];
+    const double e1 = e_task[d * (nb + 1) + b + 1];
+    double lo, sc;
+    switch (d % 3) {
+        case 0: lo = g.q_min; sc = g.q_max - g.q_min; break;   // r (comoving)
+        case 1: lo = 0.0; sc = kPi; break;                     // theta
+        default: lo = -kPi; sc = kTwoPi; break;                // phi - pi
+    }
+    return make_float2(static_cast<float>(lo + sc * e0), static_cast<float>(sc * (e1 - e0)));
+}
+
 // Arguments of the sample kernel.
 struct EvalParams {
     Geometry geo;
@@ -293,6 +311,7 @@ struct EvalParams {
     const SpeciesConst* sconst;
     const TimeState* ts;
     const double* edges;        // [task][map_stride]
+    const float2* map32;        // FP32 kernels: [task][map32_stride] map tables (map32_entry)
     const Segment* segs;
     const int32_t* cta_seg;     // segments of chunk c: [cta_seg[c], cta_seg[c+1])
     int32_t n_chunks;           // chunks of the partition

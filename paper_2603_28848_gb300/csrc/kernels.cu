@@ -509,7 +509,7 @@ __global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
                               const int32_t* __restrict__ active, const int32_t* __restrict__ task_seg,
                               const Segment* __restrict__ segs, const double* __restrict__ partials,
                               double* edges, TaskAcc* acc, TaskConst* tconst_next,
-                              const double* __restrict__ strat_est, SegConst32* tconst32) {
+                              const double* __restrict__ strat_est, SegConst32* tconst32, float2* map32) {
     extern __shared__ double hist[];
     const int t = active[blockIdx.x];
     const TaskDesc td = tasks[t];
@@ -667,6 +667,28 @@ __global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
         fr = fr < 0.0 ? 0.0 : (fr > 1.0 ? 1.0 : fr);
         const double* oe = olde + d * (nb + 1);
         e[q] = oe[i] + fr * (oe[i + 1] - oe[i]);
+    }
+    if (map32) {
+        // the FP32 kernels' table of the refined map
+        __syncthreads();
+        float2* m = map32 + static_cast<int64_t>(t) * map32_stride(g);
+        for (int k = threadIdx.x; k < D * nb; k += blockDim.x) m[k] = map32_entry(e, k / nb, k % nb, nb, g);
+    }
+}
+
+// The FP32 kernels' map tables of tasks [0, n_tasks) from their FP64 edges
+// (edges [task][map_stride], tables [task][map32_stride]); one thread per
+// entry.
+__global__ void map32_kernel(Geometry g, const TaskDesc* __restrict__ tasks, int n_tasks,
+                             const double* __restrict__ edges, float2* map32) {
+    const int stride = map32_stride(g);
+    const int64_t total = static_cast<int64_t>(n_tasks) * stride;
+    for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
+         q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int t = static_cast<int>(q / stride), k = static_cast<int>(q - static_cast<int64_t>(t) * stride);
+        const int nb = tasks[t].nbins, D = tasks[t].dim;
+        if (k < D * nb)
+            map32[q] = map32_entry(edges + static_cast<int64_t>(t) * g.map_stride, k / nb, k % nb, nb, g);
     }
 }
 

@@ -22,6 +22,7 @@ __global__ void spline_build_kernel(Geometry, const double*, int, const double*,
 __global__ void prepare_kernel(Geometry, const SideDesc*, const TaskDesc*, const double*, const double*,
                                const TimeState*, const double*, TaskConst*, TaskAcc*, int, const double*,
                                const SpeciesConst*, SegConst32*);
+__global__ void map32_kernel(Geometry, const TaskDesc*, int, const double*, float2*);
 void* eval_kernel_ptr_f32(int nmax);
 void* eval_kernel_ptr_f64(int nmax);
 best_status check_config(const best_config* cfg);
@@ -49,7 +50,8 @@ constexpr size_t kOffSide = up(kOffSc + sizeof(SpeciesConst) * BEST_MAX_SPECIES)
 constexpr size_t kOffTask = up(kOffSide + sizeof(SideDesc));
 constexpr size_t kOffTconst = up(kOffTask + sizeof(TaskDesc));
 constexpr size_t kOffTc32 = up(kOffTconst + sizeof(TaskConst));
-constexpr size_t kOffAcc = up(kOffTc32 + sizeof(SegConst32));
+constexpr size_t kOffMap32 = up(kOffTc32 + sizeof(SegConst32));
+constexpr size_t kOffAcc = up(kOffMap32 + sizeof(float2) * kMaxDim * kMaxBins);
 constexpr size_t kOffPrev = up(kOffAcc + sizeof(TaskAcc));
 constexpr size_t kOffKnots = up(kOffPrev + sizeof(double));
 constexpr size_t kOffKnots32 = up(kOffKnots + sizeof(double) * kMaxGrid);
@@ -281,6 +283,8 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     const size_t spline_smem = 5 * sizeof(double) * n;
     spline_build_kernel<<<S, 256, spline_smem, st>>>(g, f_dev, 0, knots, ts, sc, fgrid, coef64, coef32);
     prepare_kernel<<<1, 32, 0, st>>>(g, dsd, dtd, knots, fgrid, ts, prev, dtc, dacc, 1, nullptr, sc, dtc32);
+    float2* map32 = reinterpret_cast<float2*>(base + kOffMap32);
+    if (f32) map32_kernel<<<1, 256, 0, st>>>(g, dtd, 1, edges_dev, map32);
 
     // The sample kernel indexes its descriptor arrays and the map by the
     // segment's task index (0 here: the scratch arrays and the caller's map
@@ -295,6 +299,7 @@ extern "C" best_status best_vegas_iteration_noalloc(const best_config* cfg, int3
     P.sconst = sc;
     P.ts = ts;
     P.edges = edges_dev;
+    P.map32 = map32;
     P.segs = reinterpret_cast<const Segment*>(base + kOffSegs);
     P.cta_seg = reinterpret_cast<const int32_t*>(base + kOffCtaSeg);
     P.n_chunks = ctas;                  // one chunk (segment) per CTA, no counter
