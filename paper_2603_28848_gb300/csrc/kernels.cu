@@ -386,24 +386,38 @@ __global__ void strat_refine_kernel(const TaskDesc* __restrict__ tasks, const in
         double s1 = 0.0, s2 = 0.0;
         b_h[0][threadIdx.x] = -1;
         b_h[1][threadIdx.x] = -1;
-        for (int64_t i = i0; i < i1; ++i) {
-            const int32_t h = static_cast<int32_t>(ih[i]);
-            if (h != cur) {
-                if (cur >= 0) {
-                    if (b_h[0][threadIdx.x] < 0) {
-                        b_h[0][threadIdx.x] = cur; b_1[0][threadIdx.x] = s1; b_2[0][threadIdx.x] = s2;
-                    } else {
-                        S1h[cur] = s1;
-                        S2h[cur] = s2;
-                    }
-                }
-                cur = h;
-                s1 = 0.0;
-                s2 = 0.0;
+        // eight items per step, their loads issued together (the run logic
+        // below is serial per thread and would otherwise wait on each load)
+        constexpr int U = 8;
+        for (int64_t i = i0; i < i1; i += U) {
+            int32_t hh[U];
+            double2 rr[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool in = i + u < i1;
+                hh[u] = in ? static_cast<int32_t>(ih[i + u]) : -1;
+                rr[u] = in ? rec[i + u] : make_double2(0.0, 0.0);
             }
-            const double2 r = rec[i];
-            s1 += r.x;
-            s2 += r.y;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int32_t h = hh[u];
+                if (h < 0) continue;
+                if (h != cur) {
+                    if (cur >= 0) {
+                        if (b_h[0][threadIdx.x] < 0) {
+                            b_h[0][threadIdx.x] = cur; b_1[0][threadIdx.x] = s1; b_2[0][threadIdx.x] = s2;
+                        } else {
+                            S1h[cur] = s1;
+                            S2h[cur] = s2;
+                        }
+                    }
+                    cur = h;
+                    s1 = 0.0;
+                    s2 = 0.0;
+                }
+                s1 += rr[u].x;
+                s2 += rr[u].y;
+            }
         }
         if (cur >= 0) {
             const int k = b_h[0][threadIdx.x] < 0 ? 0 : 1;
