@@ -387,6 +387,19 @@ int32_t best_num_side_integrals(const best_ctx* ctx);
  * Synchronises `stream`. */
 best_status best_get_budgets(best_ctx* ctx, int64_t* neval, void* stream);
 
+/* The work partition of VEGAS iteration `iteration` as the next sweep will
+ * use it (built on the host, or rebuilt on the device after variance-driven
+ * budgets changed): groups[t] (caller-owned host array [n_tasks]) receives
+ * the number of sample groups the iteration's segments of task t cover, 0
+ * for a task not active in that iteration, or -1 when its segments do not
+ * tile [0, groups) exactly (a gap, an overlap or an out-of-order segment).
+ * A sample group is the samples of one Philox block set: 2 (FP64) or 4
+ * (FP32) uniforms per block shared over D-dimensional samples, so a task of
+ * N samples has ceil(N / G) groups (for stratified tasks, whole items of 8
+ * samples).  Synchronises the device.  BEST_ERR_INVALID when ctx or groups
+ * is NULL or the iteration is out of range. */
+best_status best_partition_groups(best_ctx* ctx, int32_t iteration, int64_t* groups);
+
 /* Integrand evaluations of one sweep: in VEGAS iteration `iteration` (one
  * launch of the sample kernel), or in all iterations when iteration < 0.
  * With variance-driven budgets these are the next sweep's budgets as the

@@ -393,6 +393,15 @@ class Collision:
         check(self.lib.best_profile_read(self.ctx, ctypes.byref(ms), ctypes.byref(n)), self.ctx)
         return ms.value, n.value
 
+    def partition_groups(self, iteration):
+        """Sample groups of every task covered by the work partition of VEGAS
+        iteration `iteration` (int64 array; -1 where a task's segments do not
+        tile its groups exactly, 0 for inactive tasks)."""
+        out = np.zeros(self.n_tasks, dtype=np.int64)
+        check(self.lib.best_partition_groups(self.ctx, int(iteration), out.ctypes.data_as(ctypes.c_void_p)),
+              self.ctx)
+        return out
+
     def sweep_samples(self, iteration=-1):
         """Integrand evaluations per sweep (or in one VEGAS iteration)."""
         return self.lib.best_sweep_samples(self.ctx, int(iteration))

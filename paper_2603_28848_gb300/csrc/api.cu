@@ -1767,6 +1767,38 @@ best_status best_get_budgets(best_ctx* ctx, int64_t* neval, void* stream) {
     return BEST_OK;
 }
 
+best_status best_partition_groups(best_ctx* ctx, int32_t iteration, int64_t* groups) {
+    if (!ctx || !groups) return fail(ctx, BEST_ERR_INVALID, "NULL argument");
+    if (iteration < 0 || iteration >= ctx->max_nitn) return fail(ctx, BEST_ERR_INVALID, "iteration out of range");
+    CK(cudaDeviceSynchronize());
+    const IterPlan& pl = ctx->plans[iteration];
+    const int T = ctx->geo.n_tasks;
+    for (int t = 0; t < T; ++t) groups[t] = 0;
+    if (pl.n_active == 0) return BEST_OK;
+    // the device may have rebuilt the partition: read its current shape
+    std::vector<int32_t> active(pl.n_active), task_seg(pl.n_active + 1), cta_seg(ctx->n_chunks + 1);
+    CK(cudaMemcpy(active.data(), pl.d_active, active.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(task_seg.data(), pl.d_task_seg, task_seg.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(cta_seg.data(), pl.d_cta_seg, cta_seg.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    const int n_segs = cta_seg[ctx->n_chunks];
+    if (n_segs < 0 || cta_seg[0] != 0) return fail(ctx, BEST_ERR_INVALID, "internal: malformed partition");
+    std::vector<Segment> segs(n_segs);
+    if (n_segs > 0) CK(cudaMemcpy(segs.data(), pl.d_segs, n_segs * sizeof(Segment), cudaMemcpyDeviceToHost));
+    for (int c = 0; c < ctx->n_chunks; ++c)
+        if (cta_seg[c + 1] < cta_seg[c]) return fail(ctx, BEST_ERR_INVALID, "internal: malformed partition");
+    for (int a = 0; a < pl.n_active; ++a) {
+        const int t = active[a];
+        int64_t next = 0;
+        bool ok = task_seg[a] <= task_seg[a + 1] && task_seg[a + 1] <= n_segs;
+        for (int k = task_seg[a]; ok && k < task_seg[a + 1]; ++k) {
+            ok = segs[k].task == t && segs[k].g0 == next && segs[k].g1 > segs[k].g0;
+            next = segs[k].g1;
+        }
+        groups[t] = ok ? next : -1;
+    }
+    return BEST_OK;
+}
+
 best_status best_get_task_results(best_ctx* ctx, double* mean, double* err, void* stream) {
     if (!ctx) return fail(nullptr, BEST_ERR_INVALID, "ctx is NULL");
     CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
