@@ -364,6 +364,13 @@ int group_size(int D, bool f32) {
     return per / a;
 }
 
+// CTAs of 256 threads for map32_kernel: one thread per table entry, at most
+// 4096 CTAs (the kernel strides over the rest).
+int map32_blocks(const Geometry& g) {
+    const int64_t entries = static_cast<int64_t>(g.n_tasks) * map32_stride(g);
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((entries + 255) / 256, 4096)));
+}
+
 // Dynamic shared memory of the sample kernel with `threads` per CTA: spline
 // tables of all species, the map table, per-warp histograms, the reduction
 // scratch and (FP32) the per-warp sample queues, in the kernel's layout.
@@ -550,7 +557,7 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
                                                             ctx->d_tconst32);
     ctx->launches += 2;
     if (ctx->d_map32) {
-        map32_kernel<<<2 * 152, 256, 0, st>>>(g, ctx->d_tasks, g.n_tasks, ctx->d_edges, ctx->d_map32);
+        map32_kernel<<<map32_blocks(g), 256, 0, st>>>(g, ctx->d_tasks, g.n_tasks, ctx->d_edges, ctx->d_map32);
         ctx->launches += 1;
     }
     const bool f32 = ctx->precision == BEST_FP32;
@@ -1288,7 +1295,7 @@ best_status best_collision_vjp(best_ctx* ctx, const double* f_dev, double t, con
                                                             ctx->d_ts, ctx->d_prev, ctx->d_tconst, ctx->d_acc, 0,
                                                             ctx->d_width, ctx->d_sconst, ctx->d_tconst32);
     if (ctx->d_map32)
-        map32_kernel<<<2 * 152, 256, 0, st>>>(g, ctx->d_tasks, g.n_tasks, ctx->d_edges, ctx->d_map32);
+        map32_kernel<<<map32_blocks(g), 256, 0, st>>>(g, ctx->d_tasks, g.n_tasks, ctx->d_edges, ctx->d_map32);
     vjp_seed_kernel<<<(g.n_tasks + 127) / 128, 128, 0, st>>>(g, ctx->d_sides, ctx->d_tasks, ctx->d_tconst, v_dev,
                                                              ctx->d_u);
     CK(cudaMemsetAsync(ctx->d_gcoef, 0, sizeof(double) * g.n_species * (g.n_grid - 1) * 4, st));
@@ -1396,7 +1403,7 @@ static best_status enqueue_jvp(best_ctx* ctx, const double* f_dev, double t, con
                                                                 ctx->d_acc, 0, ctx->d_width, ctx->d_sconst,
                                                                 ctx->d_tconst32);
         if (ctx->d_map32) {
-            map32_kernel<<<2 * 152, 256, 0, st>>>(g, ctx->d_tasks, g.n_tasks, ctx->d_edges, ctx->d_map32);
+            map32_kernel<<<map32_blocks(g), 256, 0, st>>>(g, ctx->d_tasks, g.n_tasks, ctx->d_edges, ctx->d_map32);
             ctx->launches += 1;
         }
         ctx->launches += 3;

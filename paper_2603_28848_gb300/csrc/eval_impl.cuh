@@ -134,6 +134,14 @@ struct SegConst {
     int fd[NI];
 };
 
+// log2 of a normal positive float, the bare special-function op (no
+// subnormal handling: the spline lookups take momenta >= q_0 > 0).
+__device__ __forceinline__ float lg2_ftz(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Cubic spline value at comoving q inside [q_0, q_{n-1}] (Sec. 3B).
 template <typename R>
 __device__ __forceinline__ R spline_eval(const SplineView<R>& sv, R q, const Geometry& g,
@@ -143,7 +151,7 @@ __device__ __forceinline__ R spline_eval(const SplineView<R>& sv, R q, const Geo
     int j;
     if (g.log_spaced) {
         // log2(q / q0) / step = log2(q) / step - log2(q0) / step
-        j = static_cast<int>(fmaf(__log2f(static_cast<float>(q)), static_cast<float>(inv_step),
+        j = static_cast<int>(fmaf(lg2_ftz(static_cast<float>(q)), static_cast<float>(inv_step),
                                   -static_cast<float>(lq0_step)));
     } else {
         j = static_cast<int>(static_cast<float>((q - q0) * inv_step));

@@ -37,7 +37,7 @@ __device__ __forceinline__ Hit<R> spline_hit(const SplineView<R>& sv, R q, const
                                              R lq0_step, bool fd) {
     int j;
     if (g.log_spaced) {
-        j = static_cast<int>(fmaf(__log2f(static_cast<float>(q)), static_cast<float>(inv_step),
+        j = static_cast<int>(fmaf(lg2_ftz(static_cast<float>(q)), static_cast<float>(inv_step),
                                   -static_cast<float>(lq0_step)));
     } else {
         j = static_cast<int>(static_cast<float>((q - q0) * inv_step));
