@@ -31,10 +31,20 @@ struct Real2 { R y0, dy; };
 
 template <typename R> struct RMath;
 
+// 1/sqrt(x) of a normal positive float, the bare special-function op (the
+// FP32 kernels guard its arguments to at least 1e-30: momenta and energies
+// squared, never subnormal there).
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <> struct RMath<float> {
     static constexpr bool kF32 = true;
     __device__ static __forceinline__ void sincos_(float x, float* s, float* c) { __sincosf(x, s, c); }
-    __device__ static __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+    __device__ static __forceinline__ float rsqrt_(float x) { return rsqrt_ftz(x); }
+    static constexpr float kTiny = 1e-30f;         // smallest argument rsqrt_ is given
     __device__ static __forceinline__ float exp2_(float x) { return exp2f(x); }
     __device__ static __forceinline__ float expm1_(float x) { return expm1f(x); }
     __device__ static __forceinline__ float exp_(float x) { return __expf(x); }
@@ -45,6 +55,7 @@ template <> struct RMath<double> {
     static constexpr bool kF32 = false;
     __device__ static __forceinline__ void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
     __device__ static __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+    static constexpr double kTiny = 0.0;
     __device__ static __forceinline__ double exp2_(double x) { return exp2(x); }
     __device__ static __forceinline__ double expm1_(double x) { return expm1(x); }
     __device__ static __forceinline__ double exp_(double x) { return exp(x); }
@@ -227,12 +238,12 @@ __device__ __forceinline__ R kin_at(const SegConst<R, NLEG>& C, const R* y, R ja
     // conserved leg (Eq. (10), App. A)
     const R pc2 = fma(px, px, fma(py, py, pz * pz));
     const R Ec2 = pc2 + C.m2c;
-    const R rEc = RMath<R>::rsqrt_(Ec2 > R(0) ? Ec2 : R(1e-30));
+    const R rEc = RMath<R>::rsqrt_(Ec2 > RMath<R>::kTiny ? Ec2 : R(1e-30));
     Ec = Ec2 * rEc;
     cut |= Ec < C.e_cut;
     bal.add(C.sgn_cons * Ec);
     const R dE = bal.value();
-    qc = pc2 * (pc2 > R(0) ? RMath<R>::rsqrt_(pc2) : R(0)) * C.a;
+    qc = pc2 * (pc2 > RMath<R>::kTiny ? RMath<R>::rsqrt_(pc2) : R(0)) * C.a;
     R gauss;
     if (C.frac) {
         // sigma = w S / 2 with S = E_in + E_out: exponent
@@ -310,7 +321,7 @@ __device__ __forceinline__ float2 kin_pair(const SegConst<float, NLEG>& C, const
         py = fma2(nps, sp, py);
         pz = fma2(mul2(p, bc2(C.sig[j])), ct, pz);
         const float2 E2 = fma2(p, p, bc2(C.m2[j]));
-        const float2 rE = make_float2(rsqrtf(E2.x), rsqrtf(E2.y));
+        const float2 rE = make_float2(rsqrt_ftz(E2.x), rsqrt_ftz(E2.y));
         const float2 E = mul2(E2, rE);
         emin0 = fminf(emin0, E.x);
         emin1 = fminf(emin1, E.y);
@@ -322,13 +333,13 @@ __device__ __forceinline__ float2 kin_pair(const SegConst<float, NLEG>& C, const
     // conserved leg (Eq. (10), App. A)
     const float2 pc2 = fma2(px, px, fma2(py, py, mul2(pz, pz)));
     const float2 Ec2q = add2(pc2, bc2(C.m2c));
-    const float2 rEc = make_float2(rsqrtf(Ec2q.x > 0.0f ? Ec2q.x : 1e-30f), rsqrtf(Ec2q.y > 0.0f ? Ec2q.y : 1e-30f));
+    const float2 rEc = make_float2(rsqrt_ftz(Ec2q.x > 1e-30f ? Ec2q.x : 1e-30f), rsqrt_ftz(Ec2q.y > 1e-30f ? Ec2q.y : 1e-30f));
     Ec = mul2(Ec2q, rEc);
     emin0 = fminf(emin0, Ec.x);
     emin1 = fminf(emin1, Ec.y);
     bal.add(mul2(bc2(C.sgn_cons), Ec));
     const float2 dE = bal.value();
-    const float2 rpc = make_float2(pc2.x > 0.0f ? rsqrtf(pc2.x) : 0.0f, pc2.y > 0.0f ? rsqrtf(pc2.y) : 0.0f);
+    const float2 rpc = make_float2(pc2.x > 1e-30f ? rsqrt_ftz(pc2.x) : 0.0f, pc2.y > 1e-30f ? rsqrt_ftz(pc2.y) : 0.0f);
     qc = mul2(mul2(pc2, rpc), bc2(C.a));
     float2 gauss;
     if (C.frac) {

@@ -438,12 +438,12 @@ __device__ __forceinline__ void vjp_segment(const VjpParams& V, const Segment& s
             }
             const R pc2 = fma(px, px, fma(py, py, pz * pz));
             const R Ec2 = pc2 + m2c;
-            const R rEc = RMath<R>::rsqrt_(Ec2 > R(0) ? Ec2 : R(1e-30));
+            const R rEc = RMath<R>::rsqrt_(Ec2 > RMath<R>::kTiny ? Ec2 : R(1e-30));
             const R Ec = Ec2 * rEc;
             cut |= Ec < e_cut;
             bal.add(sgn_cons * Ec);
             const R dE = bal.value();
-            const R qc = pc2 * (pc2 > R(0) ? RMath<R>::rsqrt_(pc2) : R(0)) * a;
+            const R qc = pc2 * (pc2 > RMath<R>::kTiny ? RMath<R>::rsqrt_(pc2) : R(0)) * a;
             // Gaussian and, for the adjoint, 1/sigma^2 and the derivative of
             // log(1/sigma) with exp(-dE^2 / 2 sigma^2) through sigma(E_k)
             R gs, inv_sig2, sig_term;
