@@ -31,6 +31,13 @@ struct Real2 { R y0, dy; };
 
 template <typename R> struct RMath;
 
+// 2^x with denormal results flushed to zero (the bare special-function op)
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // 1/sqrt(x) of a normal positive float, the bare special-function op (the
 // FP32 kernels guard its arguments to at least 1e-30: momenta and energies
 // squared, never subnormal there).
@@ -45,7 +52,7 @@ template <> struct RMath<float> {
     __device__ static __forceinline__ void sincos_(float x, float* s, float* c) { __sincosf(x, s, c); }
     __device__ static __forceinline__ float rsqrt_(float x) { return rsqrt_ftz(x); }
     static constexpr float kTiny = 1e-30f;         // smallest argument rsqrt_ is given
-    __device__ static __forceinline__ float exp2_(float x) { return exp2f(x); }
+    __device__ static __forceinline__ float exp2_(float x) { return ex2_ftz(x); }   // (Gaussian: x <= 0)
     __device__ static __forceinline__ float expm1_(float x) { return expm1f(x); }
     __device__ static __forceinline__ float exp_(float x) { return __expf(x); }
     __device__ static __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
@@ -288,12 +295,6 @@ struct EBal2 {
     }
     __device__ __forceinline__ float2 value() const { return add2(s, c); }
 };
-// 2^x with denormal results flushed to zero (the bare special-function op)
-__device__ __forceinline__ float ex2_ftz(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 // kin_at for two samples at once (constant |M|^2), each FP32 operation
 // packed over the pair; the special-function operations stay per sample.
