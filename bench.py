@@ -40,8 +40,8 @@ CPU_NEVAL = 20_000  # samples per iteration of the oracle tasks timed on the hos
 # 5e5 samples per task (summarised under profiles/); the tables it reads do not grow with
 # the sample count.  The kernel is issue-bound, so its instruction issue rate against the SMs' issue peak
 # says how close it is to the hardware limit.
-TRAFFIC_BYTES_PER_LAUNCH = 1.9392e6
-INSTR_PER_SAMPLE_C2 = 332.2
+TRAFFIC_BYTES_PER_LAUNCH = 1.903872e6
+INSTR_PER_SAMPLE_C2 = 310.4
 ISSUE_PEAK_TINSTR = 152 * 4 * 32 * 2.07e9 / 1e12     # 4 schedulers x 1 warp instruction / clock
 FP32_PEAK_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
