@@ -909,7 +909,7 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
                                      static_cast<int>(ctx->spline_smem)) != cudaSuccess)
                 return bail(fail(ctx, BEST_ERR_CUDA, "cannot set shared memory of the spline kernels"));
         }
-        ctx->refine_smem = sizeof(double) * (5 * static_cast<size_t>(kMaxDim) * nb_max + 3 * kMaxDim + 2);
+        ctx->refine_smem = sizeof(double) * (5 * static_cast<size_t>(kMaxDim) * nb_max + 4 * kMaxDim + 2);
         if (cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(&refine_kernel)) != cudaSuccess)
             return bail(fail(ctx, BEST_ERR_CUDA, "cannot query the refinement kernel"));
         if (static_cast<size_t>(fa.maxDynamicSharedSizeBytes) < ctx->refine_smem &&

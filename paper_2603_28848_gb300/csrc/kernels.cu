@@ -594,8 +594,8 @@ __global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
     // parallel: the increment where the running sum reaches k / nb of the
     // total, and the linear interpolation inside it
     double* sm = hist + 2 + D * nb;            // smoothed, then compressed weights [D][nb]
-    double* tot = sm + D * nb;                 // per-dimension sums [D]
-    double* olde = tot + D;                    // old edges [D][nb + 1]
+    double* tot = sm + D * nb;                 // per-dimension sums [D], then (FP32 path) their reciprocals [D]
+    double* olde = tot + 2 * D;                // old edges [D][nb + 1]
     double* rom = olde + D * (nb + 1);         // reciprocals of the compressed weights [D][nb]
     double* cum = rom + D * nb;                // running sums of the compressed weights [D][nb + 1]
     const double* e_task = edges + static_cast<int64_t>(t) * g.map_stride;
@@ -611,36 +611,44 @@ __global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
         sm[k] = v;
     }
     __syncthreads();
+    const bool f32 = g.precision == BEST_FP32;
     if (threadIdx.x < D) {
         double t = 0.0;
         for (int b = 0; b < nb; ++b) t += sm[threadIdx.x * nb + b];
         tot[threadIdx.x] = t;
+        // FP32 path: the totals are sums of FP32 training data, so their
+        // reciprocals are finite (an FP64 total can be subnormal)
+        tot[D + threadIdx.x] = f32 && t > 0.0 ? 1.0 / t : 0.0;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < D * nb; k += blockDim.x) {
         const int d = k / nb;
         const double t = tot[d];
-        double o = 0.0;
+        double o = 0.0, r = 0.0;
         if (t > 0.0) {
-            const double v = sm[k] / t;
-            if (v < 1e-30) o = 0.0;            // numerically empty increment
-            else if (v >= 1.0) o = 1.0;
-            else if (g.precision == BEST_FP32) {
+            if (f32) {
                 // the FP32 path's training data carry FP32 rounding: its
-                // compression is evaluated in FP32 too (FP64 log and pow run
-                // at a small fraction of the FP32 rate on this GPU)
-                const float vf = static_cast<float>(v);
-                o = vf < 1.0f ? static_cast<double>(powf((1.0f - vf) / -logf(vf), static_cast<float>(td.alpha)))
-                              : 1.0;
+                // normalisation, compression and reciprocal are evaluated in
+                // FP32 (FP64 division, log and pow run at a small fraction of
+                // the FP32 rate on this GPU)
+                const float vf = static_cast<float>(sm[k] * tot[D + d]);
+                float of = 1.0f;               // v >= 1, or not a number (FP32 training data overflowed)
+                if (vf < 1e-30f) of = 0.0f;    // numerically empty increment
+                else if (vf < 1.0f) of = powf((1.0f - vf) / -logf(vf), static_cast<float>(td.alpha));
+                o = of;
+                r = of > 0.0f ? __frcp_rn(of) : 0.0f;
             } else {
-                o = pow((1.0 - v) / -log(v), td.alpha);
+                const double v = sm[k] / t;
+                if (v < 1e-30) o = 0.0;        // numerically empty increment
+                else if (v >= 1.0) o = 1.0;
+                else o = pow((1.0 - v) / -log(v), td.alpha);
+                // the interpolation below multiplies by these reciprocals (o is
+                // 0 or at least (1 / ln 1e30)^alpha)
+                r = o > 0.0 ? 1.0 / o : 0.0;
             }
         }
         sm[k] = o;
-        // the interpolation below multiplies by these reciprocals (o is 0 or
-        // at least (1 / ln 1e30)^alpha): FP64 division is a long dependent
-        // sequence on this GPU
-        rom[k] = o > 0.0 ? 1.0 / o : 0.0;
+        rom[k] = r;
     }
     __syncthreads();
     if (threadIdx.x < D) {
