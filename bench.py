@@ -42,6 +42,10 @@ CPU_NEVAL = 20_000  # samples per iteration of the oracle tasks timed on the hos
 # says how close it is to the hardware limit.
 TRAFFIC_BYTES_PER_LAUNCH = 1.903872e6
 INSTR_PER_SAMPLE_C2 = 310.4
+# FP32 FLOP per sample measured by ncu's FP32 operation counters (FFMA, FADD, FMUL and their packed
+# FP32x2 forms) on the same launch shape: the source count charges every sample the statistical
+# factor, which the per-warp queue evaluates only for near-shell samples.
+MEASURED_FLOPS_PER_SAMPLE_C2 = 122.9
 ISSUE_PEAK_TINSTR = 152 * 4 * 32 * 2.07e9 / 1e12     # 4 schedulers x 1 warp instruction / clock
 FP32_PEAK_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
@@ -379,6 +383,7 @@ def run_native(args, rank, world):
         roof["issue"] = {"achieved": issued, "peak": ISSUE_PEAK_TINSTR, "unit": "T thread-instructions/s",
                          "frac": issued / ISSUE_PEAK_TINSTR, "instructions_per_sample": INSTR_PER_SAMPLE_C2,
                          "source": "ncu capture in profiles/eval_kernel_f32_c2_bose_2to2.md"}
+        roof["flops_per_sample_ncu"] = MEASURED_FLOPS_PER_SAMPLE_C2
 
     out = {
         "metric": METRIC, "value": sweeps_per_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -225,6 +225,17 @@ __device__ inline double clamp_scale(double scale, double obs_factor) {
     return scale < lo ? lo : (scale > hi ? hi : scale);
 }
 
+// x^k for a non-negative integer k by repeated squaring (the task constants'
+// integer powers: a few multiplications instead of an FP64 pow sequence)
+__device__ inline double ipow(double x, int k) {
+    double r = 1.0;
+    for (; k > 0; k >>= 1) {
+        if (k & 1) r *= x;
+        x *= x;
+    }
+    return r;
+}
+
 __global__ void prepare_kernel(Geometry g, const SideDesc* __restrict__ sides,
                                const TaskDesc* __restrict__ tasks, const double* __restrict__ knots,
                                const double* __restrict__ fgrid, const TimeState* ts,
@@ -241,9 +252,9 @@ __global__ void prepare_kernel(Geometry g, const SideDesc* __restrict__ sides,
     const double E = sqrt(p * p + m * m);
     const int n = sd.n;
     const int D = 3 * (n - 2);
-    const double nbD = pow(static_cast<double>(td.nbins), D);
-    const double two_pi_pow = pow(kTwoPi, 3 * (n - 1) - 4);
-    const double a3 = pow(a, -3.0 * (n - 2));
+    const double nbD = ipow(static_cast<double>(td.nbins), D);
+    const double two_pi_pow = ipow(kTwoPi, 3 * (n - 1) - 4);
+    const double a3 = ipow(ts->inv_a, 3 * (n - 2));             // a^{-3(n-2)}
     TaskConst c;
     c.p_obs = p;
     c.E_obs = E;
