@@ -107,6 +107,7 @@ struct best_ctx {
     size_t eval_smem = 0;
     size_t spline_smem = 0;
     size_t refine_smem = 0;
+    int refine_threads = 128;       // one thread per entry of a task's reduced record, 128 to 512
     void* eval_fn = nullptr;
     int n_variants = 0;             // sample-kernel variants (register budget, CTA size, samples per step)
     SampleVariant variants[kMaxVariants] = {};
@@ -614,7 +615,7 @@ best_status enqueue_sweep(best_ctx* ctx, const double* src, int src_mode, double
                                                              ctx->d_item_h, ctx->d_strat_est);
             ctx->launches += 1;
         }
-        refine_kernel<<<pl.n_active, 128, ctx->refine_smem, st>>>(
+        refine_kernel<<<pl.n_active, ctx->refine_threads, ctx->refine_smem, st>>>(
             g, ctx->d_sides, ctx->d_tasks, ctx->d_tconst, pl.d_active, pl.d_task_seg, pl.d_segs,
             ctx->d_partials, ctx->d_edges, ctx->d_acc, ctx->d_tconst, ctx->d_strat_est, ctx->d_tconst32,
             ctx->d_map32);
@@ -910,6 +911,9 @@ best_status best_collision_init(const best_config* cfg, best_ctx** out) {
                 return bail(fail(ctx, BEST_ERR_CUDA, "cannot set shared memory of the spline kernels"));
         }
         ctx->refine_smem = sizeof(double) * (5 * static_cast<size_t>(kMaxDim) * nb_max + 4 * kMaxDim + 2);
+        // the refinement's first phase sums each entry of the records (2 + D nb) over the task's
+        // segments, one entry per thread where they fit: a chain of dependent loads per entry
+        ctx->refine_threads = std::min(512, std::max(128, (2 + 3 * (ctx->nmax_legs - 2) * nb_max + 31) / 32 * 32));
         if (cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(&refine_kernel)) != cudaSuccess)
             return bail(fail(ctx, BEST_ERR_CUDA, "cannot query the refinement kernel"));
         if (static_cast<size_t>(fa.maxDynamicSharedSizeBytes) < ctx->refine_smem &&

@@ -543,16 +543,15 @@ __global__ void refine_kernel(Geometry g, const SideDesc* __restrict__ sides,
     const int s0 = task_seg[blockIdx.x], s1 = task_seg[blockIdx.x + 1];
     const int L = 2 + D * nb;
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
-        // the records in segment order; four loads in flight at a time
+        // the records in segment order; eight loads in flight at a time
         double v = 0.0;
         int s = s0;
-        for (; s + 4 <= s1; s += 4) {
-            const double a0 = partials[segs[s].part + k], a1 = partials[segs[s + 1].part + k];
-            const double a2 = partials[segs[s + 2].part + k], a3 = partials[segs[s + 3].part + k];
-            v += a0;
-            v += a1;
-            v += a2;
-            v += a3;
+        for (; s + 8 <= s1; s += 8) {
+            double a[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] = partials[segs[s + u].part + k];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v += a[u];
         }
         for (; s < s1; ++s) v += partials[segs[s].part + k];
         hist[k] = v;
