@@ -380,11 +380,15 @@ size_t sample_smem(const best_ctx* ctx, int threads) {
     const bool f32 = ctx->precision == BEST_FP32;
     const size_t rs = f32 ? 4 : 8;
     const size_t spl = static_cast<size_t>(g.n_species) * 4 * (g.n_grid - 1) + g.n_grid;
-    const size_t map_elems = static_cast<size_t>(kMaxDim) * g.nbins_max;
+    // the kernel's table stride: 12 dimensions, or in the extended instantiations
+    // (stratified tasks or an s-dependent |M|^2) those of their NMAX (4 or 6 legs)
+    const bool ext = ctx->any_strat || ctx->any_me;
+    const int dims = ext ? (ctx->nmax_legs <= 4 ? 6 : 12) : kMaxDim;
+    const size_t map_elems = static_cast<size_t>(dims) * g.nbins_max;
     const size_t hist_elems = static_cast<size_t>(threads / 32) * map_elems;
+    const size_t queue = ctx->any_strat ? strat_queue_floats(ctx->nmax_legs) : kQueueSlots * queue_words(ctx->nmax_legs);
     return rs * ((spl + 3) & ~size_t(3)) + 2 * rs * map_elems + rs * ((hist_elems + 3) & ~size_t(3)) +
-           2 * 32 * sizeof(double) +
-           (f32 ? sizeof(float) * (threads / 32) * kQueueSlots * queue_words(ctx->nmax_legs) : 0);
+           2 * 32 * sizeof(double) + (f32 ? sizeof(float) * (threads / 32) * queue : 0);
 }
 
 // Partition of the active tasks of one iteration into n_chunks chunks cut at

@@ -563,7 +563,8 @@ template <typename R, int NLEG, bool STRAT, int SPL>
 __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& seg,
                                             const SideDesc& sd, const TaskDesc& td,
                                             const TaskConst& tc, R* s_spline,
-                                            Real2<R>* s_map, R* s_hist, double* s_red, float* s_queue) {
+                                            Real2<R>* s_map, R* s_hist, double* s_red, float* s_queue,
+                                            int map_elems) {
     constexpr int NI = NLEG - 2;
     constexpr int D = 3 * NI;
     constexpr bool F32 = RMath<R>::kF32;
@@ -606,7 +607,6 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
     // per-warp histograms: atomics from different warps never share an
     // address, and the warps are summed in a fixed order at the end, so the
     // training data do not depend on warp scheduling
-    const int map_elems = kMaxDim * g.nbins_max;
     const int nwarps = blockDim.x >> 5;
     for (int k = tid; k < nwarps * map_elems; k += blockDim.x) s_hist[k] = R(0);
     R* w_hist = s_hist + (tid >> 5) * map_elems;
@@ -826,8 +826,8 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
         }
     }
     else if constexpr (STRAT) {
-        // Adaptive stratified sampling: one thread per item of kItem samples,
-        // all in hypercube h = item_h[item] with strata (i_0 .. i_{D-1});
+        // Adaptive stratified sampling: items of kItem samples, all in
+        // hypercube h = item_h[item] with strata (i_0 .. i_{D-1});
         // x_d = (i_d + u_d) / M.  The item's (sum w, sum w^2) go to its own
         // record (summed per hypercube in a fixed order afterwards); the
         // training data weigh w^2 by 1 / m_h.
@@ -837,66 +837,202 @@ __device__ __forceinline__ void run_segment(const EvalParams& P, const Segment& 
         const uint32_t* ih = P.item_h + td.strat_off_item;
         const int32_t* sm = P.strat_m + td.strat_off_h;
         double2* rec = reinterpret_cast<double2*>(P.item_rec) + td.strat_off_item;
-        const int32_t it1 = g1 / GPI;
-        for (int32_t item = static_cast<int32_t>(seg.g0) / GPI + tid; item < it1; item += blockDim.x) {
-            const uint32_t h = ih[item];
-            const R inv_m = R(1) / static_cast<R>(sm[h]);
-            R xi[D];                                     // i_d as R
-            {
-                uint32_t r = h;
+        const int32_t it0 = static_cast<int32_t>(seg.g0) / GPI, it1 = g1 / GPI;
+        if constexpr (F32) {
+            // The per-warp queue of the plain loop: a warp takes KI items per
+            // lane (a round), queues the samples with a non-zero kinematic
+            // part together with their item's slot in the round and 1 / m_h,
+            // and evaluates them 32 at a time; w and w^2 go to the slot's
+            // shared-memory sums.  At the round's end the queue is drained and
+            // the round's item records are written.
+            constexpr int QW = queue_words(NLEG);
+            constexpr int KI = kStratItemsPerLane;
+            constexpr int NB = (D + 3) / 4;
+            float* q = s_queue + (tid >> 5) * strat_queue_floats(NLEG);
+            float* isum = q + kQueueSlots * (QW + 2);          // [2][32 KI]: sum w, sum w^2 per item slot
+            const int lane = tid & 31;
+            const uint32_t lanes_below = (1u << lane) - 1u;
+            int qn = 0;                                       // queued samples (warp-uniform)
+            auto drain = [&](int slot) {
+                R r[NI];
 #pragma unroll
-                for (int d = 0; d < D; ++d) {
-                    const uint32_t q = r / static_cast<uint32_t>(M);
-                    xi[d] = static_cast<R>(r - q * static_cast<uint32_t>(M));
-                    r = q;
+                for (int j = 0; j < NI; ++j) r[j] = q[(1 + j) * kQueueSlots + slot];
+                const R qc = q[(1 + NI) * kQueueSlots + slot];
+                const R Ec = q[(2 + NI) * kQueueSlots + slot];
+                const R w = stat_at<R, NLEG>(C, r, qc, Ec, s_spline, knots, g, inv_step, q0, lq0_step, qN, ncoef) *
+                            q[slot];
+                const R w2 = w * w;
+                acc_w.add(w);
+                acc_w2.add(w2);
+                const uint32_t is = __float_as_uint(q[QW * kQueueSlots + slot]);
+                atomicAdd(&isum[is], w);
+                atomicAdd(&isum[32 * KI + is], w2);
+                if (w2 != R(0)) {
+                    const R w2m = w2 * q[(QW + 1) * kQueueSlots + slot];
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) {
+                        const uint32_t pb = __float_as_uint(q[(3 + NI + k) * kQueueSlots + slot]);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (4 * k + e < D)
+                                atomicAdd(&w_hist[(4 * k + e) * nb + ((pb >> (8 * e)) & 0xFFu)], w2m);
+                    }
                 }
-            }
-            R s1 = R(0), s2 = R(0);
-#pragma unroll 1
-            for (int gi = 0; gi < GPI; ++gi) {
-                const int32_t grp = item * GPI + gi;
-                uint32_t uw[F32 ? SS::kUniforms : 1];
-                R u[F32 ? 1 : SS::kUniforms];
-                if constexpr (F32) group_words<D>(uw, grp, P.itn, call, task, P.rk);
-                else group_uniforms<D, F32, R>(u, grp, P.itn, call, task, P.rk);
+            };
+            auto push = [&](bool keep, float kin, const float* r, float qc, float Ec, const uint32_t* pb, uint32_t is,
+                            float inv_m) {
+                const uint32_t vote = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int slot = qn + __popc(vote & lanes_below);     // < 2 * 32
+                    q[slot] = kin;
 #pragma unroll
-                for (int sgi = 0; sgi < G; ++sgi) {
-                    R y[D];
-                    int bin[D];
-                    R jac = R(1);
+                    for (int j = 0; j < NI; ++j) q[(1 + j) * kQueueSlots + slot] = r[j];
+                    q[(1 + NI) * kQueueSlots + slot] = qc;
+                    q[(2 + NI) * kQueueSlots + slot] = Ec;
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) q[(3 + NI + k) * kQueueSlots + slot] = __uint_as_float(pb[k]);
+                    q[QW * kQueueSlots + slot] = __uint_as_float(is);
+                    q[(QW + 1) * kQueueSlots + slot] = inv_m;
+                }
+                qn += __popc(vote);
+                if (qn >= 32) {
+                    __syncwarp();
+                    drain(lane);
+                    __syncwarp();
+                    if (lane < qn - 32) {
+#pragma unroll
+                        for (int f = 0; f < QW + 2; ++f) q[f * kQueueSlots + lane] = q[f * kQueueSlots + 32 + lane];
+                    }
+                    __syncwarp();
+                    qn -= 32;
+                }
+            };
+            // the warp runs the rounds in step (a lane past the segment's last
+            // item computes samples that are not queued), so its votes see all
+            // 32 lanes
+            const int32_t stride = static_cast<int32_t>(blockDim.x) * KI;
+            for (int32_t ib = it0 + (tid & ~31) * KI; ib < it1; ib += stride) {
+#pragma unroll
+                for (int k = 0; k < KI; ++k) {
+                    isum[k * 32 + lane] = 0.0f;
+                    isum[32 * KI + k * 32 + lane] = 0.0f;
+                }
+                __syncwarp();
+#pragma unroll 1
+                for (int k = 0; k < KI; ++k) {
+                    const int32_t item = ib + k * 32 + lane;
+                    const bool ivalid = item < it1;
+                    const uint32_t h = ivalid ? ih[item] : 0u;
+                    const R inv_m = R(1) / static_cast<R>(sm[h]);
+                    R xi[D];                                 // i_d as R
+                    {
+                        uint32_t r = h;
+#pragma unroll
+                        for (int d = 0; d < D; ++d) {
+                            const uint32_t qq = r / static_cast<uint32_t>(M);
+                            xi[d] = static_cast<R>(r - qq * static_cast<uint32_t>(M));
+                            r = qq;
+                        }
+                    }
+#pragma unroll 1
+                    for (int gi = 0; gi < GPI; ++gi) {
+                        const int32_t grp = item * GPI + gi;
+                        uint32_t uw[SS::kUniforms];
+                        group_words<D>(uw, grp, P.itn, call, task, P.rk);
+#pragma unroll
+                        for (int sgi = 0; sgi < G; ++sgi) {
+                            R y[D];
+                            uint32_t pb[NB];
+#pragma unroll
+                            for (int k2 = 0; k2 < NB; ++k2) pb[k2] = 0u;
+                            R jac = R(1);
+#pragma unroll
+                            for (int d = 0; d < D; ++d) {
+                                const float uf = static_cast<float>(uw[sgi * D + d]) * 2.3283064365386963e-10f;   // word 2^-32
+                                const R x = fmaf(uf, invM, xi[d] * invM);
+                                const R t = x * nbR;
+                                int b = static_cast<int>(t);
+                                b = b < nb - 1 ? b : nb - 1;
+                                const R fr = t - static_cast<R>(b);
+                                const Real2<R> e = s_map[d * nb + b];
+                                y[d] = fma(e.dy, fr, e.y0);
+                                jac *= e.dy;
+                                pb[d >> 2] |= static_cast<uint32_t>(b) << (8 * (d & 3));
+                            }
+                            R r[NI], qc, Ec;
+                            const R kin = kin_at<R, NLEG, STRAT>(C, y, jac, r, qc, Ec);
+                            push(ivalid && kin != R(0), kin, r, qc, Ec, pb, static_cast<uint32_t>(k * 32 + lane), inv_m);
+                        }
+                    }
+                }
+                // the round's samples are all evaluated: its item sums are complete
+                __syncwarp();
+                if (lane < qn) drain(lane);
+                qn = 0;
+                __syncwarp();
+#pragma unroll
+                for (int k = 0; k < KI; ++k) {
+                    const int32_t item = ib + k * 32 + lane;
+                    if (item < it1)
+                        rec[item] = make_double2(static_cast<double>(isum[k * 32 + lane]),
+                                                 static_cast<double>(isum[32 * KI + k * 32 + lane]));
+                }
+                __syncwarp();
+            }
+        } else {
+            // FP64: one thread per item, the item's sums in its registers
+            for (int32_t item = it0 + tid; item < it1; item += blockDim.x) {
+                const uint32_t h = ih[item];
+                const R inv_m = R(1) / static_cast<R>(sm[h]);
+                R xi[D];                                     // i_d as R
+                {
+                    uint32_t r = h;
 #pragma unroll
                     for (int d = 0; d < D; ++d) {
-                        R x;
-                        if constexpr (F32) {
-                            const float uf = static_cast<float>(uw[sgi * D + d]) * 2.3283064365386963e-10f;   // word 2^-32
-                            x = fmaf(uf, invM, xi[d] * invM);
-                        } else {
-                            x = (xi[d] + u[sgi * D + d]) / static_cast<R>(M);
-                        }
-                        const R t = x * nbR;
-                        int b = static_cast<int>(t);
-                        b = b < nb - 1 ? b : nb - 1;
-                        const R fr = t - static_cast<R>(b);
-                        const Real2<R> e = s_map[d * nb + b];
-                        y[d] = fma(e.dy, fr, e.y0);
-                        jac *= e.dy;
-                        bin[d] = b;
-                    }
-                    const R w = weight_at<R, NLEG, STRAT>(C, y, jac, s_spline, knots, g, inv_step, q0, lq0_step, qN,
-                                                   ncoef);
-                    const R w2 = w * w;
-                    s1 += w;
-                    s2 += w2;
-                    acc_w.add(w);
-                    acc_w2.add(w2);
-                    if (w2 != R(0)) {
-                        const R w2m = w2 * inv_m;
-#pragma unroll
-                        for (int d = 0; d < D; ++d) atomicAdd(&w_hist[d * nb + bin[d]], w2m);
+                        const uint32_t qq = r / static_cast<uint32_t>(M);
+                        xi[d] = static_cast<R>(r - qq * static_cast<uint32_t>(M));
+                        r = qq;
                     }
                 }
+                R s1 = R(0), s2 = R(0);
+#pragma unroll 1
+                for (int gi = 0; gi < GPI; ++gi) {
+                    const int32_t grp = item * GPI + gi;
+                    R u[SS::kUniforms];
+                    group_uniforms<D, F32, R>(u, grp, P.itn, call, task, P.rk);
+#pragma unroll
+                    for (int sgi = 0; sgi < G; ++sgi) {
+                        R y[D];
+                        int bin[D];
+                        R jac = R(1);
+#pragma unroll
+                        for (int d = 0; d < D; ++d) {
+                            const R x = (xi[d] + u[sgi * D + d]) / static_cast<R>(M);
+                            const R t = x * nbR;
+                            int b = static_cast<int>(t);
+                            b = b < nb - 1 ? b : nb - 1;
+                            const R fr = t - static_cast<R>(b);
+                            const Real2<R> e = s_map[d * nb + b];
+                            y[d] = fma(e.dy, fr, e.y0);
+                            jac *= e.dy;
+                            bin[d] = b;
+                        }
+                        const R w = weight_at<R, NLEG, STRAT>(C, y, jac, s_spline, knots, g, inv_step, q0, lq0_step,
+                                                              qN, ncoef);
+                        const R w2 = w * w;
+                        s1 += w;
+                        s2 += w2;
+                        acc_w.add(w);
+                        acc_w2.add(w2);
+                        if (w2 != R(0)) {
+                            const R w2m = w2 * inv_m;
+#pragma unroll
+                            for (int d = 0; d < D; ++d) atomicAdd(&w_hist[d * nb + bin[d]], w2m);
+                        }
+                    }
+                }
+                rec[item] = make_double2(static_cast<double>(s1), static_cast<double>(s2));
             }
-            rec[item] = make_double2(static_cast<double>(s1), static_cast<double>(s2));
         }
     }
 
@@ -944,7 +1080,13 @@ eval_kernel(EvalParams P) {
     R* s_spline = reinterpret_cast<R*>(smem_raw);
     const int nsp = P.smem_spline_elems;
     Real2<R>* s_map = reinterpret_cast<Real2<R>*>(s_spline + ((nsp + 3) & ~3));
-    const int map_elems = kMaxDim * P.geo.nbins_max;
+    // map table and per-warp histograms of kDims x nbins_max entries: the
+    // largest process the library supports, or, in the extended
+    // instantiations, the largest process of their NMAX (the stratified
+    // queue's item sums need the room; plain 2 -> 2 kernels measured slower
+    // with the smaller stride)
+    constexpr int kDims = STRAT ? 3 * (NMAX - 2) : kMaxDim;
+    const int map_elems = kDims * P.geo.nbins_max;
     R* s_hist = reinterpret_cast<R*>(s_map + map_elems);      // [warps][map_elems]
     double* s_red = reinterpret_cast<double*>(s_hist + (((THREADS / 32) * map_elems + 3) & ~3));
     float* s_queue = reinterpret_cast<float*>(s_red + 2 * 32);   // FP32: [warps][queue_words][kQueueSlots]
@@ -977,10 +1119,10 @@ eval_kernel(EvalParams P) {
             const TaskConst tc = P.tconst[seg.task];
             __syncthreads();
             switch (sd.n) {
-                case 3: if constexpr (NMAX >= 3) run_segment<R, 3, STRAT, SPL>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue); break;
-                case 4: if constexpr (NMAX >= 4) run_segment<R, 4, STRAT, SPL>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue); break;
-                case 5: if constexpr (NMAX >= 5) run_segment<R, 5, STRAT, SPL>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue); break;
-                case 6: if constexpr (NMAX >= 6) run_segment<R, 6, STRAT, SPL>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue); break;
+                case 3: if constexpr (NMAX >= 3) run_segment<R, 3, STRAT, SPL>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue, map_elems); break;
+                case 4: if constexpr (NMAX >= 4) run_segment<R, 4, STRAT, SPL>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue, map_elems); break;
+                case 5: if constexpr (NMAX >= 5) run_segment<R, 5, STRAT, SPL>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue, map_elems); break;
+                case 6: if constexpr (NMAX >= 6) run_segment<R, 6, STRAT, SPL>(P, seg, sd, td, tc, s_spline, s_map, s_hist, s_red, s_queue, map_elems); break;
                 default: break;
             }
         }

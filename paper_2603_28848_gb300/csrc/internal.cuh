@@ -29,6 +29,16 @@ __host__ __device__ constexpr int vjp_queue_words(int nleg, bool tangent) {
     return tangent ? 3 + (nleg - 2) : 7 + 2 * (nleg - 2);
 }
 constexpr int kItem = 8;               // samples per item of stratified sampling (a multiple of every group size)
+
+// Stratified sampling in the FP32 sample kernel: the items a lane takes
+// between two flushes of its warp's sample queue, and the floats of one
+// warp's queue: the plain queue words of each sample plus its item's slot in
+// the warp's round of 32 kStratItemsPerLane items and 1 / m_h, then the
+// round's per-item sums of w and w^2.
+constexpr int kStratItemsPerLane = 2;
+__host__ __device__ constexpr int strat_queue_floats(int nleg) {
+    return kQueueSlots * (queue_words(nleg) + 2) + 2 * 32 * kStratItemsPerLane;
+}
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTwoPi = 6.28318530717958647692;
 
