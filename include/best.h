@@ -400,6 +400,22 @@ best_status best_get_budgets(best_ctx* ctx, int64_t* neval, void* stream);
  * is NULL or the iteration is out of range. */
 best_status best_partition_groups(best_ctx* ctx, int32_t iteration, int64_t* groups);
 
+/* The chunk bounds of the dynamic work partition of one VEGAS iteration
+ * (host arithmetic only, no device access; the sample kernel's CTAs take the
+ * chunks in order from an atomic counter).  `cost`: the iteration's
+ * estimated cost in the partition's units (per sample group, its samples x
+ * (dimensions + 6)); `grid`: the persistent grid's CTAs.  *chunks receives
+ * the chunk count, 16 x grid; bounds (caller-owned host array of n int64,
+ * n >= *chunks + 1) receives the chunk starts: bounds[0] = 0, bounds[*chunks]
+ * = cost, non-decreasing.  With cost >= 16 x grid x 98304 (98304: 8192
+ * samples of a 2 -> 2 task) the chunks come in 8 stages of 2 x grid equal
+ * chunks, the stages covering 1/2, 1/4, ... of the cost and the last one the
+ * remainder; with less, max(grid, cost / 98304) equal chunks and empty ones
+ * after them.  BEST_ERR_INVALID when cost < 0, grid < 1, chunks is NULL, or
+ * bounds is NULL or too short (*chunks is set first, so a call with n = 0
+ * asks for the count). */
+best_status best_chunk_bounds(int64_t cost, int32_t grid, int64_t* bounds, int32_t n, int32_t* chunks);
+
 /* Integrand evaluations of one sweep: in VEGAS iteration `iteration` (one
  * launch of the sample kernel), or in all iterations when iteration < 0.
  * With variance-driven budgets these are the next sweep's budgets as the

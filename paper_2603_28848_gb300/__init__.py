@@ -13,13 +13,30 @@ import numpy as np
 from . import _lib
 from ._lib import BestError, check
 
-__all__ = ["Collision", "BestError", "build", "config_from_problem", "fixed_sample_collision",
+__all__ = ["Collision", "BestError", "build", "chunk_bounds", "config_from_problem", "fixed_sample_collision",
            "vegas_iteration_noalloc"]
 
 
 def build(verbose=False, force=False):
     from .buildlib import build as _build
     return _build(verbose=verbose, force=force)
+
+
+def chunk_bounds(cost, grid):
+    """Chunk starts of the dynamic work partition of one VEGAS iteration of
+    estimated cost `cost` over `grid` persistent CTAs (best_chunk_bounds;
+    host arithmetic, no device needed): int64 array of chunks + 1 entries,
+    0 first and cost last."""
+    lib = _lib.load()
+    k = ctypes.c_int32(0)
+    lib.best_chunk_bounds(int(cost), int(grid), None, 0, ctypes.byref(k))     # asks for the count
+    if k.value <= 0:
+        raise BestError(f"best_chunk_bounds: {lib.best_last_error(None).decode()}")
+    out = np.zeros(k.value + 1, dtype=np.int64)
+    st = lib.best_chunk_bounds(int(cost), int(grid), out.ctypes.data_as(ctypes.c_void_p), len(out), ctypes.byref(k))
+    if st != 0:
+        raise BestError(f"best_chunk_bounds: {lib.best_last_error(None).decode()}")
+    return out
 
 
 def config_from_problem(problem, precision):

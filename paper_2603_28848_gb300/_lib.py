@@ -78,6 +78,7 @@ SIGNATURES = {
     "best_num_side_integrals": ([c_void_p], c_int32),
     "best_sweep_samples": ([c_void_p, c_int32], c_int64),
     "best_partition_groups": ([c_void_p, c_int32, c_void_p], c_int32),
+    "best_chunk_bounds": ([c_int64, c_int32, c_void_p, c_int32, c_void_p], c_int32),
     "best_get_task_results": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "best_map_stride": ([c_void_p], c_int64),
     "best_get_maps": ([c_void_p, c_void_p], c_int32),

@@ -1782,6 +1782,16 @@ best_status best_get_budgets(best_ctx* ctx, int64_t* neval, void* stream) {
     return BEST_OK;
 }
 
+best_status best_chunk_bounds(int64_t cost, int32_t grid, int64_t* bounds, int32_t n, int32_t* chunks) {
+    if (!chunks || grid < 1 || cost < 0) return fail(nullptr, BEST_ERR_INVALID, "chunk bounds: invalid argument");
+    const int K = chunk_count(grid);
+    *chunks = K;
+    if (!bounds || n < K + 1) return fail(nullptr, BEST_ERR_INVALID, "chunk bounds: bounds needs %d entries", K + 1);
+    const ChunkShape sh = chunk_shape(cost, grid);
+    for (int c = 0; c <= K; ++c) bounds[c] = chunk_bound(cost, c, sh);
+    return BEST_OK;
+}
+
 best_status best_partition_groups(best_ctx* ctx, int32_t iteration, int64_t* groups) {
     if (!ctx || !groups) return fail(ctx, BEST_ERR_INVALID, "NULL argument");
     if (iteration < 0 || iteration >= ctx->max_nitn) return fail(ctx, BEST_ERR_INVALID, "iteration out of range");
