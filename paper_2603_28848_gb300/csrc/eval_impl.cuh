@@ -1083,8 +1083,8 @@ eval_kernel(EvalParams P) {
     // map table and per-warp histograms of kDims x nbins_max entries: the
     // largest process the library supports, or, in the extended
     // instantiations, the largest process of their NMAX (the stratified
-    // queue's item sums need the room; plain 2 -> 2 kernels measured slower
-    // with the smaller stride)
+    // queue's item sums need the room).  A compile-time constant: read as a
+    // kernel parameter, the plain 2 -> 2 kernel measured 1.8% slower.
     constexpr int kDims = STRAT ? 3 * (NMAX - 2) : kMaxDim;
     const int map_elems = kDims * P.geo.nbins_max;
     R* s_hist = reinterpret_cast<R*>(s_map + map_elems);      // [warps][map_elems]
